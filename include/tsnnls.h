@@ -1,0 +1,250 @@
+/*
+ * tsnnls.h -- C ABI of a GB300 (sm_103a) block principal pivoting solver for
+ *
+ *     min_x 1/2 ||A x - b||_2^2   subject to   x >= 0              (Eq. 1)
+ *
+ * where A is an m x n sparse matrix with m > n and full column rank, given in
+ * CSR form.  The method is the block principal pivoting algorithm of Section 2
+ * (algorithm box): it moves through complementary basic solutions
+ *     x_F = argmin ||A_F x_F - b||                                  (Eq. 4)
+ *     y_G = A_G^T (A_F x_F - b)                                      (Eq. 5)
+ * exchanging the infeasible variables (negative entries of x_F and y_G)
+ * between the index sets F and G, with a backup counter p = 3 and a
+ * single-variable fallback, and zeroing entries within 1e-12 of zero.  As in
+ * Section 3, A^T A and A^T b are formed once and every pivot factors the
+ * F x F block of A^T A.
+ *
+ * All computation runs on the GPU in this library's own kernels.  There is no
+ * CPU fallback: without a usable CUDA device every call returns
+ * TSNNLS_ENODEV or TSNNLS_ECUDA.
+ *
+ * Conventions for every function below
+ *   - Return value: a TSNNLS_* status code; no function throws or aborts.
+ *   - Pointers marked "device" must be device memory of the context's GPU;
+ *     "host" pointers are ordinary (pageable or pinned) host memory.
+ *   - Input arrays are read-only and remain owned by the caller.  The library
+ *     copies what it needs, except where a call says the caller's buffers must
+ *     stay alive until the call (or its ticket) completes.
+ *   - Indices are 0-based.  CSR column indices must be strictly ascending
+ *     within a row (sorted, no duplicates); violations give TSNNLS_EINVAL.
+ *   - Calls on one context are serialised by the context (thread-safe), but
+ *     run in the order they are made.
+ */
+#ifndef TSNNLS_H
+#define TSNNLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TSNNLS_OK 0
+#define TSNNLS_EINVAL 1    /* bad argument: m <= n, n == 0, malformed CSR, NULL pointer */
+#define TSNNLS_ENOMEM 2    /* device allocation failed */
+#define TSNNLS_EADMIT 3    /* the problem's device footprint exceeds the context's HBM budget */
+#define TSNNLS_ENOTPD 4    /* Cholesky breakdown of (A^T A)_FF: A_F is (numerically) rank deficient */
+#define TSNNLS_EMAXITER 5  /* the pivot loop hit opts.max_iter without a feasible split */
+#define TSNNLS_ENOCONV 6   /* iterative refinement stagnated above opts.rel_tol */
+#define TSNNLS_ETIMEOUT 7  /* a bounded device-side wait gave up (no kernel hangs) */
+#define TSNNLS_PENDING 8   /* tsnnls_poll: the ticket has not finished yet */
+#define TSNNLS_ECUDA 9     /* a CUDA runtime call failed */
+#define TSNNLS_ENODEV 10   /* no usable CUDA device / the requested device does not exist */
+
+/* ---- precision / path selectors ---------------------------------------- */
+/* MIXED: Gram block gathered and factored in FP32 (tensor-core trailing
+ *   updates), FP32 triangular solves, and FP64 iterative refinement of x_F
+ *   with FP64 residuals b - A_F x_F, FP64 A^T r and FP64 sign tests.
+ * FP64: every step in FP64, one normal-equations solve per pivot and no
+ *   refinement (the plain baseline path). */
+#define TSNNLS_MIXED 0
+#define TSNNLS_FP64 1
+
+#define TSNNLS_PATH_AUTO 0    /* factor when A^T A fits the budget, LSQR otherwise */
+#define TSNNLS_PATH_FACTOR 1  /* normal equations on the cached A^T A (Sections 2-3) */
+#define TSNNLS_PATH_LSQR 2    /* LSQR on A_F for each pivot (Section 3's LSQR, no A^T A) */
+
+/* A sparse matrix in CSR form.  row_ptr has m+1 entries, row_ptr[0] == 0 and
+ * row_ptr[m] == nnz; col_idx and val have nnz entries.  on_device selects
+ * where row_ptr/col_idx/val AND the b / x_out arguments of the call live:
+ * 0 = host memory, 1 = device memory of the context's GPU. */
+typedef struct {
+    int64_t m, n, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const double *val;
+    int32_t on_device;
+} tsnnls_csr;
+
+typedef struct {
+    double rel_tol;      /* refinement stops when ||dx_F||_inf <= rel_tol ||x_F||_inf (default 1e-14) */
+    double zero_tol;     /* |x_i|, |y_i| below this are set to 0 after each update (default 1e-12, Section 2) */
+    int32_t p_max;       /* backup full exchanges before the single-variable rule (default 3) */
+    int32_t max_iter;    /* pivot limit; 0 means 10 n + 100 */
+    int32_t precision;   /* TSNNLS_MIXED (default) or TSNNLS_FP64 */
+    int32_t path;        /* TSNNLS_PATH_* (default AUTO) */
+    int32_t max_refine;  /* refinement steps per pivot before TSNNLS_ENOCONV (default 30) */
+    int32_t reserved;
+} tsnnls_opts;
+
+typedef struct {
+    int32_t status;          /* same as the return value of the call */
+    int32_t iters;           /* pivots performed (exchange + solve) */
+    int32_t refine_steps;    /* total refinement steps over all pivots */
+    int32_t nF;              /* |F| at the solution */
+    int32_t path_used;       /* TSNNLS_PATH_FACTOR or TSNNLS_PATH_LSQR */
+    int32_t precision_used;  /* TSNNLS_MIXED or TSNNLS_FP64 */
+    double last_rel_step;    /* ||dx_F||_inf / ||x_F||_inf of the last refinement step */
+    double time_ms;          /* device time of the solve, CUDA events */
+    int64_t kernel_launches; /* kernels this call launched */
+} tsnnls_info;
+
+typedef struct tsnnls_ctx tsnnls_ctx;
+typedef int64_t tsnnls_ticket;
+
+/* Fill *opts with the defaults listed above. */
+void tsnnls_opts_default(tsnnls_opts *opts);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *tsnnls_strerror(int status);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the context may hold for problem state at once (0 = 90 % of
+ * the free memory at creation).  All work runs on the context's own
+ * non-blocking streams.  *ctx is set only on TSNNLS_OK. */
+int tsnnls_ctx_create(tsnnls_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Wait for all outstanding tickets, free every device buffer, destroy ctx. */
+void tsnnls_ctx_destroy(tsnnls_ctx *ctx);
+
+/* Blocking solve of Eq. 1 (Section 2 algorithm box; Section 3 caching of
+ * A^T A).  b has m entries, x_out n entries, both in host or device memory
+ * as A->on_device says.  x_out is written only on TSNNLS_OK.  opts may be
+ * NULL (defaults); info may be NULL, and is filled on every return.
+ * Thread-safe on one context. */
+int tsnnls_solve(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *x_out,
+                 const tsnnls_opts *opts, tsnnls_info *info);
+
+/* tsnnls_solve with extra outputs, for inspection and tests.  y_out (n
+ * doubles) receives y = A^T (A x - b) on G and 0 on F (Eq. 3, Eq. 5);
+ * inF_out (n bytes) the final F as 0/1 -- both in the same memory space as
+ * x_out and written only on TSNNLS_OK.  trace (host, 5 * trace_cap int64)
+ * receives one row per pivot: {infeasible count, N before the branch
+ * (INT64_MAX = infinity), p after the branch, branch (0 = count dropped and
+ * full exchange, 1 = backup full exchange, 2 = single exchange of the
+ * largest infeasible index), |F| after the exchange}.  Any of the three may
+ * be NULL. */
+int tsnnls_solve_ex(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *x_out,
+                    double *y_out, uint8_t *inF_out, int64_t *trace, int64_t trace_cap,
+                    const tsnnls_opts *opts, tsnnls_info *info);
+
+/* Asynchronous solve: returns at once with *ticket.  A's arrays, b and x_out
+ * must stay valid and unmodified until tsnnls_poll/tsnnls_wait reports
+ * completion of the ticket.  The request is admitted by device footprint:
+ * it waits in the context's queue until its state fits the HBM budget and a
+ * slot is free, then runs concurrently with the other admitted requests
+ * (continuous batching across the context's streams). */
+int tsnnls_submit(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *x_out,
+                  const tsnnls_opts *opts, tsnnls_ticket *ticket);
+
+/* TSNNLS_PENDING while the ticket runs; otherwise its final status (and the
+ * ticket is released; polling it again gives TSNNLS_EINVAL). */
+int tsnnls_poll(tsnnls_ctx *ctx, tsnnls_ticket ticket, tsnnls_info *info);
+
+/* Wait up to timeout_us microseconds (< 0: no limit).  Returns
+ * TSNNLS_PENDING if the time ran out, else as tsnnls_poll. */
+int tsnnls_wait(tsnnls_ctx *ctx, tsnnls_ticket ticket, int64_t timeout_us, tsnnls_info *info);
+
+/* Batched dense solves (many small or uneven problems).  Problem i has
+ * A_i = a[i] (m[i] x n[i], row-major FP32, device memory), b_i = b[i]
+ * (m[i] doubles, device) and x_i = x_out[i] (n[i] doubles, device).  The
+ * pointer arrays a, b, x_out, m and n are host arrays of `count` entries.
+ * All pivot iterations of all problems run in one persistent kernel launched
+ * from a captured CUDA graph; A^T A is formed by one batched GEMM.  status_out
+ * (host, count entries, may be NULL) receives each problem's status.
+ * Returns TSNNLS_OK if every problem succeeded, else the first failure. */
+int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
+                             const float *const *a, const double *const *b,
+                             double *const *x_out, const tsnnls_opts *opts,
+                             int32_t *status_out, tsnnls_info *info);
+
+/* ---- per-phase device-time accounting ----------------------------------
+ * When enabled, blocking solves on the context bracket every phase of the
+ * pivot loop with CUDA events on the stream the kernels run on, and add up
+ * the elapsed device time, the launches, and the phase's algorithmic work
+ * (bytes for bandwidth-bound phases, flops for the factorisation) as the
+ * per-unit figures of the method give them.  Off by default. */
+#define TSNNLS_PHASE_SETUP 0     /* validation and CSR -> CSC transpose */
+#define TSNNLS_PHASE_GRAM 1      /* A^T A and A^T b (Section 3) */
+#define TSNNLS_PHASE_EXCHANGE 2  /* zeroing, infeasible count, exchange (Section 2) */
+#define TSNNLS_PHASE_GATHER 3    /* (A^T A)_FF */
+#define TSNNLS_PHASE_FACTOR 4    /* Cholesky */
+#define TSNNLS_PHASE_TRSV 5      /* the two triangular solves */
+#define TSNNLS_PHASE_SPMV 6      /* FP64 A x and A^T r (Eq. 5, refinement) */
+#define TSNNLS_PHASE_VECTOR 7    /* small vector kernels (gathers, updates) */
+#define TSNNLS_PHASE_LSQR 8      /* LSQR iterations on A_F */
+#define TSNNLS_NUM_PHASES 9
+
+typedef struct {
+    double ms;          /* summed device time */
+    int64_t launches;   /* kernel launches */
+    double bytes;       /* algorithmic DRAM bytes (bandwidth-bound phases) */
+    double flops;       /* algorithmic flops */
+} tsnnls_phase_stat;
+
+/* enable != 0 turns accounting on and zeroes the counters; 0 turns it off. */
+int tsnnls_profile_enable(tsnnls_ctx *ctx, int32_t enable);
+
+/* Copy min(count, TSNNLS_NUM_PHASES) phase records (host array). */
+int tsnnls_profile_read(tsnnls_ctx *ctx, tsnnls_phase_stat *out, int32_t count);
+
+/* ---- step-level entry points --------------------------------------------
+ * Each runs one step of the pivot loop on caller-owned DEVICE buffers, on
+ * the context's stream, and returns after the step completes.  They exist so
+ * that every step can be checked on its own against an independent
+ * implementation. */
+
+/* Section 3: G = A^T A by column dot products (lower triangle written,
+ * column-major, leading dimension ldg >= n; the strict upper triangle is not
+ * touched) and c = A^T b.  precision TSNNLS_MIXED writes G as float,
+ * TSNNLS_FP64 as double; c is always double.  A must be on the device. */
+int tsnnls_gram(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, int32_t precision,
+                void *G, int64_t ldg, double *c);
+
+/* Section 3: S = G_FF (lower triangle, column-major, leading dimension lds)
+ * for the index list F (k ascending int32 indices < n) from a G laid out as
+ * tsnnls_gram writes it.  Element type by precision as above. */
+int tsnnls_gather(tsnnls_ctx *ctx, int32_t precision, const void *G, int64_t ldg,
+                  const int32_t *F, int64_t k, void *S, int64_t lds);
+
+/* Section 2 (normal equations solver): in-place lower Cholesky S = L L^T of a
+ * k x k column-major symmetric positive definite matrix (lower triangle
+ * read and overwritten; strict upper triangle untouched).  Blocked,
+ * right-looking; MIXED runs in FP32 with tensor-core trailing updates, FP64
+ * in FP64.  *info_out (host, may be NULL) = 0, or 1 + the column of the
+ * first non-positive pivot (then the call returns TSNNLS_ENOTPD). */
+int tsnnls_cholesky(tsnnls_ctx *ctx, int32_t precision, void *S, int64_t k, int64_t lds,
+                    int32_t *info_out);
+
+/* Eq. 4 through the factor: overwrite rhs (k entries, float for MIXED,
+ * double for FP64) with (L L^T)^{-1} rhs, using the lower factor L written
+ * by tsnnls_cholesky.  Two triangular solves; the diagonal blocks are solved
+ * warp by warp. */
+int tsnnls_chol_solve(tsnnls_ctx *ctx, int32_t precision, const void *L, int64_t k, int64_t lds,
+                      void *rhs);
+
+/* Sparse products in FP64 on a device CSR matrix:
+ *   trans == 0:  out = alpha * A x + beta * z   (x: n entries, out, z: m)
+ *   trans == 1:  out = alpha * A^T x + beta * z (x: m entries, out, z: n)
+ * z may be NULL when beta == 0.  All vectors are device doubles.  Each output
+ * entry is summed in a fixed order, so results are reproducible. */
+int tsnnls_spmv(tsnnls_ctx *ctx, const tsnnls_csr *A, int32_t trans, double alpha,
+                const double *x, double beta, const double *z, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSNNLS_H */

@@ -1,0 +1,346 @@
+"""Python binding of libtsnnls (include/tsnnls.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels.  There is no CPU
+path: if the library is missing or no GPU is usable, the calls raise.
+
+Host inputs are numpy arrays; device inputs are torch CUDA tensors (PyTorch
+provides device memory and streams here, nothing else).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+OK, EINVAL, ENOMEM, EADMIT, ENOTPD, EMAXITER, ENOCONV, ETIMEOUT, PENDING, ECUDA, ENODEV = range(11)
+MIXED, FP64 = 0, 1
+PATH_AUTO, PATH_FACTOR, PATH_LSQR = 0, 1, 2
+
+# every entry point declared in include/tsnnls.h
+EXPORTS = (
+    "tsnnls_opts_default", "tsnnls_strerror", "tsnnls_ctx_create", "tsnnls_ctx_destroy",
+    "tsnnls_solve", "tsnnls_solve_ex", "tsnnls_submit", "tsnnls_poll", "tsnnls_wait",
+    "tsnnls_solve_batch_dense", "tsnnls_gram", "tsnnls_gather", "tsnnls_cholesky",
+    "tsnnls_chol_solve", "tsnnls_spmv", "tsnnls_profile_enable", "tsnnls_profile_read",
+)
+
+PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr")
+
+
+class TsnnlsError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} (status {status})")
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("rel_tol", ctypes.c_double), ("zero_tol", ctypes.c_double),
+                ("p_max", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("refine_steps", ctypes.c_int32), ("nF", ctypes.c_int32),
+                ("path_used", ctypes.c_int32), ("precision_used", ctypes.c_int32),
+                ("last_rel_step", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build_mod.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libtsnnls.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build_mod.LIB
+    if build_if_missing and not _build_mod.up_to_date():
+        _build_mod.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtsnnls is not built ({path}); run paper_cs_0408029_gb300.build")
+    lib = ctypes.CDLL(path)
+    p, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sigs = {
+        "tsnnls_opts_default": ([ctypes.POINTER(Opts)], None),
+        "tsnnls_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "tsnnls_ctx_create": ([ctypes.POINTER(p), ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+        "tsnnls_ctx_destroy": ([p], None),
+        "tsnnls_solve": ([p, ctypes.POINTER(CSR), p, p, ctypes.POINTER(Opts), ctypes.POINTER(Info)],
+                         ctypes.c_int),
+        "tsnnls_solve_ex": ([p, ctypes.POINTER(CSR), p, p, p, p, p, i64, ctypes.POINTER(Opts),
+                             ctypes.POINTER(Info)], ctypes.c_int),
+        "tsnnls_submit": ([p, ctypes.POINTER(CSR), p, p, ctypes.POINTER(Opts),
+                           ctypes.POINTER(i64)], ctypes.c_int),
+        "tsnnls_poll": ([p, i64, ctypes.POINTER(Info)], ctypes.c_int),
+        "tsnnls_wait": ([p, i64, i64, ctypes.POINTER(Info)], ctypes.c_int),
+        "tsnnls_solve_batch_dense": ([p, i32, p, p, p, p, p, ctypes.POINTER(Opts), p,
+                                      ctypes.POINTER(Info)], ctypes.c_int),
+        "tsnnls_gram": ([p, ctypes.POINTER(CSR), p, i32, p, i64, p], ctypes.c_int),
+        "tsnnls_gather": ([p, i32, p, i64, p, i64, p, i64], ctypes.c_int),
+        "tsnnls_cholesky": ([p, i32, p, i64, i64, ctypes.POINTER(i32)], ctypes.c_int),
+        "tsnnls_chol_solve": ([p, i32, p, i64, i64, p], ctypes.c_int),
+        "tsnnls_spmv": ([p, ctypes.POINTER(CSR), i32, d, p, d, p, p], ctypes.c_int),
+        "tsnnls_profile_enable": ([p, i32], ctypes.c_int),
+        "tsnnls_profile_read": ([p, p, i32], ctypes.c_int),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load(build_if_missing=False).tsnnls_strerror(status).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return f"status {status}"
+
+
+def _check(st, what):
+    if st != OK:
+        raise TsnnlsError(st, what)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().tsnnls_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"mixed": MIXED, "fp64": FP64}[v]
+        if k == "path" and isinstance(v, str):
+            v = {"auto": PATH_AUTO, "factor": PATH_FACTOR, "lsqr": PATH_LSQR}[v]
+        setattr(o, k, v)
+    return o
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dev_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class HostCSR:
+    """CSR arrays in host memory (keeps contiguous copies alive)."""
+
+    def __init__(self, m, n, row_ptr, col_idx, val):
+        self.m, self.n = int(m), int(n)
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        self.col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        self.val = np.ascontiguousarray(val, dtype=np.float64)
+
+    @classmethod
+    def from_problem(cls, p):
+        return cls(p.m, p.n, p.row_ptr, p.col_idx, p.val)
+
+    def struct(self):
+        return CSR(self.m, self.n, int(self.row_ptr[-1]), _np_ptr(self.row_ptr),
+                   _np_ptr(self.col_idx), _np_ptr(self.val), 0)
+
+
+class DeviceCSR:
+    """CSR arrays resident in device memory (torch CUDA tensors)."""
+
+    def __init__(self, m, n, row_ptr, col_idx, val):
+        self.m, self.n = int(m), int(n)
+        self.row_ptr, self.col_idx, self.val = row_ptr, col_idx, val
+        self.nnz = int(val.numel())
+
+    @classmethod
+    def from_problem(cls, p, device="cuda"):
+        import torch
+
+        return cls(p.m, p.n, torch.as_tensor(p.row_ptr, dtype=torch.int64, device=device),
+                   torch.as_tensor(p.col_idx, dtype=torch.int32, device=device),
+                   torch.as_tensor(p.val, dtype=torch.float64, device=device))
+
+    def struct(self):
+        return CSR(self.m, self.n, self.nnz, _dev_ptr(self.row_ptr), _dev_ptr(self.col_idx),
+                   _dev_ptr(self.val), 1)
+
+
+class PhaseStat(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_int64), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
+
+class Context:
+    """A tsnnls context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        _check(self._lib.tsnnls_ctx_create(ctypes.byref(self._h), device, hbm_budget), "ctx_create")
+
+    def close(self):
+        if self._h:
+            self._lib.tsnnls_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    # -- solves -------------------------------------------------------------
+
+    def solve(self, A, b, x_out=None, opts=None, raise_on_error=True, **kw):
+        """Solve Eq. 1.  A is HostCSR (b numpy) or DeviceCSR (b a CUDA tensor).
+        Returns (x, Info)."""
+        o = opts if opts is not None else default_opts(**kw)
+        info = Info()
+        s = A.struct()
+        if isinstance(A, HostCSR):
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            x = np.empty(A.n) if x_out is None else x_out
+            st = self._lib.tsnnls_solve(self._h, ctypes.byref(s), _np_ptr(b), _np_ptr(x),
+                                        ctypes.byref(o), ctypes.byref(info))
+        else:
+            import torch
+
+            x = torch.empty(A.n, dtype=torch.float64, device=b.device) if x_out is None else x_out
+            st = self._lib.tsnnls_solve(self._h, ctypes.byref(s), _dev_ptr(b), _dev_ptr(x),
+                                        ctypes.byref(o), ctypes.byref(info))
+        if raise_on_error:
+            _check(st, "solve")
+        return x, info
+
+    def solve_ex(self, A: HostCSR, b, trace_cap=1000, opts=None, **kw):
+        """Host solve returning (x, y, inF(bool), trace[iters, 5], Info)."""
+        o = opts if opts is not None else default_opts(**kw)
+        info = Info()
+        s = A.struct()
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty(A.n)
+        y = np.empty(A.n)
+        f = np.empty(A.n, dtype=np.uint8)
+        tr = np.zeros((trace_cap, 5), dtype=np.int64)
+        st = self._lib.tsnnls_solve_ex(self._h, ctypes.byref(s), _np_ptr(b), _np_ptr(x), _np_ptr(y),
+                                       _np_ptr(f), _np_ptr(tr), trace_cap, ctypes.byref(o),
+                                       ctypes.byref(info))
+        _check(st, "solve_ex")
+        return x, y, f.astype(bool), tr[: min(info.iters, trace_cap)], info
+
+    def submit(self, A, b, x_out, opts=None, **kw):
+        o = opts if opts is not None else default_opts(**kw)
+        s = A.struct()
+        t = ctypes.c_int64()
+        bp = _np_ptr(b) if isinstance(b, np.ndarray) else _dev_ptr(b)
+        xp = _np_ptr(x_out) if isinstance(x_out, np.ndarray) else _dev_ptr(x_out)
+        _check(self._lib.tsnnls_submit(self._h, ctypes.byref(s), bp, xp, ctypes.byref(o),
+                                       ctypes.byref(t)), "submit")
+        return t.value
+
+    def poll(self, ticket):
+        info = Info()
+        st = self._lib.tsnnls_poll(self._h, ticket, ctypes.byref(info))
+        return st, info
+
+    def wait(self, ticket, timeout_us=-1):
+        info = Info()
+        st = self._lib.tsnnls_wait(self._h, ticket, timeout_us, ctypes.byref(info))
+        return st, info
+
+    def solve_batch_dense(self, a_list, b_list, x_list, opts=None, **kw):
+        """Dense batched solve; a_list: CUDA float32 [m_i, n_i] row-major, b_list,
+        x_list: CUDA float64.  Returns (status array, Info)."""
+        o = opts if opts is not None else default_opts(**kw)
+        cnt = len(a_list)
+        ms = np.array([a.shape[0] for a in a_list], dtype=np.int32)
+        ns = np.array([a.shape[1] for a in a_list], dtype=np.int32)
+        ap = np.array([t.data_ptr() for t in a_list], dtype=np.uint64)
+        bp = np.array([t.data_ptr() for t in b_list], dtype=np.uint64)
+        xp = np.array([t.data_ptr() for t in x_list], dtype=np.uint64)
+        stat = np.zeros(cnt, dtype=np.int32)
+        info = Info()
+        st = self._lib.tsnnls_solve_batch_dense(self._h, cnt, _np_ptr(ms), _np_ptr(ns), _np_ptr(ap),
+                                                _np_ptr(bp), _np_ptr(xp), ctypes.byref(o),
+                                                _np_ptr(stat), ctypes.byref(info))
+        return st, stat, info
+
+    # -- per-phase device time ---------------------------------------------
+
+    def profile(self, enable=True):
+        _check(self._lib.tsnnls_profile_enable(self._h, 1 if enable else 0), "profile_enable")
+
+    def profile_read(self):
+        arr = (PhaseStat * len(PHASES))()
+        _check(self._lib.tsnnls_profile_read(self._h, ctypes.cast(arr, ctypes.c_void_p), len(PHASES)),
+               "profile_read")
+        return {name: {"ms": s.ms, "launches": s.launches, "bytes": s.bytes, "flops": s.flops}
+                for name, s in zip(PHASES, arr)}
+
+    # -- step-level entry points (device tensors) ----------------------------
+
+    def gram(self, A: DeviceCSR, b, precision=MIXED):
+        import torch
+
+        ldg = ((A.n + 31) // 32) * 32
+        dt = torch.float32 if precision == MIXED else torch.float64
+        G = torch.zeros((A.n, ldg), dtype=dt, device=b.device)  # column j = row j of this tensor
+        c = torch.empty(A.n, dtype=torch.float64, device=b.device)
+        s = A.struct()
+        _check(self._lib.tsnnls_gram(self._h, ctypes.byref(s), _dev_ptr(b), precision, _dev_ptr(G),
+                                     ldg, _dev_ptr(c)), "gram")
+        return G, ldg, c
+
+    def gather(self, G, ldg, F, precision=MIXED):
+        import torch
+
+        k = int(F.numel())
+        lds = max(k, 1)
+        S = torch.zeros((max(k, 1), lds), dtype=G.dtype, device=G.device)
+        _check(self._lib.tsnnls_gather(self._h, precision, _dev_ptr(G), ldg, _dev_ptr(F), k,
+                                       _dev_ptr(S), lds), "gather")
+        return S
+
+    def cholesky(self, S, k, lds, precision=MIXED):
+        """In place; S holds column j at S.view(-1)[j*lds : j*lds + k]."""
+        info = ctypes.c_int32()
+        st = self._lib.tsnnls_cholesky(self._h, precision, _dev_ptr(S), k, lds, ctypes.byref(info))
+        return st, info.value
+
+    def chol_solve(self, L, k, lds, rhs, precision=MIXED):
+        _check(self._lib.tsnnls_chol_solve(self._h, precision, _dev_ptr(L), k, lds, _dev_ptr(rhs)),
+               "chol_solve")
+        return rhs
+
+    def spmv(self, A: DeviceCSR, trans, alpha, x, beta=0.0, z=None):
+        import torch
+
+        rows = A.n if trans else A.m
+        out = torch.empty(rows, dtype=torch.float64, device=x.device)
+        zp = _dev_ptr(z) if z is not None else ctypes.c_void_p(0)
+        s = A.struct()
+        _check(self._lib.tsnnls_spmv(self._h, ctypes.byref(s), int(trans), float(alpha), _dev_ptr(x),
+                                     float(beta), zp, _dev_ptr(out)), "spmv")
+        return out

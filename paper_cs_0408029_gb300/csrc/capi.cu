@@ -1,0 +1,433 @@
+// The C ABI declared in include/tsnnls.h: contexts, the blocking and
+// asynchronous solves, and the step-level entry points.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <chrono>
+#include <cstring>
+#include <new>
+
+#include "engine.h"
+
+using namespace tsnnls;
+
+struct tsnnls_ctx {
+    Context c;
+};
+
+namespace {
+
+int check_csr_args(const tsnnls_csr *A, const double *b, const double *x_out) {
+    if (!A || !b || !x_out) return TSNNLS_EINVAL;
+    if (A->n <= 0 || A->m <= A->n || A->nnz < 0) return TSNNLS_EINVAL;
+    if (A->n > INT32_MAX || A->m > INT32_MAX) return TSNNLS_EINVAL;
+    if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val))) return TSNNLS_EINVAL;
+    return TSNNLS_OK;
+}
+
+tsnnls_opts resolve_opts(const tsnnls_opts *o) {
+    tsnnls_opts r;
+    tsnnls_opts_default(&r);
+    if (o) r = *o;
+    if (r.p_max < 0) r.p_max = 0;
+    if (r.max_refine <= 0) r.max_refine = 30;
+    if (!(r.rel_tol > 0)) r.rel_tol = 1e-14;
+    if (!(r.zero_tol >= 0)) r.zero_tol = 1e-12;
+    return r;
+}
+
+void worker_loop(tsnnls_ctx *ctx, int lane_id) {
+    Context &c = ctx->c;
+    cudaSetDevice(c.device);
+    Lane &lane = c.lanes[lane_id];
+    std::unique_lock<std::mutex> lk(c.q_mu);
+    for (;;) {
+        std::shared_ptr<Request> req;
+        c.q_cv.wait(lk, [&] {
+            if (c.stopping) return true;
+            for (tsnnls_ticket t : c.waiting) {
+                auto &r = c.requests[t];
+                if (r->footprint <= c.budget - c.in_use) return true;
+            }
+            return false;
+        });
+        if (c.stopping && c.waiting.empty()) return;
+        // first request in arrival order that fits the free budget
+        for (auto it = c.waiting.begin(); it != c.waiting.end(); ++it) {
+            auto &r = c.requests[*it];
+            if (r->footprint <= c.budget - c.in_use) {
+                req = r;
+                c.waiting.erase(it);
+                break;
+            }
+        }
+        if (!req) {
+            if (c.stopping) return;
+            continue;
+        }
+        c.in_use += req->footprint;
+        c.active += 1;
+        lk.unlock();
+        tsnnls_info info;
+        int st = solve_on_lane(c, lane, req->A, req->b, req->x_out, req->opts, &info, nullptr);
+        lk.lock();
+        c.in_use -= req->footprint;
+        c.active -= 1;
+        req->status = st;
+        req->info = info;
+        req->done = true;
+        c.done_cv.notify_all();
+        c.q_cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void tsnnls_opts_default(tsnnls_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->rel_tol = 1e-14;
+    o->zero_tol = 1e-12;
+    o->p_max = 3;
+    o->max_iter = 0;
+    o->precision = TSNNLS_MIXED;
+    o->path = TSNNLS_PATH_AUTO;
+    o->max_refine = 30;
+}
+
+const char *tsnnls_strerror(int s) {
+    switch (s) {
+        case TSNNLS_OK: return "ok";
+        case TSNNLS_EINVAL: return "invalid argument";
+        case TSNNLS_ENOMEM: return "device allocation failed";
+        case TSNNLS_EADMIT: return "problem does not fit the HBM budget";
+        case TSNNLS_ENOTPD: return "Cholesky breakdown: A_F rank deficient";
+        case TSNNLS_EMAXITER: return "pivot limit reached";
+        case TSNNLS_ENOCONV: return "iterative refinement did not converge";
+        case TSNNLS_ETIMEOUT: return "a device-side wait timed out";
+        case TSNNLS_PENDING: return "pending";
+        case TSNNLS_ECUDA: return "CUDA runtime error";
+        case TSNNLS_ENODEV: return "no usable CUDA device";
+        default: return "unknown status";
+    }
+}
+
+int tsnnls_ctx_create(tsnnls_ctx **out, int device, size_t hbm_budget_bytes) {
+    if (!out) return TSNNLS_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) return TSNNLS_ENODEV;
+    if (device < 0 || device >= count) return TSNNLS_ENODEV;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    tsnnls_ctx *ctx = new (std::nothrow) tsnnls_ctx();
+    if (!ctx) return TSNNLS_ENOMEM;
+    ctx->c.device = device;
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return status_from_cuda(e);
+    }
+    ctx->c.budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
+    // keep freed stream-ordered allocations in the pool for the next solve
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    int st = lane_create(ctx->c.lane0);
+    if (st != TSNNLS_OK) {
+        lane_destroy(ctx->c.lane0);
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return TSNNLS_OK;
+}
+
+static int ensure_workers(tsnnls_ctx *ctx) {
+    Context &c = ctx->c;
+    if (!c.workers.empty()) return TSNNLS_OK;
+    int nl = 4;
+    if (const char *env = std::getenv("TSNNLS_LANES")) nl = std::max(1, std::atoi(env));
+    c.lanes.resize(nl);
+    for (int i = 0; i < nl; ++i) {
+        int st = lane_create(c.lanes[i]);
+        if (st != TSNNLS_OK) return st;
+    }
+    for (int i = 0; i < nl; ++i) c.workers.emplace_back(worker_loop, ctx, i);
+    return TSNNLS_OK;
+}
+
+void tsnnls_ctx_destroy(tsnnls_ctx *ctx) {
+    if (!ctx) return;
+    Context &c = ctx->c;
+    {
+        std::unique_lock<std::mutex> lk(c.q_mu);
+        c.done_cv.wait(lk, [&] { return c.waiting.empty() && c.active == 0; });
+        c.stopping = true;
+        c.q_cv.notify_all();
+    }
+    for (auto &t : c.workers) t.join();
+    for (auto &l : c.lanes) lane_destroy(l);
+    lane_destroy(c.lane0);
+    delete ctx;
+}
+
+int tsnnls_solve_ex(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *x_out,
+                    double *y_out, uint8_t *inF_out, int64_t *trace, int64_t trace_cap,
+                    const tsnnls_opts *opts, tsnnls_info *info);
+
+int tsnnls_solve(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *x_out,
+                 const tsnnls_opts *opts, tsnnls_info *info) {
+    return tsnnls_solve_ex(ctx, A, b, x_out, nullptr, nullptr, nullptr, 0, opts, info);
+}
+
+int tsnnls_solve_ex(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *x_out,
+                    double *y_out, uint8_t *inF_out, int64_t *trace, int64_t trace_cap,
+                    const tsnnls_opts *opts, tsnnls_info *info) {
+    if (info) std::memset(info, 0, sizeof(*info));
+    int st = ctx ? check_csr_args(A, b, x_out) : TSNNLS_EINVAL;
+    if (st != TSNNLS_OK) {
+        if (info) info->status = st;
+        return st;
+    }
+    tsnnls_opts o = resolve_opts(opts);
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    cudaSetDevice(c.device);
+    if (solve_footprint(*A, o) > c.budget) {
+        if (info) info->status = TSNNLS_EADMIT;
+        return TSNNLS_EADMIT;
+    }
+    SolveExtras ex;
+    ex.y_out = y_out;
+    ex.inF_out = inF_out;
+    ex.trace = trace;
+    ex.trace_cap = trace ? trace_cap : 0;
+    return solve_on_lane(c, c.lane0, *A, b, x_out, o, info, &ex);
+}
+
+int tsnnls_submit(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *x_out,
+                  const tsnnls_opts *opts, tsnnls_ticket *ticket) {
+    if (!ctx || !ticket) return TSNNLS_EINVAL;
+    int st = check_csr_args(A, b, x_out);
+    if (st != TSNNLS_OK) return st;
+    Context &c = ctx->c;
+    auto req = std::make_shared<Request>();
+    req->A = *A;
+    req->b = b;
+    req->x_out = x_out;
+    req->opts = resolve_opts(opts);
+    req->footprint = solve_footprint(*A, req->opts);
+    if (req->footprint > c.budget) return TSNNLS_EADMIT;
+    std::lock_guard<std::mutex> g(c.q_mu);
+    st = ensure_workers(ctx);
+    if (st != TSNNLS_OK) return st;
+    const tsnnls_ticket t = c.next_ticket++;
+    c.requests[t] = req;
+    c.waiting.push_back(t);
+    *ticket = t;
+    c.q_cv.notify_all();
+    return TSNNLS_OK;
+}
+
+int tsnnls_poll(tsnnls_ctx *ctx, tsnnls_ticket t, tsnnls_info *info) {
+    if (!ctx) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.q_mu);
+    auto it = c.requests.find(t);
+    if (it == c.requests.end()) return TSNNLS_EINVAL;
+    if (!it->second->done) return TSNNLS_PENDING;
+    const int st = it->second->status;
+    if (info) *info = it->second->info;
+    c.requests.erase(it);
+    return st;
+}
+
+int tsnnls_wait(tsnnls_ctx *ctx, tsnnls_ticket t, int64_t timeout_us, tsnnls_info *info) {
+    if (!ctx) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::unique_lock<std::mutex> lk(c.q_mu);
+    auto it = c.requests.find(t);
+    if (it == c.requests.end()) return TSNNLS_EINVAL;
+    auto req = it->second;
+    if (timeout_us < 0) {
+        c.done_cv.wait(lk, [&] { return req->done; });
+    } else if (!c.done_cv.wait_for(lk, std::chrono::microseconds(timeout_us),
+                                   [&] { return req->done; })) {
+        return TSNNLS_PENDING;
+    }
+    const int st = req->status;
+    if (info) *info = req->info;
+    c.requests.erase(t);
+    return st;
+}
+
+int tsnnls_profile_enable(tsnnls_ctx *ctx, int32_t enable) {
+    if (!ctx) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    c.lane0.prof = enable != 0;
+    std::memset(c.lane0.stats, 0, sizeof(c.lane0.stats));
+    return TSNNLS_OK;
+}
+
+int tsnnls_profile_read(tsnnls_ctx *ctx, tsnnls_phase_stat *out, int32_t count) {
+    if (!ctx || !out || count < 0) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    const int nc = count < TSNNLS_NUM_PHASES ? count : TSNNLS_NUM_PHASES;
+    std::memcpy(out, c.lane0.stats, sizeof(tsnnls_phase_stat) * (size_t)nc);
+    return TSNNLS_OK;
+}
+
+// ---- step-level entry points ---------------------------------------------
+
+static int finish(Lane &l, cudaError_t e) {
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(l.stream);
+        return status_from_cuda(e);
+    }
+    return status_from_cuda(cudaStreamSynchronize(l.stream));
+}
+
+int tsnnls_gram(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, int32_t precision,
+                void *G, int64_t ldg, double *c_out) {
+    if (!ctx || !A || !b || !G || !c_out || !A->on_device || A->n <= 0 || A->m <= 0 || ldg < A->n)
+        return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    cudaSetDevice(c.device);
+    Lane &l = c.lane0;
+    const int64_t m = A->m, n = A->n, nnz = A->nnz;
+    void *blk = nullptr;
+    const size_t bytes = 256 * 6 + sizeof(int64_t) * (n + 1) * 2 + (sizeof(int32_t) + sizeof(double)) * (nnz + 1) + sizeof(int32_t) * (n + 1);
+    cudaError_t e = cudaMallocAsync(&blk, bytes, l.stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    char *p = static_cast<char *>(blk);
+    auto take = [&](size_t sz) {
+        char *q = p;
+        p += round_up((int64_t)sz, 256);
+        return q;
+    };
+    int64_t *col_ptr = (int64_t *)take(sizeof(int64_t) * (n + 1));
+    int64_t *next = (int64_t *)take(sizeof(int64_t) * (n + 1));
+    int32_t *row_idx = (int32_t *)take(sizeof(int32_t) * (nnz + 1));
+    double *cval = (double *)take(sizeof(double) * (nnz + 1));
+    int32_t *cnt = (int32_t *)take(sizeof(int32_t) * (n + 1));
+    e = launch_csr_to_csc(l.stream, m, n, nnz, A->row_ptr, A->col_idx, A->val, col_ptr, row_idx,
+                          cval, cnt, next);
+    if (e == cudaSuccess) {
+        if (precision == TSNNLS_FP64)
+            e = launch_gram<double>(l.stream, m, n, A->row_ptr, A->col_idx, A->val, col_ptr,
+                                    row_idx, cval, b, (double *)G, ldg, c_out);
+        else
+            e = launch_gram<float>(l.stream, m, n, A->row_ptr, A->col_idx, A->val, col_ptr, row_idx,
+                                   cval, b, (float *)G, ldg, c_out);
+    }
+    cudaFreeAsync(blk, l.stream);
+    return finish(l, e);
+}
+
+int tsnnls_gather(tsnnls_ctx *ctx, int32_t precision, const void *G, int64_t ldg,
+                  const int32_t *F, int64_t k, void *S, int64_t lds) {
+    if (!ctx || !G || !S || k < 0 || (k > 0 && !F) || lds < k) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    cudaSetDevice(c.device);
+    cudaError_t e =
+        precision == TSNNLS_FP64
+            ? launch_gather<double>(c.lane0.stream, (const double *)G, ldg, F, nullptr, k, (double *)S, lds)
+            : launch_gather<float>(c.lane0.stream, (const float *)G, ldg, F, nullptr, k, (float *)S, lds);
+    return finish(c.lane0, e);
+}
+
+int tsnnls_cholesky(tsnnls_ctx *ctx, int32_t precision, void *S, int64_t k, int64_t lds,
+                    int32_t *info_out) {
+    if (!ctx || !S || k < 0 || lds < k) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    cudaSetDevice(c.device);
+    Lane &l = c.lane0;
+    cudaError_t e = cudaMemsetAsync(l.st_dev, 0, sizeof(DevStatus), l.stream);
+    if (e == cudaSuccess)
+        e = precision == TSNNLS_FP64 ? launch_cholesky<double>(l.stream, (double *)S, k, lds, l.st_dev)
+                                     : launch_cholesky<float>(l.stream, (float *)S, k, lds, l.st_dev);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(l.st_host, l.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, l.stream);
+    int st = finish(l, e);
+    if (st != TSNNLS_OK) return st;
+    if (info_out) *info_out = l.st_host->chol_info;
+    return l.st_host->chol_info ? TSNNLS_ENOTPD : TSNNLS_OK;
+}
+
+int tsnnls_chol_solve(tsnnls_ctx *ctx, int32_t precision, const void *L, int64_t k, int64_t lds,
+                      void *rhs) {
+    if (!ctx || !L || !rhs || k < 0 || lds < k) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    cudaSetDevice(c.device);
+    Lane &l = c.lane0;
+    int32_t *flags = nullptr;
+    cudaError_t e = cudaMallocAsync(&flags, sizeof(int32_t) * (size_t)(cdiv(k, 64) + 2), l.stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    e = cudaMemsetAsync(l.st_dev, 0, sizeof(DevStatus), l.stream);
+    if (e == cudaSuccess)
+        e = precision == TSNNLS_FP64
+                ? launch_chol_solve<double>(l.stream, (const double *)L, k, lds, (double *)rhs, flags, l.st_dev)
+                : launch_chol_solve<float>(l.stream, (const float *)L, k, lds, (float *)rhs, flags, l.st_dev);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(l.st_host, l.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, l.stream);
+    cudaFreeAsync(flags, l.stream);
+    int st = finish(l, e);
+    if (st != TSNNLS_OK) return st;
+    return l.st_host->timeout ? TSNNLS_ETIMEOUT : TSNNLS_OK;
+}
+
+int tsnnls_spmv(tsnnls_ctx *ctx, const tsnnls_csr *A, int32_t trans, double alpha,
+                const double *x, double beta, const double *z, double *out) {
+    if (!ctx || !A || !A->on_device || !x || !out || (beta != 0.0 && !z) || A->m <= 0 || A->n <= 0)
+        return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    cudaSetDevice(c.device);
+    Lane &l = c.lane0;
+    const int64_t m = A->m, n = A->n, nnz = A->nnz;
+    if (!trans) {
+        cudaError_t e = launch_spmv(l.stream, m, A->row_ptr, A->col_idx, A->val, alpha, x, beta, z,
+                                    out, (double)nnz / (double)m);
+        return finish(l, e);
+    }
+    void *blk = nullptr;
+    const size_t bytes = 256 * 6 + sizeof(int64_t) * (n + 1) * 2 + (sizeof(int32_t) + sizeof(double)) * (nnz + 1) + sizeof(int32_t) * (n + 1);
+    cudaError_t e = cudaMallocAsync(&blk, bytes, l.stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    char *p = static_cast<char *>(blk);
+    auto take = [&](size_t sz) {
+        char *q = p;
+        p += round_up((int64_t)sz, 256);
+        return q;
+    };
+    int64_t *col_ptr = (int64_t *)take(sizeof(int64_t) * (n + 1));
+    int64_t *next = (int64_t *)take(sizeof(int64_t) * (n + 1));
+    int32_t *row_idx = (int32_t *)take(sizeof(int32_t) * (nnz + 1));
+    double *cval = (double *)take(sizeof(double) * (nnz + 1));
+    int32_t *cnt = (int32_t *)take(sizeof(int32_t) * (n + 1));
+    e = launch_csr_to_csc(l.stream, m, n, nnz, A->row_ptr, A->col_idx, A->val, col_ptr, row_idx,
+                          cval, cnt, next);
+    if (e == cudaSuccess)
+        e = launch_spmv(l.stream, n, col_ptr, row_idx, cval, alpha, x, beta, z, out,
+                        (double)nnz / (double)n);
+    cudaFreeAsync(blk, l.stream);
+    return finish(l, e);
+}
+
+int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
+                             const float *const *a, const double *const *b, double *const *x_out,
+                             const tsnnls_opts *opts, int32_t *status_out, tsnnls_info *info);
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal declarations shared by the kernels and the engine of the GB300
+// block principal pivoting NNLS library.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "tsnnls.h"
+
+namespace tsnnls {
+
+// Device-resident state of one pivot loop, read by the host once per pivot
+// (and once per refinement step) through a pinned mirror.
+struct DevStatus {
+    int32_t k;          // |F|
+    int32_t n_inf;      // infeasible count of the last test
+    int64_t N;          // smallest infeasible count so far (INT64_MAX = infinity)
+    int32_t p;          // backup exchanges left
+    int32_t branch;     // 0: count dropped, 1: backup full exchange, 2: single exchange
+    int32_t done;       // 1 once (x_F, y_G) is feasible
+    int32_t iters;      // pivots performed
+    int32_t chol_info;  // 0, or 1 + column of the first non-positive pivot
+    int32_t timeout;    // 1 if a bounded device wait gave up
+    int32_t maxiter_hit;
+    int32_t pad;
+    double dnorm;       // ||dx_F||_inf of the last refinement step
+    double xnorm;       // ||x_F||_inf after it
+};
+
+constexpr int kSpinLimit = 1 << 22;  // bounded polls (with backoff) before a wait gives up
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+// Launch accounting: every launcher below calls note_launches() once per
+// kernel it starts; the engine reads the per-thread count around a solve.
+void note_launches(int n);
+int64_t launches_so_far();
+
+// ---- kernel launchers (each returns the launch error, never synchronises) --
+
+// CSR -> CSC transpose, rows ascending inside each column.
+cudaError_t launch_csr_to_csc(cudaStream_t s, int64_t m, int64_t n, int64_t nnz,
+                              const int64_t *row_ptr, const int32_t *col, const double *val,
+                              int64_t *col_ptr, int32_t *row_idx, double *cval,
+                              int32_t *work /* n+1 ints */, int64_t *scan_work /* n+1 */);
+
+// Section 3: lower triangle of G = A^T A (column-major, ld) and c = A^T b.
+template <typename T>
+cudaError_t launch_gram(cudaStream_t s, int64_t m, int64_t n, const int64_t *row_ptr,
+                        const int32_t *col, const double *val, const int64_t *col_ptr,
+                        const int32_t *row_idx, const double *cval, const double *b, T *G,
+                        int64_t ldg, double *c);
+
+// Lower triangle of S = G_FF from the lower triangle of G.
+template <typename T>
+cudaError_t launch_gather(cudaStream_t s, const T *G, int64_t ldg, const int32_t *F,
+                          const int32_t *k_dev, int64_t k_max, T *S, int64_t lds);
+
+// In-place blocked lower Cholesky of the k x k matrix S (column-major, lds).
+template <typename T>
+cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st);
+
+// rhs <- (L L^T)^{-1} rhs with the blocked warp-level triangular solves.
+// flags/ticket: scratch of at least 2*cdiv(k,64)+2 ints.
+template <typename T>
+cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs,
+                              int32_t *flags, DevStatus *st);
+
+// out = alpha * M x + beta * z over a CSR (or CSC viewed as CSR of M^T).
+cudaError_t launch_spmv(cudaStream_t s, int64_t rows, const int64_t *ptr, const int32_t *idx,
+                        const double *val, double alpha, const double *x, double beta,
+                        const double *z, double *out, double avg_nnz);
+
+// Pivot-loop glue kernels (exchange.cu).
+cudaError_t launch_init_state(cudaStream_t s, int64_t n, const double *c, double *x, double *y,
+                              uint8_t *inF, int32_t p_max, DevStatus *st);
+cudaError_t launch_exchange(cudaStream_t s, int64_t n, double *x, double *y, uint8_t *inF,
+                            int32_t *F, double zero_tol, int32_t p_max, int32_t max_iter,
+                            int32_t apply_zeroing, DevStatus *st);
+template <typename T>
+cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, const int32_t *F, int64_t k,
+                              T *out);
+template <typename T>
+cudaError_t launch_update_x(cudaStream_t s, const T *delta, const int32_t *F, int64_t k,
+                            double *x, DevStatus *st);
+cudaError_t launch_y_from_s(cudaStream_t s, int64_t n, const double *sv, const uint8_t *inF,
+                            double *y);
+
+}  // namespace tsnnls
+
+namespace tsnnls {
+
+// Validation of a device CSR matrix and right-hand side: writes a nonzero
+// code to *bad on the first problem found (1 row_ptr, 2 column index,
+// 3 ordering, 4 non-finite value).
+cudaError_t launch_validate(cudaStream_t s, int64_t m, int64_t n, int64_t nnz,
+                            const int64_t *row_ptr, const int32_t *col, const double *val,
+                            const double *b, int32_t *bad);
+
+}  // namespace tsnnls

@@ -1,0 +1,409 @@
+// The pivot loop of the block principal pivoting method (Section 2,
+// algorithm box) on one stream, on top of the cached A^T A of Section 3:
+//
+//   validate -> CSC transpose -> G = A^T A, c = A^T b -> F = {}, y = -c
+//   repeat: exchange (zeroing, infeasible count, N/p rule, new F)
+//           gather S = G_FF -> Cholesky S = L L^T
+//           x_F = (L L^T)^{-1} c_F, then FP64 iterative refinement
+//               r = b - A x, s = A^T r, x_F += (L L^T)^{-1} s_F
+//           y_G = -s_G (Eq. 5 from the last residual)
+//
+// MIXED keeps G, S, L and the triangular solves in FP32 and everything that
+// decides the exchange (x, r, s, y and the sign tests) in FP64.  FP64 runs
+// the same loop in FP64 with a single solve per pivot.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "engine.h"
+
+namespace tsnnls {
+
+int status_from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return TSNNLS_OK;
+    if (e == cudaErrorMemoryAllocation) return TSNNLS_ENOMEM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInvalidDevice || e == cudaErrorInsufficientDriver)
+        return TSNNLS_ENODEV;
+    return TSNNLS_ECUDA;
+}
+
+namespace {
+thread_local int64_t g_launches = 0;
+}
+
+void note_launches(int n) { g_launches += n; }
+int64_t launches_so_far() { return g_launches; }
+
+static cudaEvent_t pool_event(Lane &l) {
+    if (l.ev_used == l.ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        l.ev_pool.push_back(e);
+    }
+    return l.ev_pool[l.ev_used++];
+}
+
+void prof_begin(Lane &l, int phase) {
+    l.mark_launch0 = launches_so_far();
+    if (!l.prof) return;
+    PhaseMark mk{phase, pool_event(l), nullptr, 0.0, 0.0, 0};
+    if (mk.e0) cudaEventRecord(mk.e0, l.stream);
+    l.marks.push_back(mk);
+}
+
+void prof_end(Lane &l, double bytes, double flops) {
+    if (!l.prof || l.marks.empty()) return;
+    PhaseMark &mk = l.marks.back();
+    mk.e1 = pool_event(l);
+    if (mk.e1) cudaEventRecord(mk.e1, l.stream);
+    mk.bytes = bytes;
+    mk.flops = flops;
+    mk.launches = launches_so_far() - l.mark_launch0;
+}
+
+void prof_flush(Lane &l) {
+    for (const PhaseMark &mk : l.marks) {
+        float ms = 0.f;
+        if (mk.e0 && mk.e1 && cudaEventElapsedTime(&ms, mk.e0, mk.e1) == cudaSuccess) {
+            tsnnls_phase_stat &st = l.stats[mk.phase];
+            st.ms += ms;
+            st.launches += mk.launches;
+            st.bytes += mk.bytes;
+            st.flops += mk.flops;
+        }
+    }
+    l.marks.clear();
+    l.ev_used = 0;
+}
+
+int lane_create(Lane &l) {
+    cudaError_t e = cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&l.st_dev, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost(&l.st_host, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMalloc(&l.bad_dev, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&l.bad_host, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaEventCreate(&l.ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&l.ev1);
+    return status_from_cuda(e);
+}
+
+void lane_destroy(Lane &l) {
+    if (l.stream) cudaStreamSynchronize(l.stream);
+    if (l.ev0) cudaEventDestroy(l.ev0);
+    if (l.ev1) cudaEventDestroy(l.ev1);
+    for (cudaEvent_t e : l.ev_pool) cudaEventDestroy(e);
+    if (l.st_dev) cudaFree(l.st_dev);
+    if (l.st_host) cudaFreeHost(l.st_host);
+    if (l.bad_dev) cudaFree(l.bad_dev);
+    if (l.bad_host) cudaFreeHost(l.bad_host);
+    if (l.stream) cudaStreamDestroy(l.stream);
+    l = Lane{};
+}
+
+namespace {
+
+// Sub-allocator over one stream-ordered allocation.
+struct Carve {
+    char *base = nullptr;
+    size_t off = 0;
+    template <typename P>
+    P *take(size_t count) {
+        off = (size_t)round_up((int64_t)off, 256);
+        P *p = reinterpret_cast<P *>(base + off);
+        off += sizeof(P) * std::max<size_t>(count, 1);
+        return p;
+    }
+};
+
+template <typename T>
+size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
+    Carve c;
+    const int64_t ldg = round_up(n, 32);
+    if (host_in) {
+        c.take<int64_t>(m + 1);
+        c.take<int32_t>(nnz);
+        c.take<double>(nnz);
+        c.take<double>(m);
+    }
+    c.take<int64_t>(n + 1);
+    c.take<int32_t>(nnz);
+    c.take<double>(nnz);
+    c.take<int32_t>(n + 1);
+    c.take<int64_t>(n + 1);
+    c.take<T>((size_t)n * ldg);  // G
+    c.take<T>((size_t)n * ldg);  // S / L
+    for (int i = 0; i < 4; ++i) c.take<double>(n);  // c, x, y, s
+    c.take<double>(m);                              // r
+    c.take<T>(n);                                   // rhs
+    c.take<uint8_t>(n);
+    c.take<int32_t>(n);
+    c.take<int32_t>(cdiv(n, 64) + 2);
+    return c.off + 256;
+}
+
+struct Sync {
+    Lane &l;
+    cudaError_t read() {
+        cudaError_t e = cudaMemcpyAsync(l.st_host, l.st_dev, sizeof(DevStatus),
+                                        cudaMemcpyDeviceToHost, l.stream);
+        if (e != cudaSuccess) return e;
+        return cudaStreamSynchronize(l.stream);
+    }
+};
+
+#define TRY_CUDA(expr)                          \
+    do {                                        \
+        cudaError_t e_ = (expr);                \
+        if (e_ != cudaSuccess) {                \
+            status = status_from_cuda(e_);      \
+            goto cleanup;                       \
+        }                                       \
+    } while (0)
+
+template <typename T>
+int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,
+                 const tsnnls_opts &o, tsnnls_info *info, const SolveExtras *ex) {
+    (void)ctx;
+    const int64_t m = A.m, n = A.n, nnz = A.nnz;
+    const bool host_in = A.on_device == 0;
+    const bool mixed = o.precision == TSNNLS_MIXED;
+    const int64_t ldg = round_up(n, 32);
+    const int32_t max_iter = o.max_iter > 0 ? o.max_iter : (int32_t)std::min<int64_t>(10 * n + 100, INT32_MAX);
+    cudaStream_t s = lane.stream;
+    Sync sync{lane};
+    int status = TSNNLS_OK;
+    int refine_total = 0;
+    double last_rel = 0.0;
+    int64_t trace_rows = 0;
+    const int64_t launch0 = launches_so_far();
+
+    Carve cv;
+    const size_t bytes = layout_bytes<T>(m, n, nnz, host_in);
+    void *block = nullptr;
+    {
+        cudaError_t e = cudaMallocAsync(&block, bytes, s);
+        if (e != cudaSuccess) return status_from_cuda(e);
+    }
+    cv.base = static_cast<char *>(block);
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *val;
+    const double *bd;
+    if (host_in) {
+        int64_t *rp = cv.take<int64_t>(m + 1);
+        int32_t *ci = cv.take<int32_t>(nnz);
+        double *va = cv.take<double>(nnz);
+        double *bb = cv.take<double>(m);
+        TRY_CUDA(cudaMemcpyAsync(rp, A.row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, s));
+        if (nnz > 0) {
+            TRY_CUDA(cudaMemcpyAsync(ci, A.col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s));
+            TRY_CUDA(cudaMemcpyAsync(va, A.val, sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+        }
+        TRY_CUDA(cudaMemcpyAsync(bb, b, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+        row_ptr = rp;
+        col = ci;
+        val = va;
+        bd = bb;
+    } else {
+        row_ptr = A.row_ptr;
+        col = A.col_idx;
+        val = A.val;
+        bd = b;
+    }
+    {
+        int64_t *col_ptr = cv.take<int64_t>(n + 1);
+        int32_t *row_idx = cv.take<int32_t>(nnz);
+        double *cval = cv.take<double>(nnz);
+        int32_t *cnt = cv.take<int32_t>(n + 1);
+        int64_t *next = cv.take<int64_t>(n + 1);
+        T *G = cv.take<T>((size_t)n * ldg);
+        T *S = cv.take<T>((size_t)n * ldg);
+        double *c = cv.take<double>(n);
+        double *x = cv.take<double>(n);
+        double *y = cv.take<double>(n);
+        double *sv = cv.take<double>(n);
+        double *r = cv.take<double>(m);
+        T *rhs = cv.take<T>(n);
+        uint8_t *inF = cv.take<uint8_t>(n);
+        int32_t *F = cv.take<int32_t>(n);
+        int32_t *flags = cv.take<int32_t>(cdiv(n, 64) + 2);
+        const double avg_row = (double)nnz / (double)m, avg_col = (double)nnz / (double)n;
+        const double csr_bytes = 12.0 * nnz + 8.0 * (m + 1);
+        const double csc_bytes = 12.0 * nnz + 8.0 * (n + 1);
+
+        TRY_CUDA(cudaEventRecord(lane.ev0, s));
+        TRY_CUDA(cudaMemsetAsync(lane.bad_dev, 0, sizeof(int32_t), s));
+        prof_begin(lane, TSNNLS_PHASE_SETUP);
+        TRY_CUDA(launch_validate(s, m, n, nnz, row_ptr, col, val, bd, lane.bad_dev));
+        prof_end(lane, csr_bytes + 8.0 * m, 0.0);
+        TRY_CUDA(cudaMemcpyAsync(lane.bad_host, lane.bad_dev, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        if (*lane.bad_host != 0) {
+            status = TSNNLS_EINVAL;
+            goto cleanup;
+        }
+        // Section 3: transpose once, then G = A^T A and c = A^T b
+        prof_begin(lane, TSNNLS_PHASE_SETUP);
+        TRY_CUDA(launch_csr_to_csc(s, m, n, nnz, row_ptr, col, val, col_ptr, row_idx, cval, cnt,
+                                   next));
+        prof_end(lane, csr_bytes + csc_bytes, 0.0);
+        prof_begin(lane, TSNNLS_PHASE_GRAM);
+        TRY_CUDA(launch_gram<T>(s, m, n, row_ptr, col, val, col_ptr, row_idx, cval, bd, G, ldg, c));
+        prof_end(lane, csr_bytes + csc_bytes + 0.5 * (double)n * (n + 1) * sizeof(T) + 8.0 * (m + n), 0.0);
+        // F = {}, G = all, x = 0, y = -A^T b, p = p_max, N = infinity
+        prof_begin(lane, TSNNLS_PHASE_VECTOR);
+        TRY_CUDA(launch_init_state(s, n, c, x, y, inF, o.p_max, lane.st_dev));
+        prof_end(lane, 25.0 * n, 0.0);
+
+        for (;;) {
+            prof_begin(lane, TSNNLS_PHASE_EXCHANGE);
+            TRY_CUDA(launch_exchange(s, n, x, y, inF, F, o.zero_tol, o.p_max, max_iter,
+                                     lane.st_host->iters > 0 ? 1 : 0, lane.st_dev));
+            prof_end(lane, 17.0 * n + 17.0 * n + 4.0 * n, 0.0);
+            TRY_CUDA(sync.read());
+            const DevStatus st = *lane.st_host;
+            if (st.done) {
+                if (st.maxiter_hit) status = TSNNLS_EMAXITER;
+                break;
+            }
+            if (ex && ex->trace && trace_rows < ex->trace_cap) {
+                int64_t *t = ex->trace + 5 * trace_rows;
+                t[0] = st.n_inf;
+                t[1] = -1;  // filled below from the previous row
+                t[2] = st.p;
+                t[3] = st.branch;
+                t[4] = st.k;
+            }
+            const int64_t k = st.k;
+            const int64_t lds = round_up(std::max<int64_t>(k, 1), 32);
+            if (k > 0) {
+                const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
+                prof_begin(lane, TSNNLS_PHASE_GATHER);
+                TRY_CUDA(launch_gather<T>(s, G, ldg, F, nullptr, k, S, lds));
+                prof_end(lane, 2.0 * tri + 4.0 * k, 0.0);
+                prof_begin(lane, TSNNLS_PHASE_FACTOR);
+                TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev));
+                prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
+                // first solve: x_F = (L L^T)^{-1} c_F  (x restarts from 0)
+                prof_begin(lane, TSNNLS_PHASE_VECTOR);
+                TRY_CUDA(launch_gather_rhs<T>(s, c, F, k, rhs));
+                prof_end(lane, (12.0 + sizeof(T)) * k, 0.0);
+                prof_begin(lane, TSNNLS_PHASE_TRSV);
+                TRY_CUDA(launch_chol_solve<T>(s, S, k, lds, rhs, flags, lane.st_dev));
+                prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * k, 2.0 * (double)k * (double)k);
+                prof_begin(lane, TSNNLS_PHASE_VECTOR);
+                TRY_CUDA(launch_update_x<T>(s, rhs, F, k, x, lane.st_dev));
+                prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
+                TRY_CUDA(sync.read());
+                if (lane.st_host->chol_info) { status = TSNNLS_ENOTPD; break; }
+                if (lane.st_host->timeout) { status = TSNNLS_ETIMEOUT; break; }
+                ++refine_total;
+            }
+            double prev = lane.st_host->dnorm;
+            bool converged = !mixed || k == 0;
+            int steps = 1;
+            for (;;) {
+                // FP64 residual r = b - A_F x_F and s = A^T r (x_G = 0)
+                prof_begin(lane, TSNNLS_PHASE_SPMV);
+                TRY_CUDA(launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row));
+                TRY_CUDA(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col));
+                prof_end(lane, 2.0 * 12.0 * nnz + 8.0 * (m + 1) + 8.0 * (n + 1) + 8.0 * (3.0 * m + 2.0 * n),
+                         4.0 * nnz);
+                if (converged) break;
+                const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
+                prof_begin(lane, TSNNLS_PHASE_VECTOR);
+                TRY_CUDA(launch_gather_rhs<T>(s, sv, F, k, rhs));
+                prof_end(lane, (12.0 + sizeof(T)) * k, 0.0);
+                prof_begin(lane, TSNNLS_PHASE_TRSV);
+                TRY_CUDA(launch_chol_solve<T>(s, S, k, lds, rhs, flags, lane.st_dev));
+                prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * k, 2.0 * (double)k * (double)k);
+                prof_begin(lane, TSNNLS_PHASE_VECTOR);
+                TRY_CUDA(launch_update_x<T>(s, rhs, F, k, x, lane.st_dev));
+                prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
+                TRY_CUDA(sync.read());
+                if (lane.st_host->timeout) { status = TSNNLS_ETIMEOUT; goto cleanup; }
+                ++steps;
+                ++refine_total;
+                const double d = lane.st_host->dnorm, xn = lane.st_host->xnorm;
+                last_rel = xn > 0 ? d / xn : 0.0;
+                if (d <= o.rel_tol * xn) {
+                    converged = true;  // one more pass computes r, s for this x
+                } else if (d > 0.5 * prev && d <= 1e-9 * xn) {
+                    converged = true;  // at the rounding floor, already below the target
+                } else if (steps >= o.max_refine || (steps > 4 && d > prev)) {
+                    if (d <= 1e-9 * xn) {
+                        converged = true;
+                    } else {
+                        status = TSNNLS_ENOCONV;
+                        goto cleanup;
+                    }
+                }
+                prev = d;
+            }
+            // Eq. 5: y_G = A_G^T (A_F x_F - b) = -s_G
+            prof_begin(lane, TSNNLS_PHASE_VECTOR);
+            TRY_CUDA(launch_y_from_s(s, n, sv, inF, y));
+            prof_end(lane, 17.0 * n, 0.0);
+            ++trace_rows;
+        }
+        if (status == TSNNLS_OK) {
+            TRY_CUDA(cudaEventRecord(lane.ev1, s));
+            const cudaMemcpyKind kind = host_in ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+            TRY_CUDA(cudaMemcpyAsync(x_out, x, sizeof(double) * n, kind, s));
+            if (ex && ex->y_out) TRY_CUDA(cudaMemcpyAsync(ex->y_out, y, sizeof(double) * n, kind, s));
+            if (ex && ex->inF_out)
+                TRY_CUDA(cudaMemcpyAsync(ex->inF_out, inF, (size_t)n, kind, s));
+            TRY_CUDA(cudaStreamSynchronize(s));
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, lane.ev0, lane.ev1) == cudaSuccess && info) info->time_ms = ms;
+        }
+        if (info) {
+            info->iters = lane.st_host->iters;
+            info->nF = lane.st_host->k;
+        }
+    }
+cleanup:
+    cudaFreeAsync(block, s);
+    cudaStreamSynchronize(s);
+    prof_flush(lane);
+    if (ex && ex->trace) {
+        // column 1: N before the branch = smallest count over the earlier pivots
+        int64_t best = INT64_MAX;
+        for (int64_t i = 0; i < std::min(trace_rows, ex->trace_cap); ++i) {
+            ex->trace[5 * i + 1] = best;
+            best = std::min(best, ex->trace[5 * i]);
+        }
+    }
+    if (info) {
+        info->status = status;
+        info->refine_steps = refine_total;
+        info->last_rel_step = last_rel;
+        info->path_used = TSNNLS_PATH_FACTOR;
+        info->precision_used = o.precision;
+        info->kernel_launches = launches_so_far() - launch0;
+    }
+    return status;
+}
+
+}  // namespace
+
+size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o) {
+    const bool host_in = A.on_device == 0;
+    return o.precision == TSNNLS_FP64 ? layout_bytes<double>(A.m, A.n, A.nnz, host_in)
+                                      : layout_bytes<float>(A.m, A.n, A.nnz, host_in);
+}
+
+int solve_on_lane(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,
+                  const tsnnls_opts &o, tsnnls_info *info, const SolveExtras *extras) {
+    if (info) std::memset(info, 0, sizeof(*info));
+    std::memset(lane.st_host, 0, sizeof(DevStatus));
+    if (o.precision == TSNNLS_FP64)
+        return solve_factor<double>(ctx, lane, A, b, x_out, o, info, extras);
+    return solve_factor<float>(ctx, lane, A, b, x_out, o, info, extras);
+}
+
+}  // namespace tsnnls

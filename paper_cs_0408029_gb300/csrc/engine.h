@@ -1,0 +1,104 @@
+// Host-side solver engine: owns device memory for one solve and runs the
+// block principal pivoting loop of Section 2 on one CUDA stream.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "tsnnls.h"
+
+namespace tsnnls {
+
+// One stream with its own status block; the blocking API uses lane 0, the
+// asynchronous queue one lane per admitted request.
+struct PhaseMark {
+    int phase;
+    cudaEvent_t e0, e1;
+    double bytes, flops;
+    int64_t launches;
+};
+
+struct Lane {
+    cudaStream_t stream = nullptr;
+    DevStatus *st_dev = nullptr;
+    DevStatus *st_host = nullptr;  // pinned mirror
+    int32_t *bad_dev = nullptr;
+    int32_t *bad_host = nullptr;   // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // per-phase accounting (tsnnls_profile_*)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<PhaseMark> marks;
+    int64_t mark_launch0 = 0;
+    tsnnls_phase_stat stats[TSNNLS_NUM_PHASES] = {};
+};
+
+// Bracket a phase with events on the lane's stream (no-ops unless prof).
+void prof_begin(Lane &l, int phase);
+void prof_end(Lane &l, double bytes, double flops);
+// After the lane's stream is idle: fold the marks into l.stats.
+void prof_flush(Lane &l);
+
+struct Request {
+    tsnnls_csr A;
+    const double *b = nullptr;
+    double *x_out = nullptr;
+    tsnnls_opts opts;
+    size_t footprint = 0;
+    int status = TSNNLS_PENDING;
+    tsnnls_info info{};
+    bool done = false;
+};
+
+// Extra outputs of a solve (for tests and tools); any pointer may be NULL.
+struct SolveExtras {
+    double *y_out = nullptr;       // n entries, same memory space as x_out
+    uint8_t *inF_out = nullptr;    // n entries, same memory space as x_out
+    int64_t *trace = nullptr;      // host, 5 per pivot
+    int64_t trace_cap = 0;
+};
+
+struct Context {
+    int device = 0;
+    size_t budget = 0;
+    size_t in_use = 0;  // bytes held by admitted requests
+    Lane lane0;
+    std::mutex solve_mu;  // serialises blocking calls on lane0
+
+    // asynchronous queue (continuous batching across lanes)
+    std::mutex q_mu;
+    std::condition_variable q_cv, done_cv;
+    std::deque<tsnnls_ticket> waiting;
+    std::map<tsnnls_ticket, std::shared_ptr<Request>> requests;
+    tsnnls_ticket next_ticket = 1;
+    std::vector<std::thread> workers;
+    std::vector<Lane> lanes;
+    bool stopping = false;
+    int active = 0;
+};
+
+int lane_create(Lane &l);
+void lane_destroy(Lane &l);
+
+// Device footprint (bytes) of one factor-path solve at this size.
+size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o);
+
+// Run one solve on a lane.  Thread-compatible: one caller per lane at a time.
+int solve_on_lane(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
+                  double *x_out, const tsnnls_opts &opts, tsnnls_info *info,
+                  const SolveExtras *extras);
+
+int status_from_cuda(cudaError_t e);
+
+}  // namespace tsnnls

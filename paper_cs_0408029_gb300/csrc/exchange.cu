@@ -1,0 +1,290 @@
+// The exchange step of the block principal pivoting loop (Section 2,
+// algorithm box) and the small vector kernels around the solve.
+//
+// The exchange runs in one CTA: it applies the 1e-12 zeroing, counts the
+// infeasible variables (negative entries of x_F and y_G), runs the N / p
+// state machine, flips the F/G flags, and rebuilds the ascending F list with
+// a block-wide prefix sum.  Integer work only after the sign tests, so its
+// decisions are exact.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tsnnls {
+
+constexpr int kExThreads = 1024;
+
+__global__ void init_state_kernel(int64_t n, const double *__restrict__ c, double *__restrict__ x,
+                                  double *__restrict__ y, uint8_t *__restrict__ inF, int32_t p_max,
+                                  DevStatus *st) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        x[j] = 0.0;
+        y[j] = -c[j];  // y = -A^T b, as printed (no zeroing of the initial y)
+        inF[j] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->k = 0;
+        st->n_inf = -1;
+        st->N = INT64_MAX;
+        st->p = p_max;
+        st->branch = -1;
+        st->done = 0;
+        st->iters = 0;
+        st->chol_info = 0;
+        st->timeout = 0;
+        st->maxiter_hit = 0;
+        st->dnorm = 0.0;
+        st->xnorm = 0.0;
+    }
+}
+
+cudaError_t launch_init_state(cudaStream_t s, int64_t n, const double *c, double *x, double *y,
+                              uint8_t *inF, int32_t p_max, DevStatus *st) {
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 8));
+    init_state_kernel<<<g, 256, 0, s>>>(n, c, x, y, inF, p_max, st);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// Block-wide sum / max helpers for 1024 threads.
+__device__ __forceinline__ int64_t block_sum_i64(int64_t v, int64_t *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = sh[lane];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+__device__ __forceinline__ int64_t block_max_i64(int64_t v, int64_t *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = sh[lane];
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+__device__ __forceinline__ bool infeasible(uint8_t f, double xv, double yv) {
+    return f ? (xv < 0.0) : (yv < 0.0);
+}
+
+__global__ void __launch_bounds__(kExThreads)
+    exchange_kernel(int64_t n, double *__restrict__ x, double *__restrict__ y,
+                    uint8_t *__restrict__ inF, int32_t *__restrict__ F, double zero_tol,
+                    int32_t p_max, int32_t max_iter, int32_t apply_zeroing, DevStatus *st) {
+    __shared__ int64_t sh[32];
+    __shared__ int32_t decision;  // -1: stop, 0/1: full exchange, 2: single
+    __shared__ int64_t carry;
+    const int tid = threadIdx.x;
+
+    // zeroing of near-zero entries of x_F and y_G (Section 2); x_G = y_F = 0
+    int64_t cnt = 0, largest = -1;
+    for (int64_t j = tid; j < n; j += kExThreads) {
+        const uint8_t f = inF[j];
+        double xv = x[j], yv = y[j];
+        if (apply_zeroing) {
+            if (f) {
+                if (fabs(xv) < zero_tol) xv = 0.0;
+                yv = 0.0;
+            } else {
+                xv = 0.0;
+                if (fabs(yv) < zero_tol) yv = 0.0;
+            }
+            x[j] = xv;
+            y[j] = yv;
+        }
+        if (infeasible(f, xv, yv)) {
+            ++cnt;
+            largest = j;
+        }
+    }
+    const int64_t n_inf = block_sum_i64(cnt, sh);
+    const int64_t big = block_max_i64(largest, sh);
+
+    if (tid == 0) {
+        st->n_inf = (int32_t)n_inf;
+        int32_t d;
+        if (n_inf == 0) {
+            st->done = 1;
+            d = -1;
+        } else if (st->iters >= max_iter) {
+            st->maxiter_hit = 1;
+            st->done = 1;
+            d = -1;
+        } else if (n_inf < st->N) {
+            st->N = n_inf;
+            st->p = p_max;
+            d = 0;
+        } else if (st->p > 0) {
+            st->p -= 1;
+            d = 1;
+        } else {
+            d = 2;
+        }
+        st->branch = d;
+        decision = d;
+    }
+    __syncthreads();
+    const int32_t d = decision;
+    if (d < 0) return;
+
+    // exchange between F and G
+    if (d == 2) {
+        if (tid == 0) inF[big] ^= 1;
+    } else {
+        for (int64_t j = tid; j < n; j += kExThreads)
+            if (infeasible(inF[j], x[j], y[j])) inF[j] ^= 1;
+    }
+    __syncthreads();
+
+    // ascending F list by prefix sum; x restarts from 0 for the new solve
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int64_t base = 0; base < n; base += kExThreads) {
+        const int64_t j = base + tid;
+        const int v = (j < n) ? (int)inF[j] : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, v);
+        const int before_in_warp = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) sh[warp] = __popc(bal);
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = sh[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            sh[lane] = w;  // inclusive warp prefix
+        }
+        __syncthreads();
+        const int64_t pos = carry + (warp > 0 ? sh[warp - 1] : 0) + before_in_warp;
+        if (v) F[pos] = (int32_t)j;
+        if (j < n) x[j] = 0.0;
+        __syncthreads();
+        if (tid == 0) carry += sh[31];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        st->k = (int32_t)carry;
+        st->iters += 1;
+    }
+}
+
+cudaError_t launch_exchange(cudaStream_t s, int64_t n, double *x, double *y, uint8_t *inF,
+                            int32_t *F, double zero_tol, int32_t p_max, int32_t max_iter,
+                            int32_t apply_zeroing, DevStatus *st) {
+    exchange_kernel<<<1, kExThreads, 0, s>>>(n, x, y, inF, F, zero_tol, p_max, max_iter,
+                                             apply_zeroing, st);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void gather_rhs_kernel(const double *__restrict__ v, const int32_t *__restrict__ F,
+                                  int64_t k, T *__restrict__ out) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < k;
+         a += (int64_t)gridDim.x * blockDim.x)
+        out[a] = (T)v[F[a]];
+}
+
+template <typename T>
+cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, const int32_t *F, int64_t k,
+                              T *out) {
+    if (k <= 0) return cudaSuccess;
+    const int g = (int)std::min<int64_t>(cdiv(k, 256), 152 * 8);
+    gather_rhs_kernel<T><<<g, 256, 0, s>>>(v, F, k, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gather_rhs<float>(cudaStream_t, const double *, const int32_t *,
+                                              int64_t, float *);
+template cudaError_t launch_gather_rhs<double>(cudaStream_t, const double *, const int32_t *,
+                                               int64_t, double *);
+
+// x_F += delta (FP64), and ||delta||_inf, ||x_F||_inf into the status.
+template <typename T>
+__global__ void __launch_bounds__(kExThreads)
+    update_x_kernel(const T *__restrict__ delta, const int32_t *__restrict__ F, int64_t k,
+                    double *__restrict__ x, DevStatus *st) {
+    __shared__ double shd[32], shx[32];
+    double dm = 0.0, xm = 0.0;
+    for (int64_t a = threadIdx.x; a < k; a += kExThreads) {
+        const double d = (double)delta[a];
+        const int32_t j = F[a];
+        const double xn = x[j] + d;
+        x[j] = xn;
+        dm = fmax(dm, fabs(d));
+        xm = fmax(xm, fabs(xn));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+    }
+    if (lane == 0) {
+        shd[warp] = dm;
+        shx[warp] = xm;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        dm = shd[lane];
+        xm = shx[lane];
+        for (int o = 16; o > 0; o >>= 1) {
+            dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+            xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+        }
+        if (lane == 0) {
+            st->dnorm = dm;
+            st->xnorm = xm;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_update_x(cudaStream_t s, const T *delta, const int32_t *F, int64_t k,
+                            double *x, DevStatus *st) {
+    update_x_kernel<T><<<1, kExThreads, 0, s>>>(delta, F, k, x, st);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_update_x<float>(cudaStream_t, const float *, const int32_t *,
+                                            int64_t, double *, DevStatus *);
+template cudaError_t launch_update_x<double>(cudaStream_t, const double *, const int32_t *,
+                                             int64_t, double *, DevStatus *);
+
+// Eq. 5 from s = A^T (b - A x): y_G = -s_G, y_F = 0.
+__global__ void y_from_s_kernel(int64_t n, const double *__restrict__ sv,
+                                const uint8_t *__restrict__ inF, double *__restrict__ y) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        y[j] = inF[j] ? 0.0 : -sv[j];
+}
+
+cudaError_t launch_y_from_s(cudaStream_t s, int64_t n, const double *sv, const uint8_t *inF,
+                            double *y) {
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 8));
+    y_from_s_kernel<<<g, 256, 0, s>>>(n, sv, inF, y);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace tsnnls

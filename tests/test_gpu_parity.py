@@ -1,0 +1,259 @@
+"""Parity of the CUDA path with the CPU oracle (GPU).
+
+Every call goes through the C ABI (ctypes binding).  Step-level calls are
+compared element by element with the oracle's own routines; full solves are
+compared on x (relative error), on the F/G split outside the degenerate band
+1e-10 ||A^T b||, on the KKT certificate of Eq. 3, and on the pivot trace.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import kkt
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-9        # ||x - x*|| / ||x*|| against the FP64 oracle
+KKT_FACTOR = 1e-10    # KKT violation <= 1e-10 ||A^T b||
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ts(torch_cuda):
+    import paper_cs_0408029_gb300 as mod
+
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(ts):
+    c = ts.Context(0)
+    yield c
+    c.close()
+
+
+def _check_solution(prob, ref, x, inF=None):
+    err = np.linalg.norm(x - ref.x) / max(np.linalg.norm(ref.x), 1e-300)
+    assert err <= REL_TOL, err
+    assert kkt.violation(prob, x) <= KKT_FACTOR * kkt.atb_norm(prob)
+    if inF is not None:
+        band = 1e-10 * kkt.atb_norm(prob)
+        y = kkt.dual(prob, ref.x)
+        clear = (np.abs(ref.x) > band) | (np.abs(y) > band)
+        assert np.array_equal(inF[clear], ref.inF[clear])
+    return err
+
+
+# ---------------------------------------------------------------------------
+# step level
+
+
+@pytest.mark.parametrize("m,n,density", [(300, 200, 0.05), (1500, 1100, 0.01), (70, 33, 0.3)])
+def test_gram_bit_exact(ts, ctx, torch_cuda, oracle_mod, m, n, density):
+    """A^T A and A^T b: same products summed in the same (ascending row)
+    order as the oracle's column dot products, so FP64 results are equal bit
+    for bit, and the FP32 copy is the rounding of that value."""
+    torch = torch_cuda
+    p = workloads.random_sparse(m, n, density, seed=m + n)
+    A = ts.DeviceCSR.from_problem(p)
+    b = torch.as_tensor(p.b, device="cuda")
+    g_ref = oracle_mod.gram(p)
+    c_ref = oracle_mod.atb(p)
+    G, ldg, c = ts.Context.gram(ctx, A, b, precision=ts.FP64)
+    Gh = G.cpu().numpy()[:, :n].T  # Gh[i, j] = G(i, j)
+    lower = np.tril(np.ones((n, n), dtype=bool))
+    assert np.array_equal(Gh[lower], g_ref[lower])
+    assert np.array_equal(c.cpu().numpy(), c_ref)
+    G32, _, _ = ctx.gram(A, b, precision=ts.MIXED)
+    assert np.array_equal(G32.cpu().numpy()[:, :n].T[lower], g_ref.astype(np.float32)[lower])
+
+
+def test_gather_exact(ts, ctx, torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(3)
+    n = 300
+    g = rng.standard_normal((n, n))
+    ldg = 320
+    G = torch.zeros((n, ldg), dtype=torch.float64, device="cuda")
+    G[:, :n] = torch.as_tensor(g.T, device="cuda")  # column j of g in row j
+    F = np.sort(rng.choice(n, 137, replace=False)).astype(np.int32)
+    S = ctx.gather(G, ldg, torch.as_tensor(F, device="cuda"), precision=ts.FP64)
+    got = S.cpu().numpy().T  # got[a, b] = S(a, b)
+    want = g[np.ix_(F, F)]
+    lower = np.tril(np.ones((137, 137), dtype=bool))
+    assert np.array_equal(got[lower], want[lower])
+
+
+@pytest.mark.parametrize("k", [1, 31, 32, 33, 63, 64, 65, 130, 257, 700])
+def test_cholesky_and_solve(ts, ctx, torch_cuda, oracle_mod, k):
+    torch = torch_cuda
+    rng = np.random.default_rng(k)
+    a = rng.standard_normal((k + 40, k))
+    s = a.T @ a
+    L_ref = oracle_mod.cholesky(s)
+    rhs = rng.standard_normal(k)
+    x_ref = oracle_mod.cholesky_solve(L_ref, rhs)
+    lower = np.tril(np.ones((k, k), dtype=bool))
+    for prec, dt, tol_l, tol_x in ((ts.FP64, torch.float64, 1e-11, 1e-9),
+                                   (ts.MIXED, torch.float32, 2e-3, 5e-2)):
+        S = torch.as_tensor(s.T.copy(), dtype=dt, device="cuda")  # column-major, lds = k
+        st, info = ctx.cholesky(S, k, k, precision=prec)
+        assert st == ts.OK and info == 0
+        L = S.cpu().numpy().astype(np.float64).T
+        scale = np.abs(L_ref).max()
+        assert np.abs(L[lower] - L_ref[lower]).max() <= tol_l * scale
+        r = torch.as_tensor(rhs, dtype=dt, device="cuda")
+        ctx.chol_solve(S, k, k, r, precision=prec)
+        x = r.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(x - x_ref) <= tol_x * np.linalg.norm(x_ref)
+
+
+def test_cholesky_reports_not_pd(ts, ctx, torch_cuda):
+    torch = torch_cuda
+    s = np.eye(80)
+    s[50, 50] = -1.0
+    S = torch.as_tensor(s, device="cuda")
+    st, info = ctx.cholesky(S, 80, 80, precision=ts.FP64)
+    assert st == ts.ENOTPD and info == 51
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+def test_spmv(ts, ctx, torch_cuda, trans):
+    torch = torch_cuda
+    p = workloads.random_sparse(500, 300, 0.03, seed=11)
+    A = ts.DeviceCSR.from_problem(p)
+    a = p.dense()
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(500 if trans else 300)
+    z = rng.standard_normal(300 if trans else 500)
+    out = ctx.spmv(A, trans, -1.5, torch.as_tensor(x, device="cuda"), 0.5,
+                   torch.as_tensor(z, device="cuda")).cpu().numpy()
+    want = -1.5 * ((a.T if trans else a) @ x) + 0.5 * z
+    np.testing.assert_allclose(out, want, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# whole solves
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_plain_single_600x400(ts, ctx, oracle_mod, precision):
+    p = workloads.plain_single()
+    ref = oracle_mod.bpp_solve(p)
+    x, y, inF, trace, info = ctx.solve_ex(ts.HostCSR.from_problem(p), p.b, precision=precision)
+    _check_solution(p, ref, x, inF)
+    # the pivot path (integer decisions of the exchange rule) matches the oracle
+    assert np.array_equal(trace, ref.trace)
+    assert info.iters == ref.iters
+
+
+@pytest.mark.parametrize("m,n,density,seed", [(1500, 1000, 0.02, 1), (900, 700, 0.05, 2),
+                                              (2600, 1300, 0.004, 3), (130, 97, 0.2, 4)])
+def test_random_sparse_tiles_and_tails(ts, ctx, oracle_mod, m, n, density, seed):
+    """Sizes that span several factor / solve tiles and a ragged tail."""
+    p = workloads.random_sparse(m, n, density, seed=seed, zero_frac=0.4, noise=0.05)
+    ref = oracle_mod.bpp_solve(p)
+    for precision in ("mixed", "fp64"):
+        x, y, inF, trace, info = ctx.solve_ex(ts.HostCSR.from_problem(p), p.b, precision=precision)
+        _check_solution(p, ref, x, inF)
+        assert np.array_equal(trace, ref.trace), precision
+
+
+def test_device_input_matches_host_input(ts, ctx, torch_cuda):
+    torch = torch_cuda
+    p = workloads.random_sparse(800, 500, 0.02, seed=9)
+    xh, _ = ctx.solve(ts.HostCSR.from_problem(p), p.b)
+    xd, _ = ctx.solve(ts.DeviceCSR.from_problem(p), torch.as_tensor(p.b, device="cuda"))
+    assert np.array_equal(xh, xd.cpu().numpy())
+
+
+def test_solve_is_deterministic(ts, ctx):
+    p = workloads.random_sparse(800, 500, 0.02, seed=10)
+    A = ts.HostCSR.from_problem(p)
+    x1, _ = ctx.solve(A, p.b)
+    x2, _ = ctx.solve(A, p.b)
+    assert np.array_equal(x1, x2)
+
+
+# ---------------------------------------------------------------------------
+# degenerate and special cases
+
+
+def test_nonpositive_atb_zero_iterations(ts, ctx):
+    rng = np.random.default_rng(40)
+    a = np.abs(rng.standard_normal((20, 6)))
+    b = -np.abs(rng.standard_normal(20))
+    p = workloads.dense_to_csr(a, b)
+    x, y, inF, trace, info = ctx.solve_ex(ts.HostCSR.from_problem(p), p.b)
+    assert info.iters == 0 and np.all(x == 0) and not inF.any()
+    np.testing.assert_allclose(y, -(a.T @ b), rtol=1e-14)
+
+
+def test_single_column(ts, ctx):
+    rng = np.random.default_rng(43)
+    a = rng.standard_normal((7, 1))
+    b = a[:, 0] * 2.5 + 0.1 * rng.standard_normal(7)
+    p = workloads.dense_to_csr(a, b)
+    x, _ = ctx.solve(ts.HostCSR.from_problem(p), p.b, precision="fp64")
+    np.testing.assert_allclose(x, [float(a[:, 0] @ b) / float(a[:, 0] @ a[:, 0])], rtol=1e-13)
+
+
+def test_orthogonal_columns(ts, ctx):
+    rng = np.random.default_rng(42)
+    q, _ = np.linalg.qr(rng.standard_normal((30, 10)))
+    a = q * rng.uniform(0.5, 3.0, 10)
+    b = rng.standard_normal(30)
+    p = workloads.dense_to_csr(a, b)
+    expect = np.maximum(0.0, a.T @ b) / np.sum(a * a, axis=0)
+    x, _ = ctx.solve(ts.HostCSR.from_problem(p), p.b)
+    np.testing.assert_allclose(x, expect, rtol=1e-10, atol=1e-13)
+
+
+def test_empty_rows_and_degenerate(ts, ctx, oracle_mod):
+    prob, xs, ys = workloads.conditioned_dense(50, 30, 5.0, seed=45, zero_frac=0.5,
+                                               active_frac=0.4)
+    a = np.vstack([prob.a, np.zeros((5, 30))])  # empty rows
+    b = np.concatenate([prob.b, np.zeros(5)])
+    p = workloads.dense_to_csr(a, b)
+    x, _ = ctx.solve(ts.HostCSR.from_problem(p), p.b)
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-10)
+
+
+def test_invalid_inputs(ts, ctx):
+    p = workloads.random_sparse(40, 20, 0.2, seed=3)
+    A = ts.HostCSR.from_problem(p)
+    bad = ts.HostCSR(p.m, p.n, p.row_ptr, p.col_idx.copy(), p.val)
+    r0, r1 = int(p.row_ptr[0]), int(p.row_ptr[1])
+    assert r1 - r0 >= 2
+    bad.col_idx[r0], bad.col_idx[r0 + 1] = bad.col_idx[r0 + 1], bad.col_idx[r0]  # unsorted
+    _, info = ctx.solve(bad, p.b, raise_on_error=False)
+    assert info.status == ts.EINVAL
+    oob = ts.HostCSR(p.m, p.n, p.row_ptr, p.col_idx.copy(), p.val)
+    oob.col_idx[-1] = p.n  # out of range
+    _, info = ctx.solve(oob, p.b, raise_on_error=False)
+    assert info.status == ts.EINVAL
+    sq = ts.HostCSR(20, 20, p.row_ptr[:21], p.col_idx, p.val)  # m == n
+    _, info = ctx.solve(sq, p.b[:20], raise_on_error=False)
+    assert info.status == ts.EINVAL
+    nan_b = p.b.copy()
+    nan_b[3] = np.nan
+    _, info = ctx.solve(A, nan_b, raise_on_error=False)
+    assert info.status == ts.EINVAL
+    # the context stays usable
+    x, _ = ctx.solve(A, p.b)
+    assert np.isfinite(x).all()
+
+
+def test_admission_budget(ts):
+    p = workloads.random_sparse(300, 200, 0.05, seed=7)
+    with ts.Context(0, hbm_budget=1 << 16) as small:
+        _, info = small.solve(ts.HostCSR.from_problem(p), p.b, raise_on_error=False)
+        assert info.status == ts.EADMIT
