@@ -235,6 +235,35 @@ int tsnnls_cholesky(tsnnls_ctx *ctx, int32_t precision, void *S, int64_t k, int6
 int tsnnls_chol_solve(tsnnls_ctx *ctx, int32_t precision, const void *L, int64_t k, int64_t lds,
                       void *rhs);
 
+/* Allocation-free variant of tsnnls_chol_solve.  The paper has no
+ * counterpart: this is a library-integration convenience.
+ *
+ * Some callers may not allocate device memory at all: applications whose
+ * own pool already reserves the device memory they are allowed to use, and
+ * latency-critical host threads that cannot afford cudaMalloc/cudaFree,
+ * which may synchronise the whole device and can fail at run time.  This
+ * call needs no context and allocates nothing: the caller passes the factor
+ * L and the right-hand side (device memory, as for tsnnls_chol_solve), and
+ * the solve's scratch (block flags, a ticket counter, a status word) lives
+ * in one fixed array in the library's static device memory, about 4 KB that
+ * every GPU which loads the library keeps until the process exits.
+ *
+ *   precision  TSNNLS_MIXED (float L, rhs) or TSNNLS_FP64 (double)
+ *   k, lds     order of L and its leading dimension; k may be at most
+ *              TSNNLS_NOALLOC_MAX_K, larger k returns TSNNLS_EINVAL
+ *   stream     the cudaStream_t to run on (NULL: the default stream); the
+ *              call returns after the work on it has finished
+ *
+ * Runs on the current CUDA device.  The first call on each device looks up
+ * the device address of the static array (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (other host threads, other streams) race on it and
+ * must be serialised by the caller.  Returns TSNNLS_ETIMEOUT if a bounded
+ * wait inside the solve gave up. */
+#define TSNNLS_NOALLOC_MAX_K 65536
+int tsnnls_chol_solve_noalloc(int32_t precision, const void *L, int64_t k, int64_t lds,
+                              void *rhs, void *stream);
+
 /* Sparse products in FP64 on a device CSR matrix:
  *   trans == 0:  out = alpha * A x + beta * z   (x: n entries, out, z: m)
  *   trans == 1:  out = alpha * A^T x + beta * z (x: m entries, out, z: n)

@@ -25,6 +25,7 @@ EXPORTS = (
     "tsnnls_solve", "tsnnls_solve_ex", "tsnnls_submit", "tsnnls_poll", "tsnnls_wait",
     "tsnnls_solve_batch_dense", "tsnnls_gram", "tsnnls_gather", "tsnnls_cholesky",
     "tsnnls_chol_solve", "tsnnls_spmv", "tsnnls_profile_enable", "tsnnls_profile_read",
+    "tsnnls_chol_solve_noalloc",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr")
@@ -101,6 +102,7 @@ def load(build_if_missing: bool = True):
         "tsnnls_spmv": ([p, ctypes.POINTER(CSR), i32, d, p, d, p, p], ctypes.c_int),
         "tsnnls_profile_enable": ([p, i32], ctypes.c_int),
         "tsnnls_profile_read": ([p, p, i32], ctypes.c_int),
+        "tsnnls_chol_solve_noalloc": ([i32, p, i64, i64, p, p], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -132,6 +134,13 @@ def default_opts(**kw) -> Opts:
             v = {"auto": PATH_AUTO, "factor": PATH_FACTOR, "lsqr": PATH_LSQR}[v]
         setattr(o, k, v)
     return o
+
+
+def chol_solve_noalloc(L, k, lds, rhs, precision=MIXED, stream=None):
+    """Context-free, allocation-free factor solve on device tensors (in place
+    on rhs) using the library's static scratch; returns the status code."""
+    sp = ctypes.c_void_p(stream) if stream else ctypes.c_void_p(0)
+    return load().tsnnls_chol_solve_noalloc(precision, _dev_ptr(L), int(k), int(lds), _dev_ptr(rhs), sp)
 
 
 def _np_ptr(a):

@@ -1,0 +1,85 @@
+// Allocation-free variant of the factor solve (tsnnls_chol_solve_noalloc).
+//
+// The blocked triangular solves need a little global scratch: one "block
+// done" flag per 64-row block, a ticket counter and an abort flag, plus a
+// status word that records a timed-out wait.  tsnnls_chol_solve takes that
+// scratch from its context, which allocates device memory.  This variant
+// keeps it in a file-scope __device__ array instead, so a caller that must
+// not allocate device memory can still run the solve on its own buffers.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace tsnnls {
+namespace {
+
+// Largest k accepted: 65536 rows, i.e. 1024 blocks of 64 rows.
+constexpr int64_t kNoAllocMaxK = TSNNLS_NOALLOC_MAX_K;
+constexpr int64_t kNoAllocBlocks = kNoAllocMaxK / 64;
+// flags[0..blocks) + ticket + abort, rounded up, then one DevStatus.
+constexpr size_t kFlagBytes = sizeof(int32_t) * (size_t)((kNoAllocBlocks + 2 + 63) / 64 * 64);
+constexpr size_t kScratchBytes = kFlagBytes + sizeof(DevStatus);
+
+// Shared by every call on a device; it keeps the last call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the symbol names a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, once per device, with that device current.
+int scratch_for_current_device(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e == cudaErrorNoDevice ? TSNNLS_ENODEV : TSNNLS_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return TSNNLS_ENODEV;
+    std::lock_guard<std::mutex> g(g_setup_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return TSNNLS_ECUDA;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return TSNNLS_OK;
+}
+
+}  // namespace
+}  // namespace tsnnls
+
+using namespace tsnnls;
+
+extern "C" int tsnnls_chol_solve_noalloc(int32_t precision, const void *L, int64_t k, int64_t lds,
+                                         void *rhs, void *stream) {
+    if (!L || !rhs || k < 0 || lds < k) return TSNNLS_EINVAL;
+    if (k > kNoAllocMaxK) return TSNNLS_EINVAL;
+    if (precision != TSNNLS_MIXED && precision != TSNNLS_FP64) return TSNNLS_EINVAL;
+    if (k == 0) return TSNNLS_OK;
+    void *base = nullptr;
+    int st = scratch_for_current_device(&base);
+    if (st != TSNNLS_OK) return st;
+    int32_t *flags = static_cast<int32_t *>(base);
+    DevStatus *status = reinterpret_cast<DevStatus *>(static_cast<char *>(base) + kFlagBytes);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The flags are cleared by the solve launcher itself; the status word
+    // still holds the previous call's result and must start at zero.
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess)
+        e = precision == TSNNLS_FP64
+                ? launch_chol_solve<double>(s, static_cast<const double *>(L), k, lds,
+                                            static_cast<double *>(rhs), flags, status)
+                : launch_chol_solve<float>(s, static_cast<const float *>(L), k, lds,
+                                           static_cast<float *>(rhs), flags, status);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    int32_t timed_out = 0;
+    e = cudaMemcpy(&timed_out, &status->timeout, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    return timed_out ? TSNNLS_ETIMEOUT : TSNNLS_OK;
+}
