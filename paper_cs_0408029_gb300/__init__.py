@@ -25,7 +25,7 @@ EXPORTS = (
     "tsnnls_solve", "tsnnls_solve_ex", "tsnnls_submit", "tsnnls_poll", "tsnnls_wait",
     "tsnnls_solve_batch_dense", "tsnnls_gram", "tsnnls_gather", "tsnnls_cholesky",
     "tsnnls_chol_solve", "tsnnls_spmv", "tsnnls_profile_enable", "tsnnls_profile_read",
-    "tsnnls_chol_solve_noalloc",
+    "tsnnls_chol_solve_noalloc", "tsnnls_batch_autotune", "tsnnls_batch_set_panel",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr")
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True):
         "tsnnls_profile_enable": ([p, i32], ctypes.c_int),
         "tsnnls_profile_read": ([p, p, i32], ctypes.c_int),
         "tsnnls_chol_solve_noalloc": ([i32, p, i64, i64, p, p], ctypes.c_int),
+        "tsnnls_batch_autotune": ([p, i32, i32, p], ctypes.c_int),
+        "tsnnls_batch_set_panel": ([i32, p], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -295,6 +297,17 @@ class Context:
                                                 _np_ptr(bp), _np_ptr(xp), ctypes.byref(o),
                                                 _np_ptr(stat), ctypes.byref(info))
         return st, stat, info
+
+    def batch_autotune(self, precision=MIXED, per_bucket=64):
+        nb = np.zeros(5, dtype=np.int32)
+        _check(self._lib.tsnnls_batch_autotune(self._h, precision, per_bucket, _np_ptr(nb)),
+               "batch_autotune")
+        return nb
+
+    @staticmethod
+    def batch_set_panel(nb, precision=MIXED):
+        arr = np.ascontiguousarray(nb, dtype=np.int32)
+        _check(load().tsnnls_batch_set_panel(precision, _np_ptr(arr)), "batch_set_panel")
 
     # -- per-phase device time ---------------------------------------------
 

@@ -199,7 +199,7 @@ int tsnnls_solve_ex(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, doubl
     Context &c = ctx->c;
     std::lock_guard<std::mutex> g(c.solve_mu);
     cudaSetDevice(c.device);
-    if (solve_footprint(*A, o) > c.budget) {
+    if (solve_footprint(*A, o, c.budget) > c.budget) {
         if (info) info->status = TSNNLS_EADMIT;
         return TSNNLS_EADMIT;
     }
@@ -222,7 +222,7 @@ int tsnnls_submit(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double 
     req->b = b;
     req->x_out = x_out;
     req->opts = resolve_opts(opts);
-    req->footprint = solve_footprint(*A, req->opts);
+    req->footprint = solve_footprint(*A, req->opts, c.budget);
     if (req->footprint > c.budget) return TSNNLS_EADMIT;
     std::lock_guard<std::mutex> g(c.q_mu);
     st = ensure_workers(ctx);
@@ -429,5 +429,47 @@ int tsnnls_spmv(tsnnls_ctx *ctx, const tsnnls_csr *A, int32_t trans, double alph
 int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
                              const float *const *a, const double *const *b, double *const *x_out,
                              const tsnnls_opts *opts, int32_t *status_out, tsnnls_info *info);
+
+}  // extern "C"
+
+extern "C" {
+
+int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
+                             const float *const *a, const double *const *b, double *const *x_out,
+                             const tsnnls_opts *opts, int32_t *status_out, tsnnls_info *info) {
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (!ctx || count <= 0 || !m || !n || !a || !b || !x_out) return TSNNLS_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] <= 0 || m[i] <= n[i] || n[i] > 1024 || !a[i] || !b[i] || !x_out[i]) {
+            if (info) info->status = TSNNLS_EINVAL;
+            return TSNNLS_EINVAL;
+        }
+    }
+    tsnnls_opts o = resolve_opts(opts);
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    cudaSetDevice(c.device);
+    return run_batch_dense(c, c.lane0, count, m, n, a, b, x_out, o, status_out, info, nullptr);
+}
+
+int tsnnls_batch_autotune(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket, int32_t *nb_out) {
+    if (!ctx || (precision != TSNNLS_MIXED && precision != TSNNLS_FP64)) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.solve_mu);
+    cudaSetDevice(c.device);
+    const bool mixed = precision == TSNNLS_MIXED;
+    int st = batch_autotune(c, c.lane0, mixed, per_bucket > 0 ? per_bucket : 64);
+    if (nb_out)
+        for (int i = 0; i < 5; ++i) nb_out[i] = g_batch_nb_table[mixed ? 0 : 1][i];
+    return st;
+}
+
+int tsnnls_batch_set_panel(int32_t precision, const int32_t *nb) {
+    if (!nb || (precision != TSNNLS_MIXED && precision != TSNNLS_FP64)) return TSNNLS_EINVAL;
+    for (int i = 0; i < 5; ++i)
+        if (nb[i] < 4 || nb[i] > 64) return TSNNLS_EINVAL;
+    for (int i = 0; i < 5; ++i) g_batch_nb_table[precision == TSNNLS_MIXED ? 0 : 1][i] = nb[i];
+    return TSNNLS_OK;
+}
 
 }  // extern "C"

@@ -91,8 +91,13 @@ struct Context {
 int lane_create(Lane &l);
 void lane_destroy(Lane &l);
 
-// Device footprint (bytes) of one factor-path solve at this size.
-size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o);
+// Device footprint (bytes) of one solve at this size on the path AUTO would
+// take under `budget` (the factor path when its cached A^T A fits, else LSQR).
+size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget);
+int choose_path(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget);
+size_t lsqr_footprint(const tsnnls_csr &A, const tsnnls_opts &o);
+int solve_lsqr(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,
+               const tsnnls_opts &o, tsnnls_info *info, const SolveExtras *ex);
 
 // Run one solve on a lane.  Thread-compatible: one caller per lane at a time.
 int solve_on_lane(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
@@ -100,5 +105,14 @@ int solve_on_lane(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b
                   const SolveExtras *extras);
 
 int status_from_cuda(cudaError_t e);
+
+// Batched dense solves (batch.cu).  nb_override (count entries) forces the
+// Cholesky panel width per problem; NULL uses the tuned table.
+int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const int32_t *n,
+                    const float *const *a, const double *const *b, double *const *x,
+                    const tsnnls_opts &o, int32_t *status_out, tsnnls_info *info,
+                    const int *nb_override);
+int batch_autotune(Context &ctx, Lane &lane, bool mixed, int per_bucket);
+extern int g_batch_nb_table[2][5];
 
 }  // namespace tsnnls

@@ -1,0 +1,99 @@
+"""Batched dense path (many uneven problems in one persistent launch), GPU.
+
+Each problem of a batch is compared with the CPU oracle (FP64 A built from
+the same FP32 values) and with its own solve-alone result through the
+single-problem path; the FP64 batch path is checked the same way.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import kkt
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_cs_0408029_gb300 as ts
+
+    ctx = ts.Context(0)
+    yield ts, ctx, torch
+    ctx.close()
+
+
+def _batch(seed, count, n_lo, n_hi):
+    return workloads.batched_uneven(seed=seed, count=count, n_lo=n_lo, n_hi=n_hi)
+
+
+def _run(ts, ctx, torch, probs, precision):
+    a = [torch.as_tensor(p.a, device="cuda") for p in probs]
+    b = [torch.as_tensor(p.b, device="cuda") for p in probs]
+    x = [torch.empty(p.n, dtype=torch.float64, device="cuda") for p in probs]
+    st, stat, info = ctx.solve_batch_dense(a, b, x, precision=precision)
+    return st, stat, info, [t.cpu().numpy() for t in x]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_batch_matches_oracle(env, oracle_mod, precision):
+    ts, ctx, torch = env
+    probs = _batch(101, 24, 32, 300)
+    st, stat, info, xs = _run(ts, ctx, torch, probs, precision)
+    assert st == ts.OK and (stat == ts.OK).all(), stat
+    assert info.kernel_launches >= 2
+    for p, x in zip(probs, xs):
+        csr = workloads.dense_to_csr(p.a.astype(np.float64), p.b)
+        ref = oracle_mod.bpp_solve(csr)
+        err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-9, (p.name, err)
+        assert kkt.violation(csr, x) <= 1e-10 * kkt.atb_norm(csr)
+
+
+def test_batch_equals_solve_alone(env):
+    ts, ctx, torch = env
+    probs = _batch(102, 16, 32, 1024)
+    st, stat, info, xs = _run(ts, ctx, torch, probs, "mixed")
+    assert st == ts.OK
+    for p, x in zip(probs, xs):
+        csr = workloads.dense_to_csr(p.a.astype(np.float64), p.b)
+        alone, _ = ctx.solve(ts.HostCSR.from_problem(csr), csr.b)
+        assert np.linalg.norm(x - alone) <= 1e-9 * np.linalg.norm(alone), p.name
+
+
+def test_batch_single_and_ragged_sizes(env, oracle_mod):
+    ts, ctx, torch = env
+    rng = np.random.default_rng(7)
+    probs = []
+    for n in (1, 2, 31, 32, 33, 63, 64, 65, 129, 1024):
+        m = n + 1 + n // 2
+        a = rng.standard_normal((m, n)).astype(np.float32)
+        xs = np.where(rng.random(n) < 0.3, 0.0, rng.uniform(0.1, 1.0, n))
+        b = a.astype(np.float64) @ xs + 1e-3 * rng.standard_normal(m)
+        probs.append(workloads.DenseProblem(m, n, a, b, xs, f"n{n}"))
+    st, stat, info, xs = _run(ts, ctx, torch, probs, "mixed")
+    assert st == ts.OK, stat
+    for p, x in zip(probs, xs):
+        csr = workloads.dense_to_csr(p.a.astype(np.float64), p.b)
+        ref = oracle_mod.bpp_solve(csr)
+        assert np.linalg.norm(x - ref.x) <= 1e-9 * max(np.linalg.norm(ref.x), 1e-300), p.name
+
+
+def test_batch_rejects_bad_sizes(env):
+    ts, ctx, torch = env
+    a = [torch.zeros((4, 4), dtype=torch.float32, device="cuda")]
+    b = [torch.zeros(4, dtype=torch.float64, device="cuda")]
+    x = [torch.zeros(4, dtype=torch.float64, device="cuda")]
+    st, _, _ = ctx.solve_batch_dense(a, b, x)
+    assert st == ts.EINVAL
+
+
+def test_autotune_picks_candidate_widths(env):
+    ts, ctx, torch = env
+    nb = ctx.batch_autotune(ts.MIXED, per_bucket=16)
+    assert set(nb.tolist()) <= {8, 16, 32, 48}
+    probs = _batch(103, 8, 32, 512)
+    st, stat, info, xs = _run(ts, ctx, torch, probs, "mixed")
+    assert st == ts.OK
