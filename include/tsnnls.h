@@ -170,6 +170,18 @@ int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, c
                              double *const *x_out, const tsnnls_opts *opts,
                              int32_t *status_out, tsnnls_info *info);
 
+/* Autotuner of the batched path's Cholesky panel width.  For each problem
+ * size bucket (n <= 64, 128, 256, 512, 1024) it times the batched solve of a
+ * synthetic batch with every candidate width and keeps the fastest in the
+ * process-wide table that tsnnls_solve_batch_dense reads.  per_bucket caps
+ * the number of problems per timing batch (<= 0: 64).  nb_out (host, 5
+ * entries, may be NULL) receives the chosen widths. */
+int tsnnls_batch_autotune(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket, int32_t *nb_out);
+
+/* Set the table directly (e.g. from a cached autotune result); 5 widths in
+ * [4, 64], clamped to what the kernel's shared memory allows. */
+int tsnnls_batch_set_panel(int32_t precision, const int32_t *nb);
+
 /* ---- per-phase device-time accounting ----------------------------------
  * When enabled, blocking solves on the context bracket every phase of the
  * pivot loop with CUDA events on the stream the kernels run on, and add up
