@@ -157,6 +157,18 @@ int tsnnls_poll(tsnnls_ctx *ctx, tsnnls_ticket ticket, tsnnls_info *info);
  * TSNNLS_PENDING if the time ran out, else as tsnnls_poll. */
 int tsnnls_wait(tsnnls_ctx *ctx, tsnnls_ticket ticket, int64_t timeout_us, tsnnls_info *info);
 
+/* Counters of the asynchronous queue since the context was created. */
+typedef struct {
+    int64_t submitted;         /* tickets accepted by tsnnls_submit */
+    int64_t completed;         /* tickets whose solve has finished */
+    int64_t max_in_use_bytes;  /* largest sum of admitted footprints seen */
+    int64_t budget_bytes;      /* the context's HBM budget */
+    int32_t lanes;             /* streams that run admitted requests */
+    int32_t max_active;        /* largest number of requests running at once */
+} tsnnls_queue_stats;
+
+int tsnnls_queue_stats_read(tsnnls_ctx *ctx, tsnnls_queue_stats *out);
+
 /* Batched dense solves (many small or uneven problems).  Problem i has
  * A_i = a[i] (m[i] x n[i], row-major FP32, device memory), b_i = b[i]
  * (m[i] doubles, device) and x_i = x_out[i] (n[i] doubles, device).  The
@@ -232,18 +244,21 @@ int tsnnls_gather(tsnnls_ctx *ctx, int32_t precision, const void *G, int64_t ldg
                   const int32_t *F, int64_t k, void *S, int64_t lds);
 
 /* Section 2 (normal equations solver): in-place lower Cholesky S = L L^T of a
- * k x k column-major symmetric positive definite matrix (lower triangle
- * read and overwritten; strict upper triangle untouched).  Blocked,
- * right-looking; MIXED runs in FP32 with tensor-core trailing updates, FP64
- * in FP64.  *info_out (host, may be NULL) = 0, or 1 + the column of the
- * first non-positive pivot (then the call returns TSNNLS_ENOTPD). */
+ * k x k column-major symmetric positive definite matrix.  Blocked,
+ * right-looking with panel width NB (128 for MIXED, which runs in FP32; 64
+ * for FP64).  The lower triangle is read and overwritten with L.  The strict
+ * upper triangle of each NB x NB diagonal block receives the transpose of
+ * that block's inverse (L_KK^-1), which the solves use; the rest of the
+ * upper triangle is untouched.  *info_out (host, may be NULL) = 0, or 1 +
+ * the column of the first non-positive pivot (then the call returns
+ * TSNNLS_ENOTPD). */
 int tsnnls_cholesky(tsnnls_ctx *ctx, int32_t precision, void *S, int64_t k, int64_t lds,
                     int32_t *info_out);
 
 /* Eq. 4 through the factor: overwrite rhs (k entries, float for MIXED,
- * double for FP64) with (L L^T)^{-1} rhs, using the lower factor L written
- * by tsnnls_cholesky.  Two triangular solves; the diagonal blocks are solved
- * warp by warp. */
+ * double for FP64) with (L L^T)^{-1} rhs, using S as written by
+ * tsnnls_cholesky with the same precision (L and the diagonal-block
+ * inverses).  Two blocked triangular solves, one CTA per NB-row block. */
 int tsnnls_chol_solve(tsnnls_ctx *ctx, int32_t precision, const void *L, int64_t k, int64_t lds,
                       void *rhs);
 

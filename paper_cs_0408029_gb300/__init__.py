@@ -26,6 +26,7 @@ EXPORTS = (
     "tsnnls_solve_batch_dense", "tsnnls_gram", "tsnnls_gather", "tsnnls_cholesky",
     "tsnnls_chol_solve", "tsnnls_spmv", "tsnnls_profile_enable", "tsnnls_profile_read",
     "tsnnls_chol_solve_noalloc", "tsnnls_batch_autotune", "tsnnls_batch_set_panel",
+    "tsnnls_queue_stats_read",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr")
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = True):
         "tsnnls_chol_solve_noalloc": ([i32, p, i64, i64, p, p], ctypes.c_int),
         "tsnnls_batch_autotune": ([p, i32, i32, p], ctypes.c_int),
         "tsnnls_batch_set_panel": ([i32, p], ctypes.c_int),
+        "tsnnls_queue_stats_read": ([p, p], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -192,6 +194,12 @@ class DeviceCSR:
                    _dev_ptr(self.val), 1)
 
 
+class QueueStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("max_in_use_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
+                ("lanes", ctypes.c_int32), ("max_active", ctypes.c_int32)]
+
+
 class PhaseStat(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_int64), ("bytes", ctypes.c_double),
                 ("flops", ctypes.c_double)]
@@ -203,12 +211,14 @@ class Context:
     def __init__(self, device: int = 0, hbm_budget: int = 0):
         self._lib = load()
         self._h = ctypes.c_void_p()
+        self._inflight = {}  # ticket -> buffers that must outlive the asynchronous solve
         _check(self._lib.tsnnls_ctx_create(ctypes.byref(self._h), device, hbm_budget), "ctx_create")
 
     def close(self):
         if self._h:
-            self._lib.tsnnls_ctx_destroy(self._h)
+            self._lib.tsnnls_ctx_destroy(self._h)  # waits for every outstanding ticket
             self._h = ctypes.c_void_p()
+            self._inflight.clear()
 
     def __enter__(self):
         return self
@@ -269,17 +279,27 @@ class Context:
         xp = _np_ptr(x_out) if isinstance(x_out, np.ndarray) else _dev_ptr(x_out)
         _check(self._lib.tsnnls_submit(self._h, ctypes.byref(s), bp, xp, ctypes.byref(o),
                                        ctypes.byref(t)), "submit")
+        self._inflight[t.value] = (A, b, x_out)
         return t.value
 
     def poll(self, ticket):
         info = Info()
         st = self._lib.tsnnls_poll(self._h, ticket, ctypes.byref(info))
+        if st != PENDING:
+            self._inflight.pop(ticket, None)
         return st, info
 
     def wait(self, ticket, timeout_us=-1):
         info = Info()
         st = self._lib.tsnnls_wait(self._h, ticket, timeout_us, ctypes.byref(info))
+        if st != PENDING:
+            self._inflight.pop(ticket, None)
         return st, info
+
+    def queue_stats(self):
+        q = QueueStats()
+        _check(self._lib.tsnnls_queue_stats_read(self._h, ctypes.byref(q)), "queue_stats")
+        return {f: getattr(q, f) for f, _ in q._fields_}
 
     def solve_batch_dense(self, a_list, b_list, x_list, opts=None, **kw):
         """Dense batched solve; a_list: CUDA float32 [m_i, n_i] row-major, b_list,

@@ -67,6 +67,8 @@ void worker_loop(tsnnls_ctx *ctx, int lane_id) {
         }
         c.in_use += req->footprint;
         c.active += 1;
+        c.max_active = std::max(c.max_active, c.active);
+        c.max_in_use = std::max(c.max_in_use, c.in_use);
         lk.unlock();
         tsnnls_info info;
         int st = solve_on_lane(c, lane, req->A, req->b, req->x_out, req->opts, &info, nullptr);
@@ -76,6 +78,7 @@ void worker_loop(tsnnls_ctx *ctx, int lane_id) {
         req->status = st;
         req->info = info;
         req->done = true;
+        c.completed += 1;
         c.done_cv.notify_all();
         c.q_cv.notify_all();
     }
@@ -230,8 +233,22 @@ int tsnnls_submit(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double 
     const tsnnls_ticket t = c.next_ticket++;
     c.requests[t] = req;
     c.waiting.push_back(t);
+    c.submitted += 1;
     *ticket = t;
     c.q_cv.notify_all();
+    return TSNNLS_OK;
+}
+
+int tsnnls_queue_stats_read(tsnnls_ctx *ctx, tsnnls_queue_stats *out) {
+    if (!ctx || !out) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.q_mu);
+    out->submitted = c.submitted;
+    out->completed = c.completed;
+    out->max_in_use_bytes = (int64_t)c.max_in_use;
+    out->budget_bytes = (int64_t)c.budget;
+    out->lanes = (int32_t)c.lanes.size();
+    out->max_active = c.max_active;
     return TSNNLS_OK;
 }
 

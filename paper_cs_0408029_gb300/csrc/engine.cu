@@ -391,16 +391,28 @@ cleanup:
 
 }  // namespace
 
-size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o) {
+static size_t factor_footprint(const tsnnls_csr &A, const tsnnls_opts &o) {
     const bool host_in = A.on_device == 0;
     return o.precision == TSNNLS_FP64 ? layout_bytes<double>(A.m, A.n, A.nnz, host_in)
                                       : layout_bytes<float>(A.m, A.n, A.nnz, host_in);
+}
+
+int choose_path(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget) {
+    if (o.path == TSNNLS_PATH_FACTOR || o.path == TSNNLS_PATH_LSQR) return o.path;
+    return factor_footprint(A, o) <= budget ? TSNNLS_PATH_FACTOR : TSNNLS_PATH_LSQR;
+}
+
+size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget) {
+    return choose_path(A, o, budget) == TSNNLS_PATH_LSQR ? lsqr_footprint(A, o)
+                                                         : factor_footprint(A, o);
 }
 
 int solve_on_lane(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,
                   const tsnnls_opts &o, tsnnls_info *info, const SolveExtras *extras) {
     if (info) std::memset(info, 0, sizeof(*info));
     std::memset(lane.st_host, 0, sizeof(DevStatus));
+    if (choose_path(A, o, ctx.budget) == TSNNLS_PATH_LSQR)
+        return solve_lsqr(ctx, lane, A, b, x_out, o, info, extras);
     if (o.precision == TSNNLS_FP64)
         return solve_factor<double>(ctx, lane, A, b, x_out, o, info, extras);
     return solve_factor<float>(ctx, lane, A, b, x_out, o, info, extras);

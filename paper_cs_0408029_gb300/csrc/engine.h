@@ -86,6 +86,9 @@ struct Context {
     std::vector<Lane> lanes;
     bool stopping = false;
     int active = 0;
+    int max_active = 0;
+    int64_t submitted = 0, completed = 0;
+    size_t max_in_use = 0;
 };
 
 int lane_create(Lane &l);

@@ -201,15 +201,16 @@ def batched_uneven(seed=SEED_BASE + 2, count=512, n_lo=32, n_hi=1024,
 
 
 def lsqr_large(seed=SEED_BASE + 3, m=2_000_000, n=200_000, per_row=8,
-               zero_frac=0.6, noise=1e-3) -> CSRProblem:
+               zero_frac=0.6, noise=1e-3, col_spread=2.0) -> CSRProblem:
     """A 2e6 x 2e5: 8 nonzeros per row at distinct uniform columns, N(0,1), then
-    column j scaled by s_j = 10^U(-2, 2) (condition number ~1e4).  x*: 60 %
-    exact zeros, rest U(0.1,1).  b = A x* + N(0, (1e-3)^2)."""
+    column j scaled by s_j = 10^U(-2, 2) (condition number ~1e4; ``col_spread``
+    sets the exponent range).  x*: 60 % exact zeros, rest U(0.1,1).
+    b = A x* + N(0, (1e-3)^2)."""
     rng = np.random.default_rng(seed)
     cols = _distinct_cols_per_row(rng, m, n, per_row).reshape(-1)
     rows = np.repeat(np.arange(m), per_row)
     vals = rng.standard_normal(rows.size)
-    s = 10.0 ** rng.uniform(-2.0, 2.0, size=n)
+    s = 10.0 ** rng.uniform(-col_spread, col_spread, size=n)
     vals = vals * s[cols]
     row_ptr, col_idx, val = _csr_from_rows(m, n, rows, cols, vals)
     x, _ = _planted_x(rng, n, zero_frac)
