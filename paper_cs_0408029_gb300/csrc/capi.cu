@@ -371,9 +371,16 @@ int tsnnls_cholesky(tsnnls_ctx *ctx, int32_t precision, void *S, int64_t k, int6
     cudaSetDevice(c.device);
     Lane &l = c.lane0;
     cudaError_t e = cudaMemsetAsync(l.st_dev, 0, sizeof(DevStatus), l.stream);
+    float *panel = nullptr;
+    TcPanel tc;
+    if (e == cudaSuccess && precision != TSNNLS_FP64 && k > 0) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&panel), sizeof(float) * (size_t)k * 256, l.stream);
+        if (e == cudaSuccess) tc_panel_init(tc, panel, panel + (size_t)k * 128, k);
+    }
     if (e == cudaSuccess)
         e = precision == TSNNLS_FP64 ? launch_cholesky<double>(l.stream, (double *)S, k, lds, l.st_dev)
-                                     : launch_cholesky<float>(l.stream, (float *)S, k, lds, l.st_dev);
+                                     : launch_cholesky<float>(l.stream, (float *)S, k, lds, l.st_dev, &tc);
+    if (panel) cudaFreeAsync(panel, l.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(l.st_host, l.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, l.stream);
     int st = finish(l, e);

@@ -2,6 +2,7 @@
 // block principal pivoting NNLS library.  Nothing here is part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -59,9 +60,28 @@ template <typename T>
 cudaError_t launch_gather(cudaStream_t s, const T *G, int64_t ldg, const int32_t *F,
                           const int32_t *k_dev, int64_t k_max, T *S, int64_t lds);
 
+// Tensor-core update context for the FP32 factorisation: K-major hi / lo
+// copies of each step's panel (rows x 128 FP32 each) and their TMA maps.
+struct TcPanel {
+    CUtensorMap map_hi, map_lo;
+    float *xhi = nullptr, *xlo = nullptr;
+    int64_t rows = 0;
+    bool ok = false;
+};
+
+bool tc_available();
+bool tc_encode_panel_map(void *buf, int64_t rows, CUtensorMap *out);
+// Prepare tc over two caller-owned buffers of rows x 128 floats; false if the
+// tensor maps cannot be encoded (the factorisation then uses the SIMT update).
+bool tc_panel_init(TcPanel &tc, float *xhi, float *xlo, int64_t rows);
+cudaError_t launch_tc_update(cudaStream_t s, const CUtensorMap &hi, const CUtensorMap &lo, float *S,
+                             int64_t k, int64_t lds, int64_t T0, DevStatus *st);
+
 // In-place blocked lower Cholesky of the k x k matrix S (column-major, lds).
+// tc (FP32 only, may be NULL) selects the tensor-core trailing update.
 template <typename T>
-cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st);
+cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st,
+                            const TcPanel *tc = nullptr);
 
 // rhs <- (L L^T)^{-1} rhs with the blocked warp-level triangular solves.
 // flags/ticket: scratch of at least 2*cdiv(k,64)+2 ints.

@@ -141,6 +141,10 @@ size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     c.take<uint8_t>(n);
     c.take<int32_t>(n);
     c.take<int32_t>(cdiv(n, 64) + 2);
+    if (sizeof(T) == 4) {
+        c.take<float>((size_t)n * 128);  // K-major hi / lo panel copies for the tensor-core update
+        c.take<float>((size_t)n * 128);
+    }
     return c.off + 256;
 }
 
@@ -230,6 +234,12 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         uint8_t *inF = cv.take<uint8_t>(n);
         int32_t *F = cv.take<int32_t>(n);
         int32_t *flags = cv.take<int32_t>(cdiv(n, 64) + 2);
+        TcPanel tc;
+        if (sizeof(T) == 4) {
+            float *xhi = cv.take<float>((size_t)n * 128);
+            float *xlo = cv.take<float>((size_t)n * 128);
+            tc_panel_init(tc, xhi, xlo, n);
+        }
         const double avg_row = (double)nnz / (double)m, avg_col = (double)nnz / (double)n;
         const double csr_bytes = 12.0 * nnz + 8.0 * (m + 1);
         const double csc_bytes = 12.0 * nnz + 8.0 * (n + 1);
@@ -286,7 +296,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 TRY_CUDA(launch_gather<T>(s, G, ldg, F, nullptr, k, S, lds));
                 prof_end(lane, 2.0 * tri + 4.0 * k, 0.0);
                 prof_begin(lane, TSNNLS_PHASE_FACTOR);
-                TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev));
+                TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc));
                 prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
                 // first solve: x_F = (L L^T)^{-1} c_F  (x restarts from 0)
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);

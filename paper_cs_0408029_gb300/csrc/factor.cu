@@ -58,20 +58,28 @@ __global__ void __launch_bounds__(256)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int kb = (int)min((int64_t)NB, k - K);
     if (tid == 0) bad = 0;
-    // load the lower triangle; pad beyond kb with the identity
-    for (int e = tid; e < NB * NB; e += 256) {
-        const int c = e / NB, r = e % NB;
-        T v = T(0);
-        if (r >= c) {
-            if (r < kb && c < kb) v = S[(K + r) + (K + c) * lds];
-            else if (r == c) v = T(1);
+    // load the lower triangle; pad beyond kb with the identity; W starts at 0
+    // (eight loads in flight per thread before any shared-memory store)
+    for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int c = e / NB, r = e % NB;
+            v[u] = (r >= c && r < kb && c < kb) ? S[(K + r) + (K + c) * lds] : T(0);
         }
-        A[c][r] = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int c = e / NB, r = e % NB;
+            A[c][r] = (r == c && r >= kb) ? T(1) : v[u];
+            W[c][r] = T(0);
+        }
     }
     __syncthreads();
     for (int jb = 0; jb < NB; jb += 32) {
-        // a warp factors the 32 x 32 diagonal sub-block; lane = row
         if (warp == 0) {
+            // factor the 32 x 32 diagonal sub-block in registers (lane = row)
             T a[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) a[c] = c <= lane ? A[jb + c][jb + lane] : T(0);
@@ -94,75 +102,116 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int c = 0; c < 32; ++c)
                 if (c <= lane) A[jb + c][jb + lane] = a[c];
+            __syncwarp();
+            // its inverse, lane = column: forward substitution on the unit vector
+            T y[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                T s = (i == lane) ? T(1) : T(0);
+#pragma unroll
+                for (int l = 0; l < i; ++l) s -= A[jb + l][jb + i] * y[l];
+                y[i] = s / A[jb + i][jb + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) W[jb + lane][jb + i] = (i >= lane) ? y[i] : T(0);
         }
         __syncthreads();
-        // rows below the sub-block: X L_jj^T = B, one thread per row
+        const int rem = NB - jb - 32;
+        if (rem == 0) break;
+        // rows below: X = B W_jj^T, one thread per row, independent columns
         for (int r = jb + 32 + tid; r < NB; r += 256) {
-            T x[32];
+            T bq[32];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) x[c] = A[jb + c][r];
+            for (int l = 0; l < 32; ++l) bq[l] = A[jb + l][r];
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
-                T s = x[c];
-#pragma unroll
-                for (int l = 0; l < c; ++l) s -= x[l] * A[jb + l][jb + c];
-                x[c] = s / A[jb + c][jb + c];
-            }
-#pragma unroll
-            for (int c = 0; c < 32; ++c) A[jb + c][r] = x[c];
-        }
-        __syncthreads();
-        // trailing sub-block update
-        const int rem = NB - jb - 32;
-        for (int e = tid; e < rem * rem; e += 256) {
-            const int i = jb + 32 + e % rem, l = jb + 32 + e / rem;
-            if (i >= l) {
                 T s = T(0);
-#pragma unroll 8
-                for (int c = 0; c < 32; ++c) s += A[jb + c][i] * A[jb + c][l];
-                A[l][i] -= s;
+#pragma unroll
+                for (int l = 0; l <= c; ++l) s += bq[l] * W[jb + l][jb + c];
+                A[jb + c][r] = s;
             }
         }
         __syncthreads();
-    }
-    // W = L^-1: inverses of the 32 x 32 diagonal blocks, one warp per block,
-    // lane = column (forward substitution on the unit vector)
-    constexpr int NBB = NB / 32;
-    if (warp < NBB) {
-        const int b0 = warp * 32;
-        T y[32];
+        // trailing update, 4 x 4 register tiles on the lower triangle
+        const int tq = rem / 4;
+        const int ntile = tq * (tq + 1) / 2;
+        for (int tb = tid; tb < ntile; tb += 256) {
+            int ti = (int)((sqrtf(8.f * tb + 1.f) - 1.f) * 0.5f);
+            while (ti * (ti + 1) / 2 > tb) --ti;
+            while ((ti + 1) * (ti + 2) / 2 <= tb) ++ti;
+            const int tl = tb - ti * (ti + 1) / 2;
+            const int i0 = jb + 32 + ti * 4, l0 = jb + 32 + tl * 4;
+            T acc[4][4] = {};
+#pragma unroll 4
+            for (int c = 0; c < 32; ++c) {
+                T x[4], z[4];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            T s = (i == lane) ? T(1) : T(0);
+                for (int q = 0; q < 4; ++q) {
+                    x[q] = A[jb + c][i0 + q];
+                    z[q] = A[jb + c][l0 + q];
+                }
 #pragma unroll
-            for (int l = 0; l < i; ++l) s -= A[b0 + l][b0 + i] * y[l];
-            y[i] = s / A[b0 + i][b0 + i];
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[p][q] += x[p] * z[q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (i0 + p >= l0 + q) A[l0 + q][i0 + p] -= acc[p][q];
         }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) W[b0 + lane][b0 + i] = (i >= lane) ? y[i] : T(0);
+        __syncthreads();
     }
-    __syncthreads();
-    // off-diagonal blocks by distance d: W_IJ = -W_II sum_{l=J}^{I-1} L_Il W_lJ
-    // (Tmp holds the sums; it reuses the strict upper part of W, unused here)
+    // off-diagonal blocks of W = L^-1 by distance d:
+    //   T_IJ = sum_{m=J}^{I-1} L_Im W_mJ  (kept in the free upper part of W),  W_IJ = -W_II T_IJ
+    constexpr int NBB = NB / 32;
     for (int d = 1; d < NBB; ++d) {
         const int npairs = NBB - d;
-        for (int e = tid; e < npairs * 1024; e += 256) {
-            const int pr = e / 1024, q = e % 1024;
+        for (int w = tid; w < npairs * 64; w += 256) {
+            const int pr = w / 64, q = w % 64;
             const int J = pr, I = pr + d;
-            const int r = q % 32, c = q / 32;
-            T s = T(0);
-            for (int l = J * 32; l < I * 32; ++l) s += A[l][I * 32 + r] * W[J * 32 + c][l];
-            W[I * 32 + r][J * 32 + c] = s;  // transposed slot (upper part of W), free for now
+            const int r0 = (q % 8) * 4, c0 = (q / 8) * 4;
+            T acc[4][4] = {};
+            for (int l = J * 32; l < I * 32; ++l) {
+                T x[4], z[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    x[p] = A[l][I * 32 + r0 + p];
+                    z[p] = W[J * 32 + c0 + p][l];
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) acc[p][t] += x[p] * z[t];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) W[I * 32 + r0 + p][J * 32 + c0 + t] = acc[p][t];
         }
         __syncthreads();
-        for (int e = tid; e < npairs * 1024; e += 256) {
-            const int pr = e / 1024, q = e % 1024;
+        for (int w = tid; w < npairs * 64; w += 256) {
+            const int pr = w / 64, q = w % 64;
             const int J = pr, I = pr + d;
-            const int r = q % 32, c = q / 32;
-            T s = T(0);
-            for (int l = 0; l <= r; ++l) s += W[I * 32 + l][I * 32 + r] * W[I * 32 + l][J * 32 + c];
-            // W[col][row]: element (I*32 + r, J*32 + c) lives at W[J*32 + c][I*32 + r]
-            W[J * 32 + c][I * 32 + r] = -s;
+            const int r0 = (q % 8) * 4, c0 = (q / 8) * 4;
+            T acc[4][4] = {};
+            for (int l = 0; l < r0 + 4; ++l) {
+                T x[4], z[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    x[p] = W[I * 32 + l][I * 32 + r0 + p];  // W_II(r0 + p, l), 0 above the diagonal
+                    z[p] = W[I * 32 + l][J * 32 + c0 + p];  // T_IJ(l, c0 + p)
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) acc[p][t] += x[p] * z[t];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) W[J * 32 + c0 + t][I * 32 + r0 + p] = -acc[p][t];
         }
         __syncthreads();
     }
@@ -176,36 +225,93 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// panel: X = B W^T for the rows below the diagonal block (64 rows per CTA)
+// panel: X = B W^T for the rows below the diagonal block: 64 rows per CTA,
+// each thread a 4 x (NB/16) register tile of X
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
-    chol_panel_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K) {
+    chol_panel_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, float *__restrict__ xhi,
+                      float *__restrict__ xlo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*Wt)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);  // Wt[c][l] = W(c, l)
-    T(*B)[65] = reinterpret_cast<T(*)[65]>(smem_raw + sizeof(T) * NB * (NB + 1));  // B[l][row]
+    T(*Wl)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);  // Wl[l][c] = W(c, l)
+    T(*B)[68] = reinterpret_cast<T(*)[68]>(smem_raw + sizeof(T) * NB * (NB + 4));  // B[l][row]
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, k - K);
     const int64_t R0 = K + kb + (int64_t)blockIdx.x * 64;
     const int nr = (int)min((int64_t)64, k - R0);
     if (nr <= 0) return;
-    for (int e = tid; e < kb * kb; e += 256) {
-        const int c = e / kb, l = e % kb;
-        T v = T(0);
-        if (l < c) v = S[(K + l) + (K + c) * lds];                  // W(c, l), stored transposed
-        else if (l == c) v = T(1) / S[(K + c) + (K + c) * lds];     // W(c, c) = 1 / L(c, c)
-        Wt[c][l] = v;
+    for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int c = e / NB, l = e % NB;
+            // W(c, l) for l < c is stored transposed; W(c, c) = 1 / L(c, c)
+            v[u] = (c < kb && l <= c) ? S[(K + l) + (K + c) * lds] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int c = e / NB, l = e % NB;
+            Wl[l][c] = (l == c && c < kb) ? T(1) / v[u] : v[u];
+        }
     }
-    for (int e = tid; e < kb * 64; e += 256) {
-        const int l = e / 64, r = e % 64;
-        B[l][r] = r < nr ? S[(R0 + r) + (K + l) * lds] : T(0);
+    for (int e0 = 0; e0 < NB * 64; e0 += 256 * 8) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int l = e / 64, r = e % 64;
+            v[u] = (r < nr && l < kb) ? S[(R0 + r) + (K + l) * lds] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            B[e / 64][e % 64] = v[u];
+        }
     }
     __syncthreads();
-    const int r = tid & 63, cq = tid >> 6;
-    for (int c = cq; c < kb; c += 4) {
-        T s = T(0);
-        for (int l = 0; l <= c; ++l) s += B[l][r] * Wt[c][l];
-        if (r < nr) S[(R0 + r) + (K + c) * lds] = s;
+    constexpr int CT = NB / 16;              // columns per thread
+    const int tr = tid & 15, tc = tid >> 4;  // rows tr*4 .. +4, columns tc*CT .. +CT
+    T acc[4][CT] = {};
+#pragma unroll 4
+    for (int l = 0; l < NB; ++l) {
+        T x[4], w[CT];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) x[p] = B[l][tr * 4 + p];
+#pragma unroll
+        for (int q = 0; q < CT; ++q) w[q] = Wl[l][tc * CT + q];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < CT; ++q) acc[p][q] += x[p] * w[q];
+    }
+#pragma unroll
+    for (int q = 0; q < CT; ++q) {
+        const int c = tc * CT + q;
+        if (c >= kb) continue;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int r = tr * 4 + p;
+            if (r < nr) S[(R0 + r) + (K + c) * lds] = acc[p][q];
+        }
+    }
+    if (xhi) {
+        // K-major hi / lo split of X for the tensor-core update: hi keeps the
+        // top 10 mantissa bits (exact in TF32), lo = x - hi is exact in FP32
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int r = tr * 4 + p;
+            if (r >= nr) continue;
+#pragma unroll
+            for (int q = 0; q < CT; ++q) {
+                const int c = tc * CT + q;
+                const float v = (float)acc[p][q];
+                const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+                xhi[(R0 + r) * 128 + c] = hi;
+                xlo[(R0 + r) * 128 + c] = v - hi;
+            }
+        }
     }
 }
 
@@ -266,22 +372,30 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
         buf ^= 1;
     }
+    // loads of C first, then the stores (see the tensor-core epilogue)
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
         const int64_t gr = r0 + (x < 4 ? ty * 4 + x : 64 + ty * 4 + (x - 4));
+        T cv[8];
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
             const int64_t gc = c0 + (y < 4 ? tx * 4 + y : 64 + tx * 4 + (y - 4));
-            if (gr < k && gc < k && gr >= gc) S[gr + gc * lds] -= acc[x][y];
+            cv[y] = (gr < k && gc < k && gr >= gc) ? S[gr + gc * lds] : T(0);
+        }
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+            const int64_t gc = c0 + (y < 4 ? tx * 4 + y : 64 + tx * 4 + (y - 4));
+            if (gr < k && gc < k && gr >= gc) S[gr + gc * lds] = cv[y] - acc[x][y];
         }
     }
 }
 
 template <typename T>
-cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st) {
+cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st,
+                            const TcPanel *tc) {
     constexpr int NB = FactorCfg<T>::NB;
     const size_t smem_diag = 2 * sizeof(T) * NB * (NB + 1);
-    const size_t smem_panel = sizeof(T) * NB * (NB + 1) + sizeof(T) * NB * 65;
+    const size_t smem_panel = sizeof(T) * NB * (NB + 4) + sizeof(T) * NB * 68;
     cudaError_t e = cudaFuncSetAttribute(chol_diag_kernel<T, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
     if (e == cudaSuccess)
@@ -294,18 +408,28 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
         chol_diag_kernel<T, NB><<<1, 256, smem_diag, s>>>(S, k, lds, K, st);
         note_launches(1);
         if (below > 0) {
-            chol_panel_kernel<T, NB><<<(unsigned)cdiv(below, 64), 256, smem_panel, s>>>(S, k, lds, K);
+            const bool use_tc = NB == 128 && sizeof(T) == 4 && tc && tc->ok && tc->rows >= k;
+            chol_panel_kernel<T, NB><<<(unsigned)cdiv(below, 64), 256, smem_panel, s>>>(
+                S, k, lds, K, use_tc ? tc->xhi : nullptr, use_tc ? tc->xlo : nullptr);
             note_launches(1);
-            const int64_t t = cdiv(below, 128);
-            chol_update128_kernel<T><<<(unsigned)(t * (t + 1) / 2), 256, 0, s>>>(S, k, lds, K, kb);
-            note_launches(1);
+            if (use_tc) {
+                e = launch_tc_update(s, tc->map_hi, tc->map_lo, reinterpret_cast<float *>(S), k, lds,
+                                     K + kb, st);
+                if (e != cudaSuccess) return e;
+            } else {
+                const int64_t t = cdiv(below, 128);
+                chol_update128_kernel<T><<<(unsigned)(t * (t + 1) / 2), 256, 0, s>>>(S, k, lds, K, kb);
+                note_launches(1);
+            }
         }
     }
     return cudaGetLastError();
 }
 
-template cudaError_t launch_cholesky<float>(cudaStream_t, float *, int64_t, int64_t, DevStatus *);
-template cudaError_t launch_cholesky<double>(cudaStream_t, double *, int64_t, int64_t, DevStatus *);
+template cudaError_t launch_cholesky<float>(cudaStream_t, float *, int64_t, int64_t, DevStatus *,
+                                            const TcPanel *);
+template cudaError_t launch_cholesky<double>(cudaStream_t, double *, int64_t, int64_t, DevStatus *,
+                                             const TcPanel *);
 
 // ---------------------------------------------------------------------------
 // Triangular solves: L z = r, then L^T w = z, in place on rhs.
@@ -367,14 +491,20 @@ __global__ void __launch_bounds__(256)
     const int64_t row0 = (int64_t)i * NB;
     const int nr = (int)min((int64_t)NB, k - row0);
     const int r = tid % NB, part = tid / NB;
-    for (int e = tid; e < NB * NB; e += 256) {
-        const int rr = e / NB, l = e % NB;  // coalesced reads of the stored W^T (row l of column rr)
-        T v = T(0);
-        if (rr < nr && l < nr) {
-            if (l < rr) v = L[(row0 + l) + (row0 + rr) * lds];
-            else if (l == rr) v = T(1) / L[(row0 + rr) + (row0 + rr) * lds];
+    for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {  // coalesced reads of the stored W^T
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int rr = e / NB, l = e % NB;
+            v[u] = (rr < nr && l <= rr) ? L[(row0 + l) + (row0 + rr) * lds] : T(0);
         }
-        Ws[l][rr] = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int rr = e / NB, l = e % NB;
+            Ws[l][rr] = (l == rr && rr < nr) ? T(1) / v[u] : v[u];
+        }
     }
     T acc = T(0);
     T tile[CW];
@@ -444,14 +574,20 @@ __global__ void __launch_bounds__(256)
     const int i = blk_sh;
     const int64_t row0 = (int64_t)i * NB;
     const int nr = (int)min((int64_t)NB, k - row0);
-    for (int e = tid; e < NB * NB; e += 256) {
-        const int rr = e / NB, l = e % NB;
-        T v = T(0);
-        if (rr < nr && l < nr) {
-            if (l < rr) v = L[(row0 + l) + (row0 + rr) * lds];
-            else if (l == rr) v = T(1) / L[(row0 + rr) + (row0 + rr) * lds];
+    for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {  // coalesced reads of the stored W^T
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int rr = e / NB, l = e % NB;
+            v[u] = (rr < nr && l <= rr) ? L[(row0 + l) + (row0 + rr) * lds] : T(0);
         }
-        Ws[l][rr] = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 256 + tid;
+            const int rr = e / NB, l = e % NB;
+            Ws[l][rr] = (l == rr && rr < nr) ? T(1) / v[u] : v[u];
+        }
     }
     T acc[CPW];
 #pragma unroll
