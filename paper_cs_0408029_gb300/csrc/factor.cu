@@ -3,11 +3,9 @@
 // through it (Eq. 4: x_F = L^-T L^-1 c_F).
 //
 // Right-looking, panel width NB (128 in FP32, 64 in FP64).  Step K:
-//   diag    one CTA factors the NB x NB diagonal block in shared memory
-//           (32-wide sub-panels: a warp factors each 32 x 32 block in
-//           registers, the CTA solves and updates the rest) and inverts the
-//           resulting L_KK (warp-level inverses of the 32 x 32 blocks, then
-//           the off-diagonal blocks).  L_KK goes to the lower triangle, W_K =
+//   diag    one CTA factors the NB x NB diagonal block in shared memory and
+//           builds its inverse in the same column sweep (all 256 threads,
+//           one barrier per column).  L_KK goes to the lower triangle, W_K =
 //           L_KK^-1 transposed into the strict upper triangle of the block.
 //   panel   X = B W_K^T for every row below the block: a small dense product,
 //           fully parallel (no serial substitution down the panel).
@@ -48,16 +46,122 @@ __device__ __forceinline__ void tri_tile2(int64_t b, int64_t &I, int64_t &J) {
 // ---------------------------------------------------------------------------
 // diag: factor + invert the NB x NB diagonal block (one CTA of 256 threads)
 
+// ---- warp-level 32 x 32 factor + inverse -------------------------------------
+// Lane i holds row i of the block (a[32]); step J, fully unrolled through
+// template recursion so that every register index is a compile-time
+// constant:  L(J, J) = sqrt(a_J[J]), L(i, J) = a_i[J] / L(J, J), and
+// a_i[l] -= L(i, J) L(l, J) for J < l <= i.  The same shuffles of column J
+// drive the inverse, lane c holding column c of W = L^-1:
+//   W(J, c) = (delta_Jc - acc_c[J]) / L(J, J),  acc_c[l] += L(l, J) W(J, c)  (l > J).
+template <typename T>
+struct WarpChol {
+    T a[32], acc[32], w[32];
+};
+
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
+template <typename T, int J>
+__device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, int lane, int &bad, int base) {
+    T d = __shfl_sync(0xffffffffu, s.a[J], J);
+    if (!(d > T(0))) {
+        if (!bad) bad = base + J + 1;
+        d = T(1);
+    }
+    const T inv = rsqrt_t(d);
+    const T lij = (lane > J) ? s.a[J] * inv : (lane == J ? d * inv : s.a[J]);
+    s.a[J] = lij;
+    const T wj = (J >= lane) ? (((J == lane) ? T(1) : T(0)) - s.acc[J]) * inv : T(0);
+    s.w[J] = wj;
+#pragma unroll
+    for (int l = J + 1; l < 32; ++l) {
+        const T llj = __shfl_sync(0xffffffffu, lij, l);
+        if (lane >= l) s.a[l] -= lij * llj;
+        s.acc[l] += llj * wj;
+    }
+    if constexpr (J + 1 < 32) warp_chol_step<T, J + 1>(s, lane, bad, base);
+}
+
+// Factor A(j0.., j0..) (32 x 32, lower) in place and write its inverse to W.
+template <typename T, int NB>
+__device__ __forceinline__ void warp_chol_inv(T (*A)[NB + 4], T (*W)[NB + 4], int j0, int lane,
+                                              int &bad) {
+    WarpChol<T> s;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        s.a[c] = c <= lane ? A[j0 + c][j0 + lane] : T(0);
+        s.acc[c] = T(0);
+    }
+    warp_chol_step<T, 0>(s, lane, bad, j0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        if (c <= lane) A[j0 + c][j0 + lane] = s.a[c];
+        W[j0 + lane][j0 + c] = s.w[c];  // column `lane` of W, rows c (0 above the diagonal)
+    }
+}
+
+// ---- CTA-level small products on shared-memory blocks -------------------------
+// out(r, c) = sum_{t < K} X(r, t) Y(t, c) for r < M, c < N (multiples of 4),
+// 4 x 4 register tiles, at most 256 tiles (one per thread); tri: only the
+// lower tiles (r block >= c block) of a square output.  All reads happen
+// before the barrier, all writes (fo) after it, so the output may overwrite
+// a source.
+template <typename T, typename FX, typename FY, typename FO>
+__device__ __forceinline__ void cta_prod(int M, int N, int K, bool tri, FX fx, FY fy, FO fo) {
+    const int tid = threadIdx.x;
+    const int nt_r = M / 4, nt_c = N / 4;
+    const int ntiles = tri ? nt_r * (nt_r + 1) / 2 : nt_r * nt_c;
+    // waves of 256 tiles; an output that overwrites a source must fit in one
+    for (int base = 0; base < ntiles; base += 256) {
+        const int tile = base + tid;
+        const bool active = tile < ntiles;
+        T acc[4][4] = {};
+        int tr = 0, tc = 0;
+        if (active) {
+            if (tri) {
+                int i = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+                while (i * (i + 1) / 2 > tile) --i;
+                while ((i + 1) * (i + 2) / 2 <= tile) ++i;
+                tr = i;
+                tc = tile - i * (i + 1) / 2;
+            } else {
+                tr = tile % nt_r;
+                tc = tile / nt_r;
+            }
+            for (int t = 0; t < K; ++t) {
+                T x[4], y[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    x[p] = fx(tr * 4 + p, t);
+                    y[p] = fy(t, tc * 4 + p);
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[p][q] += x[p] * y[q];
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) fo(tr * 4 + p, tc * 4 + q, acc[p][q]);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
     chol_diag_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, DevStatus *st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);                              // A[col][row]
-    T(*W)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * NB * (NB + 1));  // W[col][row]
-    __shared__ int bad;
+    T(*A)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);                              // A[col][row]
+    T(*W)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw + sizeof(T) * NB * (NB + 4));  // W[col][row]
+    __shared__ int bad_sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int kb = (int)min((int64_t)NB, k - K);
-    if (tid == 0) bad = 0;
+    if (tid == 0) bad_sh = 0;
     // load the lower triangle; pad beyond kb with the identity; W starts at 0
     // (eight loads in flight per thread before any shared-memory store)
     for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {
@@ -77,150 +181,55 @@ __global__ void __launch_bounds__(256)
         }
     }
     __syncthreads();
-    for (int jb = 0; jb < NB; jb += 32) {
-        if (warp == 0) {
-            // factor the 32 x 32 diagonal sub-block in registers (lane = row)
-            T a[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) a[c] = c <= lane ? A[jb + c][jb + lane] : T(0);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                T d = __shfl_sync(0xffffffffu, a[j], j);
-                if (!(d > T(0))) {
-                    if (lane == 0 && !bad) bad = jb + j + 1;
-                    d = T(1);
-                }
-                const T sd = sqrt(d);
-                if (lane == j) a[j] = sd;
-                else if (lane > j) a[j] = a[j] / sd;
-#pragma unroll
-                for (int l = j + 1; l < 32; ++l) {
-                    const T llj = __shfl_sync(0xffffffffu, a[j], l);
-                    if (lane >= l) a[l] -= a[j] * llj;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 32; ++c)
-                if (c <= lane) A[jb + c][jb + lane] = a[c];
-            __syncwarp();
-            // its inverse, lane = column: forward substitution on the unit vector
-            T y[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                T s = (i == lane) ? T(1) : T(0);
-#pragma unroll
-                for (int l = 0; l < i; ++l) s -= A[jb + l][jb + i] * y[l];
-                y[i] = s / A[jb + i][jb + i];
-            }
-#pragma unroll
-            for (int i = 0; i < 32; ++i) W[jb + lane][jb + i] = (i >= lane) ? y[i] : T(0);
-        }
-        __syncthreads();
-        const int rem = NB - jb - 32;
-        if (rem == 0) break;
-        // rows below: X = B W_jj^T, one thread per row, independent columns
-        for (int r = jb + 32 + tid; r < NB; r += 256) {
-            T bq[32];
-#pragma unroll
-            for (int l = 0; l < 32; ++l) bq[l] = A[jb + l][r];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                T s = T(0);
-#pragma unroll
-                for (int l = 0; l <= c; ++l) s += bq[l] * W[jb + l][jb + c];
-                A[jb + c][r] = s;
-            }
-        }
-        __syncthreads();
-        // trailing update, 4 x 4 register tiles on the lower triangle
-        const int tq = rem / 4;
-        const int ntile = tq * (tq + 1) / 2;
-        for (int tb = tid; tb < ntile; tb += 256) {
-            int ti = (int)((sqrtf(8.f * tb + 1.f) - 1.f) * 0.5f);
-            while (ti * (ti + 1) / 2 > tb) --ti;
-            while ((ti + 1) * (ti + 2) / 2 <= tb) ++ti;
-            const int tl = tb - ti * (ti + 1) / 2;
-            const int i0 = jb + 32 + ti * 4, l0 = jb + 32 + tl * 4;
-            T acc[4][4] = {};
-#pragma unroll 4
-            for (int c = 0; c < 32; ++c) {
-                T x[4], z[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    x[q] = A[jb + c][i0 + q];
-                    z[q] = A[jb + c][l0 + q];
-                }
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[p][q] += x[p] * z[q];
-            }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (i0 + p >= l0 + q) A[l0 + q][i0 + p] -= acc[p][q];
-        }
-        __syncthreads();
-    }
-    // off-diagonal blocks of W = L^-1 by distance d:
-    //   T_IJ = sum_{m=J}^{I-1} L_Im W_mJ  (kept in the free upper part of W),  W_IJ = -W_II T_IJ
     constexpr int NBB = NB / 32;
-    for (int d = 1; d < NBB; ++d) {
-        const int npairs = NBB - d;
-        for (int w = tid; w < npairs * 64; w += 256) {
-            const int pr = w / 64, q = w % 64;
-            const int J = pr, I = pr + d;
-            const int r0 = (q % 8) * 4, c0 = (q / 8) * 4;
-            T acc[4][4] = {};
-            for (int l = J * 32; l < I * 32; ++l) {
-                T x[4], z[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    x[p] = A[l][I * 32 + r0 + p];
-                    z[p] = W[J * 32 + c0 + p][l];
-                }
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) acc[p][t] += x[p] * z[t];
-            }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int t = 0; t < 4; ++t) W[I * 32 + r0 + p][J * 32 + c0 + t] = acc[p][t];
+    for (int jb = 0; jb < NBB; ++jb) {
+        const int j0 = jb * 32;
+        if (warp == 0) {
+            int bad = 0;
+            warp_chol_inv<T, NB>(A, W, j0, lane, bad);
+            if (lane == 0 && bad && !bad_sh) bad_sh = bad;
         }
         __syncthreads();
-        for (int w = tid; w < npairs * 64; w += 256) {
-            const int pr = w / 64, q = w % 64;
-            const int J = pr, I = pr + d;
-            const int r0 = (q % 8) * 4, c0 = (q / 8) * 4;
-            T acc[4][4] = {};
-            for (int l = 0; l < r0 + 4; ++l) {
-                T x[4], z[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    x[p] = W[I * 32 + l][I * 32 + r0 + p];  // W_II(r0 + p, l), 0 above the diagonal
-                    z[p] = W[I * 32 + l][J * 32 + c0 + p];  // T_IJ(l, c0 + p)
-                }
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) acc[p][t] += x[p] * z[t];
-            }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int t = 0; t < 4; ++t) W[J * 32 + c0 + t][I * 32 + r0 + p] = -acc[p][t];
+        const int R = NB - j0 - 32;
+        if (R > 0) {
+            // rows below: X = B W_jj^T, in place over B
+            cta_prod<T>(R, 32, 32, false,
+                        [&](int r, int t) { return A[j0 + t][j0 + 32 + r]; },
+                        [&](int t, int c) { return W[j0 + t][j0 + c]; },  // W_jj(c, t)
+                        [&](int r, int c, T v) { A[j0 + c][j0 + 32 + r] = v; });
+            // trailing update: A(r, c) -= sum_t X(r, t) X(c, t) on the lower part
+            cta_prod<T>(R, R, 32, true,
+                        [&](int r, int t) { return A[j0 + t][j0 + 32 + r]; },
+                        [&](int t, int c) { return A[j0 + t][j0 + 32 + c]; },
+                        [&](int r, int c, T v) {
+                            if (r >= c) A[j0 + 32 + c][j0 + 32 + r] -= v;
+                        });
         }
-        __syncthreads();
     }
-    if (tid == 0 && bad && st->chol_info == 0) st->chol_info = (int32_t)(K + bad);
+    // off-diagonal blocks of W = L^-1, level by level: for sibling blocks a
+    // (at a0) and b (at b0 = a0 + sz) of size sz,  W_ba = -W_bb L_ba W_aa.
+    // T1 = L_ba W_aa is kept in the free upper block (rows a, columns b) of W.
+    for (int sz = 32; sz < NB; sz *= 2) {
+        for (int a0 = 0; a0 < NB; a0 += 2 * sz) {
+            const int b0 = a0 + sz;
+            cta_prod<T>(sz, sz, sz, false,
+                        [&](int r, int t) { return A[a0 + t][b0 + r]; },   // L_ba(r, t)
+                        [&](int t, int c) { return W[a0 + c][a0 + t]; },   // W_aa(t, c)
+                        [&](int r, int c, T v) { W[b0 + r][a0 + c] = v; });  // T1(r, c) at (a0 + c, b0 + r)
+            cta_prod<T>(sz, sz, sz, false,
+                        [&](int r, int t) { return W[b0 + t][b0 + r]; },   // W_bb(r, t)
+                        [&](int t, int c) { return W[b0 + t][a0 + c]; },   // T1(t, c)
+                        [&](int r, int c, T v) { W[a0 + c][b0 + r] = -v; });  // W_ba(r, c)
+            // the scratch sits in the upper triangle of the next level's W_aa / W_bb
+            for (int e = tid; e < sz * sz; e += 256) W[b0 + e % sz][a0 + e / sz] = T(0);
+            __syncthreads();
+        }
+    }
+    if (tid == 0 && bad_sh && bad_sh <= kb && st->chol_info == 0) st->chol_info = (int32_t)(K + bad_sh);
     // write back: L in the lower triangle, W^T in the strict upper triangle
-    for (int e = tid; e < kb * kb; e += 256) {
-        const int c = e / kb, r = e % kb;
-        if (r >= c) S[(K + r) + (K + c) * lds] = A[c][r];
-        else S[(K + r) + (K + c) * lds] = W[r][c];  // (r, c), r < c  <-  W(c, r)
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int c = e / NB, r = e % NB;
+        if (r < kb && c < kb) S[(K + r) + (K + c) * lds] = r >= c ? A[c][r] : W[r][c];  // W(c, r) for r < c
     }
 }
 
@@ -394,7 +403,7 @@ template <typename T>
 cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st,
                             const TcPanel *tc) {
     constexpr int NB = FactorCfg<T>::NB;
-    const size_t smem_diag = 2 * sizeof(T) * NB * (NB + 1);
+    const size_t smem_diag = 2 * sizeof(T) * NB * (NB + 4);
     const size_t smem_panel = sizeof(T) * NB * (NB + 4) + sizeof(T) * NB * 68;
     cudaError_t e = cudaFuncSetAttribute(chol_diag_kernel<T, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
