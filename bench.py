@@ -35,8 +35,6 @@ WORKLOAD = ("larger_sparse: A 20000x8000 CSR, 20 nnz/row at random columns N(0,1
             "seed 20040811")
 GOLDEN = os.path.join(ROOT, "tests", "golden", "larger_sparse_20000x8000.npz")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# plain FP32 FMA issue rate: 152 SMs x 128 lanes x 2 flops per clock
-FP32_SIMT_FLOPS_PER_CLOCK = 152 * 128 * 2
 
 
 def dist_env():
@@ -121,25 +119,64 @@ def pinned_copy(a):
     return t
 
 
-def roofline(stats, peaks, sm_mhz):
-    """Roofline of the phase with the largest device time."""
-    name, st = max(((k, v) for k, v in stats.items() if v["launches"] > 0),
-                   key=lambda kv: kv[1]["ms"])
-    sec = st["ms"] * 1e-3
-    if name == "factor":
-        flops = st["flops"] / sec
-        clock = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        peak = FP32_SIMT_FLOPS_PER_CLOCK * clock
-        return {"kernel": "cholesky (chol_panel + chol_update)", "bound": "alu",
-                "achieved": flops / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": flops / peak, "traffic": None,
-                "peak_source": "FP32 FMA rate 152x128x2 per clock at the sampled SM clock",
-                "launches": st["launches"], "avg_launch_ms": st["ms"] / max(st["launches"], 1)}
-    gbs = st["bytes"] / sec / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-            "launches": st["launches"], "avg_launch_ms": st["ms"] / max(st["launches"], 1)}
+# nominal dense TF32 : BF16 tensor rate on GB300 (1.1 : 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+# the FP32 trailing update splits each operand into hi + lo TF32 parts and
+# issues three TF32 products (hi*hi, hi*lo, lo*hi) per FP32 product
+TC_SPLITS = 3
+
+
+def kernel_rooflines(stats, peaks, sm_mhz, traffic):
+    """Achieved rate of every timed kernel class against its own roof.
+
+    stats come from the per-kernel profiling pass: device time, launches and
+    the algorithmic bytes / flops each launch was charged with."""
+    clock = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    tf32 = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+    out = {}
+    for name, st in stats.items():
+        if not st["launches"] or st["ms"] <= 0:
+            continue
+        sec = st["ms"] * 1e-3
+        r = {"launches": st["launches"], "avg_launch_us": 1e3 * st["ms"] / st["launches"],
+             "ms": st["ms"]}
+        if name == "factor_update":
+            peak = tf32 / TC_SPLITS
+            r.update(bound="tensor", unit="TFLOP/s", achieved=st["flops"] / sec / 1e12, peak=peak,
+                     peak_source=("bf16_tflops_sustained of measured x 1.1/2.25 (nominal TF32:BF16) "
+                                  "/ 3 (three TF32 products per FP32 product)"))
+        elif name == "factor_diag":
+            peak = 128 * 2 * clock / 1e12  # one CTA on one SM: 128 FP32 lanes x FMA
+            r.update(bound="alu", unit="TFLOP/s", achieved=st["flops"] / sec / 1e12, peak=peak,
+                     peak_source="one SM: 128 FP32 FMA lanes x 2 flops x sampled SM clock")
+        elif name == "factor_panel":
+            peak = 152 * 128 * 2 * clock / 1e12
+            r.update(bound="alu", unit="TFLOP/s", achieved=st["flops"] / sec / 1e12, peak=peak,
+                     peak_source="152 SMs x 128 FP32 FMA lanes x 2 flops x sampled SM clock")
+        else:
+            r.update(bound="hbm", unit="GB/s", achieved=st["bytes"] / sec / 1e9,
+                     peak=peaks["hbm_gbs"], peak_source="hbm_gbs of measured")
+        r["frac"] = r["achieved"] / r["peak"]
+        r["traffic"] = traffic.get(name)
+        out[name] = r
+    return out
+
+
+def roofline(per_kernel):
+    """The bench's roofline object: the kernel class with the largest device time."""
+    name, r = max(per_kernel.items(), key=lambda kv: kv[1]["ms"])
+    keep = ("bound", "achieved", "peak", "unit", "frac", "traffic", "launches", "avg_launch_us",
+            "peak_source")
+    return dict({"kernel": KERNEL_NAMES.get(name, name)}, **{k: r[k] for k in keep})
+
+
+KERNEL_NAMES = {"factor_diag": "chol_diag_kernel", "factor_panel": "chol_panel_kernel",
+                "factor_update": "tc_update_kernel (tcgen05 3xTF32)", "trsv": "trsv_fwd/bwd_kernel",
+                "gather": "gather_kernel", "spmv": "spmv_kernel", "gram": "gram_kernel"}
+
+# DRAM bytes per launch from one ncu capture of the kernel on this workload
+# (profiles/): None until a capture of the current kernel exists.
+NCU_TRAFFIC = {}
 
 
 def kkt_violation(prob, x):
@@ -218,6 +255,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -263,7 +301,6 @@ def main():
     peaks, peak_kind = load_peaks()
 
     # ---- timed region: mixed precision, inputs resident in HBM ----
-    ctx.profile(True)
     lat, launches = [], 0
     barrier()
     with ClockSampler(local) as clk:
@@ -274,12 +311,17 @@ def main():
             launches += info.kernel_launches
         barrier()
         wall = time.perf_counter() - t0
-    stats = ctx.profile_read()
-    ctx.profile(False)
     clocks = clk.summary()
     dev_s = max_over_ranks(sum(lat) * 1e-3)
     value = ws * args.steps / dev_s
     xs = x.cpu().numpy()
+
+    # ---- per-kernel device time (separate pass: events around every kernel) ----
+    ctx.profile(True, kernels=True)
+    for _ in range(args.profile_steps):
+        ctx.solve(A, b, x_out=x, opts=mixed)
+    stats = ctx.profile_read()
+    ctx.profile(False)
 
     # ---- plain FP64 GPU path on the same problem ----
     ctx.solve(A, b, x_out=x, opts=fp64)
@@ -321,7 +363,8 @@ def main():
         acc["rel_err_vs_oracle"] = float(np.linalg.norm(xs - g["x"]) / np.linalg.norm(g["x"]))
         acc["rel_err_vs_oracle_fp64"] = float(np.linalg.norm(x64 - g["x"]) / np.linalg.norm(g["x"]))
     lat_sorted = sorted(lat)
-    rf = roofline(stats, peaks, clocks.get("sm_mhz"))
+    per_kernel = kernel_rooflines(stats, peaks, clocks.get("sm_mhz"), NCU_TRAFFIC)
+    rf = roofline(per_kernel)
     rf["peak_kind"] = peak_kind
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -340,8 +383,11 @@ def main():
         "speedup_vs_fp64": (ws * args.steps / dev_s) / (ws * args.fp64_steps / dev64),
         "accuracy": acc,
         "wall_ms_per_step": wall * 1e3 / args.steps,
-        "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in stats.items() if v["launches"]},
         "roofline": rf,
+        "kernels": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in r.items()
+                        if kk != "peak_source"}
+                    for k, r in per_kernel.items()},
+        "profile_steps": args.profile_steps,
         "e2e": {"value": ws * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),

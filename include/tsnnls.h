@@ -209,7 +209,10 @@ int tsnnls_batch_set_panel(int32_t precision, const int32_t *nb);
 #define TSNNLS_PHASE_SPMV 6      /* FP64 A x and A^T r (Eq. 5, refinement) */
 #define TSNNLS_PHASE_VECTOR 7    /* small vector kernels (gathers, updates) */
 #define TSNNLS_PHASE_LSQR 8      /* LSQR iterations on A_F */
-#define TSNNLS_NUM_PHASES 9
+#define TSNNLS_PHASE_FACTOR_DIAG 9     /* per kernel inside FACTOR: diagonal block factor + inverse */
+#define TSNNLS_PHASE_FACTOR_PANEL 10   /*   block column below it (X = B W^T) */
+#define TSNNLS_PHASE_FACTOR_UPDATE 11  /*   trailing update (tensor cores in MIXED) */
+#define TSNNLS_NUM_PHASES 12
 
 typedef struct {
     double ms;          /* summed device time */
@@ -218,7 +221,10 @@ typedef struct {
     double flops;       /* algorithmic flops */
 } tsnnls_phase_stat;
 
-/* enable != 0 turns accounting on and zeroes the counters; 0 turns it off. */
+/* enable != 0 turns accounting on and zeroes the counters; 0 turns it off.
+ * enable == 2 also times each kernel of the factorisation separately
+ * (TSNNLS_PHASE_FACTOR_DIAG/_PANEL/_UPDATE instead of TSNNLS_PHASE_FACTOR),
+ * at the cost of two events per kernel launch. */
 int tsnnls_profile_enable(tsnnls_ctx *ctx, int32_t enable);
 
 /* Copy min(count, TSNNLS_NUM_PHASES) phase records (host array). */

@@ -29,7 +29,8 @@ EXPORTS = (
     "tsnnls_queue_stats_read",
 )
 
-PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr")
+PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
+          "factor_diag", "factor_panel", "factor_update")
 
 
 class TsnnlsError(RuntimeError):
@@ -331,8 +332,11 @@ class Context:
 
     # -- per-phase device time ---------------------------------------------
 
-    def profile(self, enable=True):
-        _check(self._lib.tsnnls_profile_enable(self._h, 1 if enable else 0), "profile_enable")
+    def profile(self, enable=True, kernels=False):
+        """Per-phase device time; kernels=True times the factorisation's
+        kernels one by one (diag / panel / update)."""
+        mode = (2 if kernels else 1) if enable else 0
+        _check(self._lib.tsnnls_profile_enable(self._h, mode), "profile_enable")
 
     def profile_read(self):
         arr = (PhaseStat * len(PHASES))()

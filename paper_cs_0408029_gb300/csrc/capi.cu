@@ -289,6 +289,7 @@ int tsnnls_profile_enable(tsnnls_ctx *ctx, int32_t enable) {
     Context &c = ctx->c;
     std::lock_guard<std::mutex> g(c.solve_mu);
     c.lane0.prof = enable != 0;
+    c.lane0.prof_kernels = enable == 2;
     std::memset(c.lane0.stats, 0, sizeof(c.lane0.stats));
     return TSNNLS_OK;
 }

@@ -77,11 +77,17 @@ bool tc_panel_init(TcPanel &tc, float *xhi, float *xlo, int64_t rows);
 cudaError_t launch_tc_update(cudaStream_t s, const CUtensorMap &hi, const CUtensorMap &lo, float *S,
                              int64_t k, int64_t lds, int64_t T0, DevStatus *st);
 
+// Optional per-kernel timing hooks (profiling only).
+struct KernelTimer {
+    virtual void begin(int phase) = 0;
+    virtual void end(double bytes, double flops) = 0;
+};
+
 // In-place blocked lower Cholesky of the k x k matrix S (column-major, lds).
 // tc (FP32 only, may be NULL) selects the tensor-core trailing update.
 template <typename T>
 cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st,
-                            const TcPanel *tc = nullptr);
+                            const TcPanel *tc = nullptr, KernelTimer *kt = nullptr);
 
 // rhs <- (L L^T)^{-1} rhs with the blocked warp-level triangular solves.
 // flags/ticket: scratch of at least 2*cdiv(k,64)+2 ints.

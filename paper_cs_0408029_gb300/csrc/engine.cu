@@ -148,6 +148,13 @@ size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     return c.off + 256;
 }
 
+struct LaneTimer : KernelTimer {
+    Lane &l;
+    explicit LaneTimer(Lane &lane) : l(lane) {}
+    void begin(int phase) override { prof_begin(l, phase); }
+    void end(double bytes, double flops) override { prof_end(l, bytes, flops); }
+};
+
 struct Sync {
     Lane &l;
     cudaError_t read() {
@@ -295,9 +302,14 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 prof_begin(lane, TSNNLS_PHASE_GATHER);
                 TRY_CUDA(launch_gather<T>(s, G, ldg, F, nullptr, k, S, lds));
                 prof_end(lane, 2.0 * tri + 4.0 * k, 0.0);
-                prof_begin(lane, TSNNLS_PHASE_FACTOR);
-                TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc));
-                prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
+                if (lane.prof && lane.prof_kernels) {
+                    LaneTimer lt{lane};
+                    TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, &lt));
+                } else {
+                    prof_begin(lane, TSNNLS_PHASE_FACTOR);
+                    TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc));
+                    prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
+                }
                 // first solve: x_F = (L L^T)^{-1} c_F  (x restarts from 0)
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
                 TRY_CUDA(launch_gather_rhs<T>(s, c, F, k, rhs));

@@ -37,6 +37,7 @@ struct Lane {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // per-phase accounting (tsnnls_profile_*)
     bool prof = false;
+    bool prof_kernels = false;  // time the factorisation's kernels one by one
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<PhaseMark> marks;

@@ -249,32 +249,33 @@ __global__ void __launch_bounds__(256)
     const int64_t R0 = K + kb + (int64_t)blockIdx.x * 64;
     const int nr = (int)min((int64_t)64, k - R0);
     if (nr <= 0) return;
-    for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {
-        T v[8];
+    constexpr int LB = 16;  // loads in flight per thread
+    for (int e0 = 0; e0 < NB * NB; e0 += 256 * LB) {
+        T v[LB];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < LB; ++u) {
             const int e = e0 + u * 256 + tid;
             const int c = e / NB, l = e % NB;
             // W(c, l) for l < c is stored transposed; W(c, c) = 1 / L(c, c)
             v[u] = (c < kb && l <= c) ? S[(K + l) + (K + c) * lds] : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < LB; ++u) {
             const int e = e0 + u * 256 + tid;
             const int c = e / NB, l = e % NB;
             Wl[l][c] = (l == c && c < kb) ? T(1) / v[u] : v[u];
         }
     }
-    for (int e0 = 0; e0 < NB * 64; e0 += 256 * 8) {
-        T v[8];
+    for (int e0 = 0; e0 < NB * 64; e0 += 256 * LB) {
+        T v[LB];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < LB; ++u) {
             const int e = e0 + u * 256 + tid;
             const int l = e / 64, r = e % 64;
             v[u] = (r < nr && l < kb) ? S[(R0 + r) + (K + l) * lds] : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < LB; ++u) {
             const int e = e0 + u * 256 + tid;
             B[e / 64][e % 64] = v[u];
         }
@@ -286,10 +287,20 @@ __global__ void __launch_bounds__(256)
 #pragma unroll 4
     for (int l = 0; l < NB; ++l) {
         T x[4], w[CT];
+        if constexpr (sizeof(T) == 4) {  // 16-byte shared loads (rows are 16-byte aligned)
+            const float4 xv = *reinterpret_cast<const float4 *>(&B[l][tr * 4]);
+            x[0] = xv.x; x[1] = xv.y; x[2] = xv.z; x[3] = xv.w;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) x[p] = B[l][tr * 4 + p];
+            for (int q = 0; q < CT; q += 4) {
+                const float4 wv = *reinterpret_cast<const float4 *>(&Wl[l][tc * CT + q]);
+                w[q] = wv.x; w[q + 1] = wv.y; w[q + 2] = wv.z; w[q + 3] = wv.w;
+            }
+        } else {
 #pragma unroll
-        for (int q = 0; q < CT; ++q) w[q] = Wl[l][tc * CT + q];
+            for (int p = 0; p < 4; ++p) x[p] = B[l][tr * 4 + p];
+#pragma unroll
+            for (int q = 0; q < CT; ++q) w[q] = Wl[l][tc * CT + q];
+        }
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(256)
 
 template <typename T>
 cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st,
-                            const TcPanel *tc) {
+                            const TcPanel *tc, KernelTimer *kt) {
     constexpr int NB = FactorCfg<T>::NB;
     const size_t smem_diag = 2 * sizeof(T) * NB * (NB + 4);
     const size_t smem_panel = sizeof(T) * NB * (NB + 4) + sizeof(T) * NB * 68;
@@ -414,13 +425,22 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
     for (int64_t K = 0; K < k; K += NB) {
         const int kb = (int)std::min<int64_t>(NB, k - K);
         const int64_t below = k - K - kb;
+        // algorithmic work of each kernel (for the optional per-kernel timing)
+        const double kbd = kb, bel = (double)below;
+        if (kt) kt->begin(TSNNLS_PHASE_FACTOR_DIAG);
         chol_diag_kernel<T, NB><<<1, 256, smem_diag, s>>>(S, k, lds, K, st);
         note_launches(1);
+        if (kt) kt->end(2.0 * sizeof(T) * kbd * kbd, 2.0 * kbd * kbd * kbd / 3.0);
         if (below > 0) {
             const bool use_tc = NB == 128 && sizeof(T) == 4 && tc && tc->ok && tc->rows >= k;
+            if (kt) kt->begin(TSNNLS_PHASE_FACTOR_PANEL);
             chol_panel_kernel<T, NB><<<(unsigned)cdiv(below, 64), 256, smem_panel, s>>>(
                 S, k, lds, K, use_tc ? tc->xhi : nullptr, use_tc ? tc->xlo : nullptr);
             note_launches(1);
+            // read B and W, write X (and its hi / lo copies)
+            if (kt) kt->end(sizeof(T) * (2.0 * bel * kbd + kbd * kbd) + (use_tc ? 8.0 * bel * kbd : 0.0),
+                            bel * kbd * kbd);
+            if (kt) kt->begin(TSNNLS_PHASE_FACTOR_UPDATE);
             if (use_tc) {
                 e = launch_tc_update(s, tc->map_hi, tc->map_lo, reinterpret_cast<float *>(S), k, lds,
                                      K + kb, st);
@@ -430,15 +450,19 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
                 chol_update128_kernel<T><<<(unsigned)(t * (t + 1) / 2), 256, 0, s>>>(S, k, lds, K, kb);
                 note_launches(1);
             }
+            // read and write the lower trailing matrix once, read the panel
+            // (both copies for the tensor-core split); 2 kb flops per element
+            if (kt) kt->end(2.0 * sizeof(T) * bel * (bel + 1.0) / 2.0 + (use_tc ? 8.0 : sizeof(T)) * bel * kbd,
+                            bel * (bel + 1.0) * kbd);
         }
     }
     return cudaGetLastError();
 }
 
 template cudaError_t launch_cholesky<float>(cudaStream_t, float *, int64_t, int64_t, DevStatus *,
-                                            const TcPanel *);
+                                            const TcPanel *, KernelTimer *);
 template cudaError_t launch_cholesky<double>(cudaStream_t, double *, int64_t, int64_t, DevStatus *,
-                                             const TcPanel *);
+                                             const TcPanel *, KernelTimer *);
 
 // ---------------------------------------------------------------------------
 // Triangular solves: L z = r, then L^T w = z, in place on rhs.

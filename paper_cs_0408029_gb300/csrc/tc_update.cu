@@ -104,21 +104,18 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tri_tile_tc(int64_t b, int64_t &I, int64_t &J) {
@@ -131,12 +128,14 @@ __device__ __forceinline__ void tri_tile_tc(int64_t b, int64_t &I, int64_t &J) {
 
 constexpr int kTile = 128;                    // M = N = 128
 constexpr int kBoxBytes = 128 * 32 * 4;       // 128 rows x 32 FP32 (one 128-byte swizzle span)
-constexpr int kHalfBytes = 2 * kBoxBytes;     // 64 columns of X
-constexpr int kSmemBytes = 4 * kHalfBytes + 1024;  // A hi/lo, B hi/lo for one half, + alignment
+constexpr int kStages = 4;                    // K = 128 in four 32-column stages
+constexpr int kSmemBytes = 4 * kBoxBytes + 1024;  // A hi/lo, B hi/lo of one stage, + alignment
+// 65 KB of shared memory and 128 tensor-memory columns per CTA: three CTAs
+// share an SM, so one CTA's epilogue overlaps another's copies and MMAs.
 
 }  // namespace
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 3)
     tc_update_kernel(const __grid_constant__ CUtensorMap map_hi,
                      const __grid_constant__ CUtensorMap map_lo, float *__restrict__ S, int64_t k,
                      int64_t lds, int64_t T0, DevStatus *st) {
@@ -146,8 +145,8 @@ __global__ void __launch_bounds__(128, 1)
     __shared__ int fail_sh;
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    unsigned char *sAh = base, *sAl = base + kHalfBytes, *sBh = base + 2 * kHalfBytes,
-                  *sBl = base + 3 * kHalfBytes;
+    unsigned char *sAh = base, *sAl = base + kBoxBytes, *sBh = base + 2 * kBoxBytes,
+                  *sBl = base + 3 * kBoxBytes;
     int64_t I, J;
     tri_tile_tc(blockIdx.x, I, J);
     const int64_t r0 = T0 + I * kTile, c0 = T0 + J * kTile;
@@ -174,16 +173,14 @@ __global__ void __launch_bounds__(128, 1)
     constexpr uint32_t idesc = idesc_tf32(kTile, kTile);
 
     uint32_t parity = 0;
-    for (int h = 0; h < 2 && !fail_sh; ++h) {
+    for (int h = 0; h < kStages && !fail_sh; ++h) {
         if (tid == 0) {
-            mbar_expect_tx(&bar_tma, 4 * kHalfBytes);
-            for (int q = 0; q < 2; ++q) {
-                const int x = 64 * h + 32 * q;
-                tma_load_2d(sAh + q * kBoxBytes, &map_hi, x, (int)r0, &bar_tma);
-                tma_load_2d(sAl + q * kBoxBytes, &map_lo, x, (int)r0, &bar_tma);
-                tma_load_2d(sBh + q * kBoxBytes, &map_hi, x, (int)c0, &bar_tma);
-                tma_load_2d(sBl + q * kBoxBytes, &map_lo, x, (int)c0, &bar_tma);
-            }
+            mbar_expect_tx(&bar_tma, 4 * kBoxBytes);
+            const int x = 32 * h;
+            tma_load_2d(sAh, &map_hi, x, (int)r0, &bar_tma);
+            tma_load_2d(sAl, &map_lo, x, (int)r0, &bar_tma);
+            tma_load_2d(sBh, &map_hi, x, (int)c0, &bar_tma);
+            tma_load_2d(sBl, &map_lo, x, (int)c0, &bar_tma);
         }
         if (!mbar_wait(&bar_tma, parity)) {
             if (tid == 0) fail_sh = 1;
@@ -191,22 +188,20 @@ __global__ void __launch_bounds__(128, 1)
         }
         tc_fence_after();
         if (tid == 0) {
-            for (int q = 0; q < 2; ++q) {
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t off = q * kBoxBytes + kk * 32;  // 8 TF32 = 32 bytes of K
-                    const uint64_t ah = sdesc_sw128(smem_u32(sAh) + off);
-                    const uint64_t al = sdesc_sw128(smem_u32(sAl) + off);
-                    const uint64_t bh = sdesc_sw128(smem_u32(sBh) + off);
-                    const uint64_t bl = sdesc_sw128(smem_u32(sBl) + off);
-                    mma_tf32(tmem, ah, bh, idesc, (h | q | kk) != 0);
-                    mma_tf32(tmem, ah, bl, idesc, 1);
-                    mma_tf32(tmem, al, bh, idesc, 1);
-                }
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t off = kk * 32;  // 8 TF32 = 32 bytes of K
+                const uint64_t ah = sdesc_sw128(smem_u32(sAh) + off);
+                const uint64_t al = sdesc_sw128(smem_u32(sAl) + off);
+                const uint64_t bh = sdesc_sw128(smem_u32(sBh) + off);
+                const uint64_t bl = sdesc_sw128(smem_u32(sBl) + off);
+                mma_tf32(tmem, ah, bh, idesc, (h | kk) != 0);
+                mma_tf32(tmem, ah, bl, idesc, 1);
+                mma_tf32(tmem, al, bh, idesc, 1);
             }
             mma_commit(&bar_mma);
         }
-        // the MMAs must be done with this half's operands before the next TMA overwrites them
+        // the MMAs must be done with this stage's operands before the next TMA overwrites them
         if (!mbar_wait(&bar_mma, parity)) {
             if (tid == 0) fail_sh = 1;
             break;
@@ -223,21 +218,21 @@ __global__ void __launch_bounds__(128, 1)
         tc_fence_after();
         const int64_t row = r0 + 32 * warp + lane;
 #pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cc * 32), v);
+        for (int cc = 0; cc < 8; ++cc) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cc * 16), v);
             if (row < k) {
                 // all loads first: the stores below could alias them as far as
                 // the compiler can tell, which would serialise every update
-                float cv[32];
+                float cv[16];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = c0 + cc * 32 + j;
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t col = c0 + cc * 16 + j;
                     cv[j] = (col < k && row >= col) ? S[row + col * lds] : 0.f;
                 }
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = c0 + cc * 32 + j;
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t col = c0 + cc * 16 + j;
                     if (col < k && row >= col) S[row + col * lds] = cv[j] - v[j];
                 }
             }
