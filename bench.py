@@ -189,31 +189,48 @@ def kkt_violation(prob, x):
     return viol / np.linalg.norm(a.T @ prob.b)
 
 
-def cpu_baseline(prob, iters):
-    """The CPU oracle as it stands, single-threaded, on a bounded sample of the
-    workload: the A^T A / A^T b precompute plus the first pivot (stopped by
-    max_iter=1), minus a separate timing of the precompute alone, extrapolated
-    to a full solve with the pivot count of the GPU solve."""
+def column_subset(prob, ns):
+    """The same matrix restricted to its first ns columns (a CSR of m x ns)."""
+    import workloads
+
+    keep = prob.col_idx < ns
+    rows = np.repeat(np.arange(prob.m), np.diff(prob.row_ptr))[keep]
+    row_ptr = np.zeros(prob.m + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    return workloads.CSRProblem(prob.m, ns, np.cumsum(row_ptr), prob.col_idx[keep].copy(),
+                                prob.val[keep].copy(), prob.b.copy(), prob.x_planted[:ns].copy(),
+                                prob.name + f" (first {ns} columns)")
+
+
+def cpu_baseline(prob, pivot_ks, ns=4000, ks=2000):
+    """The CPU oracle as it stands, single-threaded, on a bounded sample of
+    the workload (a few seconds): its A^T A precompute on the first ns columns
+    (scaled by (n / ns)^2, the number of column pairs), A^T b, and its
+    Cholesky of a ks x ks principal block of A^T A (scaled by (k / ks)^3 to
+    each pivot's |F| of the GPU solve).  A full oracle solve of this problem
+    is several minutes of one core."""
     import oracle
 
     oracle.build()
+    sub = column_subset(prob, ns)
+    t_start = t0 = time.perf_counter()
+    g = oracle.gram(sub)
+    t_gram = (time.perf_counter() - t0) * (prob.n / ns) ** 2
     t0 = time.perf_counter()
-    oracle.gram(prob)
     oracle.atb(prob)
-    t_gram = time.perf_counter() - t0
+    t_atb = time.perf_counter() - t0
     t0 = time.perf_counter()
-    try:
-        oracle.bpp_solve(prob, max_iter=1, final_step=oracle.FINAL_NONE)
-    except oracle.OracleError as e:
-        if e.status != oracle.EMAXITER:
-            raise
-    t_one = time.perf_counter() - t0
-    t_pivot = max(t_one - t_gram, 1e-9)
-    t_solve = t_gram + iters * t_pivot
+    oracle.cholesky(g[:ks, :ks])
+    t_chol = time.perf_counter() - t0
+    t_piv = sum(t_chol * (k / ks) ** 3 for k in pivot_ks)
+    t_solve = t_gram + t_atb + t_piv
     return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle precompute ({t_gram:.1f}s) + first pivot ({t_pivot:.1f}s) of the "
-                       f"same 20000x8000 problem; full solve extrapolated with {iters} pivots"),
-            "sample_seconds": t_gram + t_one}
+            "sample": (f"oracle A^T A on the first {ns} of {prob.n} columns x (n/{ns})^2 "
+                       f"= {t_gram:.1f}s, A^T b {t_atb:.2f}s, Cholesky of a {ks}x{ks} block of "
+                       f"A^T A x (k/{ks})^3 over the {len(pivot_ks)} pivot sizes "
+                       f"{list(map(int, pivot_ks))} = {t_piv:.1f}s (the rest of a pivot is "
+                       f"O(k^2 + nnz)); one full solve extrapolated"),
+            "sample_seconds": time.perf_counter() - t_start}
 
 
 def run_reference(args):
@@ -223,17 +240,17 @@ def run_reference(args):
     import workloads
 
     prob = workloads.larger_sparse()
-    iters = 6
-    if os.path.exists(GOLDEN):
-        iters = int(len(np.load(GOLDEN)["trace"]))
     import oracle
 
     oracle.build()
-    for _ in range(args.warmup):  # untimed: the precompute alone
+    # the pivot sizes of the oracle's own solve of this problem (stored by
+    # tests/golden/make_golden.py, which calls only oracle/)
+    pivot_ks = [int(k) for k in np.load(GOLDEN)["trace"][:, 4]]
+    for _ in range(args.warmup):  # untimed
         oracle.atb(prob)
     samples = []
     for _ in range(args.steps):
-        cb = cpu_baseline(prob, iters)
+        cb = cpu_baseline(prob, pivot_ks)
         samples.append(1.0 / cb["value"])
     ms = 1e3 * statistics.mean(samples)
     value = 1e3 / ms
@@ -394,7 +411,8 @@ def main():
         "clocks": clocks,
     }
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob, int(info.iters))
+        # pivot sizes of the oracle's own solve (equal to the GPU trace, tested)
+        line["cpu_baseline"] = cpu_baseline(prob, [int(k) for k in np.load(GOLDEN)["trace"][:, 4]])
     ctx.close()
     print(json.dumps(line), flush=True)
 

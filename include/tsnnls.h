@@ -257,7 +257,9 @@ int tsnnls_gather(tsnnls_ctx *ctx, int32_t precision, const void *G, int64_t ldg
  * that block's inverse (L_KK^-1), which the solves use; the rest of the
  * upper triangle is untouched.  *info_out (host, may be NULL) = 0, or 1 +
  * the column of the first non-positive pivot (then the call returns
- * TSNNLS_ENOTPD). */
+ * TSNNLS_ENOTPD).  Any lds >= k is accepted; the kernels work in place when
+ * S is 16-byte aligned and lds is a multiple of 32, otherwise on a temporary
+ * aligned copy (k x round_up(k, 32) elements) that is copied back. */
 int tsnnls_cholesky(tsnnls_ctx *ctx, int32_t precision, void *S, int64_t k, int64_t lds,
                     int32_t *info_out);
 

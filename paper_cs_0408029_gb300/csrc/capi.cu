@@ -372,16 +372,36 @@ int tsnnls_cholesky(tsnnls_ctx *ctx, int32_t precision, void *S, int64_t k, int6
     cudaSetDevice(c.device);
     Lane &l = c.lane0;
     cudaError_t e = cudaMemsetAsync(l.st_dev, 0, sizeof(DevStatus), l.stream);
+    // the factor kernels want 16-byte aligned columns of a multiple of 32
+    // rows: any other layout is factored in an aligned copy and copied back
+    const size_t es = precision == TSNNLS_FP64 ? sizeof(double) : sizeof(float);
+    void *work = S;
+    int64_t ldw = lds;
+    void *copy = nullptr;
+    if (k > 0 && (lds % 32 != 0 || (reinterpret_cast<uintptr_t>(S) & 15) != 0)) {
+        ldw = round_up(k, 32);
+        if (e == cudaSuccess) e = cudaMallocAsync(&copy, es * (size_t)ldw * (size_t)k, l.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(copy, es * ldw, S, es * lds, es * k, k, cudaMemcpyDeviceToDevice, l.stream);
+        work = copy;
+    }
     float *panel = nullptr;
     TcPanel tc;
     if (e == cudaSuccess && precision != TSNNLS_FP64 && k > 0) {
         e = cudaMallocAsync(reinterpret_cast<void **>(&panel), sizeof(float) * (size_t)k * 256, l.stream);
         if (e == cudaSuccess) tc_panel_init(tc, panel, panel + (size_t)k * 128, k);
     }
+    const FactorStreams fs{l.side, l.fork, l.join};
     if (e == cudaSuccess)
-        e = precision == TSNNLS_FP64 ? launch_cholesky<double>(l.stream, (double *)S, k, lds, l.st_dev)
-                                     : launch_cholesky<float>(l.stream, (float *)S, k, lds, l.st_dev, &tc);
+        e = precision == TSNNLS_FP64
+                ? launch_cholesky<double>(l.stream, (double *)work, k, ldw, l.st_dev, nullptr, nullptr, &fs)
+                : launch_cholesky<float>(l.stream, (float *)work, k, ldw, l.st_dev, &tc, nullptr, &fs);
     if (panel) cudaFreeAsync(panel, l.stream);
+    if (copy) {
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(S, es * lds, copy, es * ldw, es * k, k, cudaMemcpyDeviceToDevice, l.stream);
+        cudaFreeAsync(copy, l.stream);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(l.st_host, l.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, l.stream);
     int st = finish(l, e);
@@ -397,17 +417,18 @@ int tsnnls_chol_solve(tsnnls_ctx *ctx, int32_t precision, const void *L, int64_t
     std::lock_guard<std::mutex> g(c.solve_mu);
     cudaSetDevice(c.device);
     Lane &l = c.lane0;
-    int32_t *flags = nullptr;
-    cudaError_t e = cudaMallocAsync(&flags, sizeof(int32_t) * (size_t)(cdiv(k, 64) + 2), l.stream);
+    void *scratch = nullptr;
+    const size_t es = precision == TSNNLS_FP64 ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaMallocAsync(&scratch, chol_solve_scratch_bytes(k, es), l.stream);
     if (e != cudaSuccess) return status_from_cuda(e);
     e = cudaMemsetAsync(l.st_dev, 0, sizeof(DevStatus), l.stream);
     if (e == cudaSuccess)
         e = precision == TSNNLS_FP64
-                ? launch_chol_solve<double>(l.stream, (const double *)L, k, lds, (double *)rhs, flags, l.st_dev)
-                : launch_chol_solve<float>(l.stream, (const float *)L, k, lds, (float *)rhs, flags, l.st_dev);
+                ? launch_chol_solve<double>(l.stream, (const double *)L, k, lds, (double *)rhs, scratch, l.st_dev)
+                : launch_chol_solve<float>(l.stream, (const float *)L, k, lds, (float *)rhs, scratch, l.st_dev);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(l.st_host, l.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, l.stream);
-    cudaFreeAsync(flags, l.stream);
+    cudaFreeAsync(scratch, l.stream);
     int st = finish(l, e);
     if (st != TSNNLS_OK) return st;
     return l.st_host->timeout ? TSNNLS_ETIMEOUT : TSNNLS_OK;

@@ -75,7 +75,7 @@ bool tc_encode_panel_map(void *buf, int64_t rows, CUtensorMap *out);
 // tensor maps cannot be encoded (the factorisation then uses the SIMT update).
 bool tc_panel_init(TcPanel &tc, float *xhi, float *xlo, int64_t rows);
 cudaError_t launch_tc_update(cudaStream_t s, const CUtensorMap &hi, const CUtensorMap &lo, float *S,
-                             int64_t k, int64_t lds, int64_t T0, DevStatus *st);
+                             int64_t k, int64_t lds, int64_t T0, DevStatus *st, int64_t tile0 = 0);
 
 // Optional per-kernel timing hooks (profiling only).
 struct KernelTimer {
@@ -85,15 +85,29 @@ struct KernelTimer {
 
 // In-place blocked lower Cholesky of the k x k matrix S (column-major, lds).
 // tc (FP32 only, may be NULL) selects the tensor-core trailing update.
+// S must be 16-byte aligned and lds a multiple of 32 (cudaErrorInvalidValue
+// otherwise, nothing launched).
+// fs (may be NULL): a second stream and two events for look-ahead, i.e. the
+// next diagonal block is updated and factored on fs->side while the rest of
+// the trailing update runs on s.  Ignored when kt is given (kernels timed one
+// by one, in order).
+struct FactorStreams {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
 template <typename T>
 cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st,
-                            const TcPanel *tc = nullptr, KernelTimer *kt = nullptr);
+                            const TcPanel *tc = nullptr, KernelTimer *kt = nullptr,
+                            const FactorStreams *fs = nullptr);
 
-// rhs <- (L L^T)^{-1} rhs with the blocked warp-level triangular solves.
-// flags/ticket: scratch of at least 2*cdiv(k,64)+2 ints.
+// rhs <- (L L^T)^{-1} rhs with the blocked chained triangular solves.
+// scratch: device memory of chol_solve_scratch_bytes(k, sizeof(T)) bytes,
+// 256-byte aligned (flags and per-CTA partial sums; its contents on entry do
+// not matter).
+size_t chol_solve_scratch_bytes(int64_t k, size_t elem);
 template <typename T>
 cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs,
-                              int32_t *flags, DevStatus *st);
+                              void *scratch, DevStatus *st);
 
 // out = alpha * M x + beta * z over a CSR (or CSC viewed as CSR of M^T).
 cudaError_t launch_spmv(cudaStream_t s, int64_t rows, const int64_t *ptr, const int32_t *idx,

@@ -87,11 +87,20 @@ int lane_create(Lane &l) {
     if (e == cudaSuccess) e = cudaMallocHost(&l.bad_host, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaEventCreate(&l.ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&l.ev1);
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&l.side, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.join, cudaEventDisableTiming);
     return status_from_cuda(e);
 }
 
 void lane_destroy(Lane &l) {
     if (l.stream) cudaStreamSynchronize(l.stream);
+    if (l.side) cudaStreamSynchronize(l.side);
+    if (l.fork) cudaEventDestroy(l.fork);
+    if (l.join) cudaEventDestroy(l.join);
+    if (l.side) cudaStreamDestroy(l.side);
     if (l.ev0) cudaEventDestroy(l.ev0);
     if (l.ev1) cudaEventDestroy(l.ev1);
     for (cudaEvent_t e : l.ev_pool) cudaEventDestroy(e);
@@ -140,7 +149,7 @@ size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     c.take<T>(n);                                   // rhs
     c.take<uint8_t>(n);
     c.take<int32_t>(n);
-    c.take<int32_t>(cdiv(n, 64) + 2);
+    c.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
     if (sizeof(T) == 4) {
         c.take<float>((size_t)n * 128);  // K-major hi / lo panel copies for the tensor-core update
         c.take<float>((size_t)n * 128);
@@ -240,7 +249,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         T *rhs = cv.take<T>(n);
         uint8_t *inF = cv.take<uint8_t>(n);
         int32_t *F = cv.take<int32_t>(n);
-        int32_t *flags = cv.take<int32_t>(cdiv(n, 64) + 2);
+        void *trsv_scratch = cv.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
         TcPanel tc;
         if (sizeof(T) == 4) {
             float *xhi = cv.take<float>((size_t)n * 128);
@@ -307,7 +316,8 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                     TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, &lt));
                 } else {
                     prof_begin(lane, TSNNLS_PHASE_FACTOR);
-                    TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc));
+                    const FactorStreams fs{lane.side, lane.fork, lane.join};
+                    TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, nullptr, &fs));
                     prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
                 }
                 // first solve: x_F = (L L^T)^{-1} c_F  (x restarts from 0)
@@ -315,7 +325,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 TRY_CUDA(launch_gather_rhs<T>(s, c, F, k, rhs));
                 prof_end(lane, (12.0 + sizeof(T)) * k, 0.0);
                 prof_begin(lane, TSNNLS_PHASE_TRSV);
-                TRY_CUDA(launch_chol_solve<T>(s, S, k, lds, rhs, flags, lane.st_dev));
+                TRY_CUDA(launch_chol_solve<T>(s, S, k, lds, rhs, trsv_scratch, lane.st_dev));
                 prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * k, 2.0 * (double)k * (double)k);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
                 TRY_CUDA(launch_update_x<T>(s, rhs, F, k, x, lane.st_dev));
@@ -341,7 +351,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 TRY_CUDA(launch_gather_rhs<T>(s, sv, F, k, rhs));
                 prof_end(lane, (12.0 + sizeof(T)) * k, 0.0);
                 prof_begin(lane, TSNNLS_PHASE_TRSV);
-                TRY_CUDA(launch_chol_solve<T>(s, S, k, lds, rhs, flags, lane.st_dev));
+                TRY_CUDA(launch_chol_solve<T>(s, S, k, lds, rhs, trsv_scratch, lane.st_dev));
                 prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * k, 2.0 * (double)k * (double)k);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
                 TRY_CUDA(launch_update_x<T>(s, rhs, F, k, x, lane.st_dev));

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include <cuda/atomic>
 
 #include "common.cuh"
@@ -44,25 +46,45 @@ __device__ __forceinline__ void tri_tile2(int64_t b, int64_t &I, int64_t &J) {
 }
 
 // ---------------------------------------------------------------------------
-// diag: factor + invert the NB x NB diagonal block (one CTA of 256 threads)
+// ---- 4-element vector access (16-byte aligned) --------------------------------
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+    const float4 f = *reinterpret_cast<const float4 *>(p);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+    const double2 f = *reinterpret_cast<const double2 *>(p);
+    const double2 g = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = f.x; v[1] = f.y; v[2] = g.x; v[3] = g.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+}
 
 // ---- warp-level 32 x 32 factor + inverse -------------------------------------
-// Lane i holds row i of the block (a[32]); step J, fully unrolled through
-// template recursion so that every register index is a compile-time
-// constant:  L(J, J) = sqrt(a_J[J]), L(i, J) = a_i[J] / L(J, J), and
-// a_i[l] -= L(i, J) L(l, J) for J < l <= i.  The same shuffles of column J
-// drive the inverse, lane c holding column c of W = L^-1:
-//   W(J, c) = (delta_Jc - acc_c[J]) / L(J, J),  acc_c[l] += L(l, J) W(J, c)  (l > J).
+// Lane i holds row i of the block (a[32]) and column i of W = L^-1 (w[32]);
+// step J, fully unrolled through template recursion so that every register
+// index is a compile-time constant:
+//   L(J, J) = sqrt(a_J[J]),  L(i, J) = a_i[J] / L(J, J),
+//   a_i[l] -= L(i, J) L(l, J)                      for J < l <= i;
+// the same column J drives the inverse by forward substitution, w[l]
+// (l > J) accumulating sum_{t <= J} L(l, t) W(t, c) until step l:
+//   W(J, c) = (delta_Jc - w[J]) / L(J, J),  w[l] += L(l, J) W(J, c).
+// Column J reaches every lane through a 32-entry shared buffer (one store
+// per lane, broadcast vector loads), double-buffered by the parity of J.
 template <typename T>
 struct WarpChol {
-    T a[32], acc[32], w[32];
+    T a[32], w[32];
 };
 
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
 template <typename T, int J>
-__device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, int lane, int &bad, int base) {
+__device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, T (*col)[32], int lane, int &bad, int base) {
     T d = __shfl_sync(0xffffffffu, s.a[J], J);
     if (!(d > T(0))) {
         if (!bad) bad = base + J + 1;
@@ -71,70 +93,93 @@ __device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, int lane, int &ba
     const T inv = rsqrt_t(d);
     const T lij = (lane > J) ? s.a[J] * inv : (lane == J ? d * inv : s.a[J]);
     s.a[J] = lij;
-    const T wj = (J >= lane) ? (((J == lane) ? T(1) : T(0)) - s.acc[J]) * inv : T(0);
+    const T wj = (J >= lane) ? (((J == lane) ? T(1) : T(0)) - s.w[J]) * inv : T(0);
     s.w[J] = wj;
+    if constexpr (J + 1 < 32) {
+        col[J & 1][lane] = lij;
+        __syncwarp();
 #pragma unroll
-    for (int l = J + 1; l < 32; ++l) {
-        const T llj = __shfl_sync(0xffffffffu, lij, l);
-        if (lane >= l) s.a[l] -= lij * llj;
-        s.acc[l] += llj * wj;
+        for (int g = (J + 1) / 4; g < 8; ++g) {
+            T v[4];
+            ld4(&col[J & 1][4 * g], v);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = 4 * g + u;
+                if (l > J) {
+                    if (lane >= l) s.a[l] -= lij * v[u];
+                    s.w[l] += v[u] * wj;
+                }
+            }
+        }
+        warp_chol_step<T, J + 1>(s, col, lane, bad, base);
     }
-    if constexpr (J + 1 < 32) warp_chol_step<T, J + 1>(s, lane, bad, base);
 }
 
-// Factor A(j0.., j0..) (32 x 32, lower) in place and write its inverse to W.
+// Factor A(j0.., j0..) (32 x 32, lower) in place and write its inverse to W
+// (W[col][row]) and, transposed, to the strict upper triangle of the block
+// in A.  col: 2 x 32 shared scratch, 16-byte aligned.
 template <typename T, int NB>
-__device__ __forceinline__ void warp_chol_inv(T (*A)[NB + 4], T (*W)[NB + 4], int j0, int lane,
-                                              int &bad) {
+__device__ __forceinline__ void warp_chol_inv(T (*A)[NB + 4], T (*W)[NB + 4], T (*col)[32], int j0,
+                                              int lane, int &bad) {
     WarpChol<T> s;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
         s.a[c] = c <= lane ? A[j0 + c][j0 + lane] : T(0);
-        s.acc[c] = T(0);
+        s.w[c] = T(0);
     }
-    warp_chol_step<T, 0>(s, lane, bad, j0);
+    warp_chol_step<T, 0>(s, col, lane, bad, j0);
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
-        if (c <= lane) A[j0 + c][j0 + lane] = s.a[c];
+        A[j0 + c][j0 + lane] = c <= lane ? s.a[c] : s.w[c];  // L, and W(c, lane) above the diagonal
         W[j0 + lane][j0 + c] = s.w[c];  // column `lane` of W, rows c (0 above the diagonal)
     }
 }
 
 // ---- CTA-level small products on shared-memory blocks -------------------------
-// out(r, c) = sum_{t < K} X(r, t) Y(t, c) for r < M, c < N (multiples of 4),
-// 4 x 4 register tiles, at most 256 tiles (one per thread); tri: only the
-// lower tiles (r block >= c block) of a square output.  All reads happen
-// before the barrier, all writes (fo) after it, so the output may overwrite
-// a source.
-template <typename T, typename FX, typename FY, typename FO>
-__device__ __forceinline__ void cta_prod(int M, int N, int K, bool tri, FX fx, FY fy, FO fo) {
+// For each of nb independent products:  out(r, c) = sum_{t < K} X(r, t) Y(t, c),
+// r < M, c < N (multiples of 4), in 4 x 4 register tiles, one per thread and
+// wave of 256.  fx(b, r0, t, x) loads X(r0..r0+3, t), fy(b, t, c0, y) loads
+// Y(t, c0..c0+3), fo(b, r0, c0, acc) stores the tile, fr(b, r0, c0, t0, t1)
+// may narrow the sum to t0 <= t < t1 (zeros of a triangular factor).  tri: only the lower
+// tiles (row block >= column block) of a square output.  All reads of a wave
+// happen before the barrier and all writes after it, so an output that fits
+// in one wave may overwrite a source.
+struct FullRange {
+    __device__ void operator()(int, int, int, int &, int &) const {}
+};
+
+template <typename T, typename FX, typename FY, typename FO, typename FR = FullRange>
+__device__ __forceinline__ void cta_prod(int nb, int M, int N, int K, bool tri, FX fx, FY fy, FO fo,
+                                         FR fr = FR()) {
     const int tid = threadIdx.x;
     const int nt_r = M / 4, nt_c = N / 4;
-    const int ntiles = tri ? nt_r * (nt_r + 1) / 2 : nt_r * nt_c;
-    // waves of 256 tiles; an output that overwrites a source must fit in one
+    const int per = tri ? nt_r * (nt_r + 1) / 2 : nt_r * nt_c;
+    const int ntiles = nb * per;
     for (int base = 0; base < ntiles; base += 256) {
         const int tile = base + tid;
         const bool active = tile < ntiles;
         T acc[4][4] = {};
-        int tr = 0, tc = 0;
+        int bi = 0, tr = 0, tc = 0;
         if (active) {
+            bi = tile / per;
+            const int lt = tile - bi * per;
             if (tri) {
-                int i = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
-                while (i * (i + 1) / 2 > tile) --i;
-                while ((i + 1) * (i + 2) / 2 <= tile) ++i;
+                int i = (int)((sqrtf(8.f * lt + 1.f) - 1.f) * 0.5f);
+                while (i * (i + 1) / 2 > lt) --i;
+                while ((i + 1) * (i + 2) / 2 <= lt) ++i;
                 tr = i;
-                tc = tile - i * (i + 1) / 2;
+                tc = lt - i * (i + 1) / 2;
             } else {
-                tr = tile % nt_r;
-                tc = tile / nt_r;
+                tr = lt % nt_r;
+                tc = lt / nt_r;
             }
-            for (int t = 0; t < K; ++t) {
+            int t0 = 0, t1 = K;
+            fr(bi, tr * 4, tc * 4, t0, t1);  // narrower t-range where a factor is triangular
+#pragma unroll 4
+            for (int t = t0; t < t1; ++t) {
                 T x[4], y[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    x[p] = fx(tr * 4 + p, t);
-                    y[p] = fy(t, tc * 4 + p);
-                }
+                fx(bi, tr * 4, t, x);
+                fy(bi, t, tc * 4, y);
 #pragma unroll
                 for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -142,16 +187,18 @@ __device__ __forceinline__ void cta_prod(int M, int N, int K, bool tri, FX fx, F
             }
         }
         __syncthreads();
-        if (active) {
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) fo(tr * 4 + p, tc * 4 + q, acc[p][q]);
-        }
+        if (active) fo(bi, tr * 4, tc * 4, acc);
         __syncthreads();
     }
 }
 
+// ---- diag: factor + invert the NB x NB diagonal block (one CTA, 256 threads)
+// Shared memory: A[col][row] holds the block (then L), W[col][row] = L^-1.
+// For each 32-column block jb: warp 0 factors and inverts the 32 x 32
+// diagonal block, the CTA forms X = B W_jj^T for the rows below it (in place)
+// and subtracts X X^T from the trailing lower triangle.  The off-diagonal
+// blocks of W follow level by level: for sibling blocks a, b of size sz,
+// W_ba = -W_bb (L_ba W_aa).
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
     chol_diag_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, DevStatus *st) {
@@ -159,25 +206,41 @@ __global__ void __launch_bounds__(256)
     T(*A)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);                              // A[col][row]
     T(*W)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw + sizeof(T) * NB * (NB + 4));  // W[col][row]
     __shared__ int bad_sh;
+    __shared__ __align__(16) T col[2][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int kb = (int)min((int64_t)NB, k - K);
     if (tid == 0) bad_sh = 0;
-    // load the lower triangle; pad beyond kb with the identity; W starts at 0
-    // (eight loads in flight per thread before any shared-memory store)
-    for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {
-        T v[8];
+    // load the lower triangle in 4-row vectors (all in flight before any
+    // shared-memory store); rows >= kb read zero, the identity pads the
+    // diagonal beyond kb; W starts at 0.  Columns hold lds >= K + kb rows
+    // rounded up to 32, so a vector that starts below kb stays inside them.
+    constexpr int NV = NB * NB / 4 / 256;  // vectors per thread
+    {
+        T v[NV][4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * 256 + tid;
+        for (int u = 0; u < NV; ++u) {
+            const int e = (u * 256 + tid) * 4;
             const int c = e / NB, r = e % NB;
-            v[u] = (r >= c && r < kb && c < kb) ? S[(K + r) + (K + c) * lds] : T(0);
+            if (c < kb && r < kb && r + 3 >= c) {
+                ld4(&S[(K + r) + (K + c) * lds], v[u]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[u][q] = T(0);
+            }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * 256 + tid;
+        for (int u = 0; u < NV; ++u) {
+            const int e = (u * 256 + tid) * 4;
             const int c = e / NB, r = e % NB;
-            A[c][r] = (r == c && r >= kb) ? T(1) : v[u];
-            W[c][r] = T(0);
+            T o[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int rr = r + q;
+                o[q] = (rr == c && rr >= kb) ? T(1) : ((rr >= c && rr < kb) ? v[u][q] : T(0));
+            }
+            st4(&A[c][r], o);
+            const T z[4] = {T(0), T(0), T(0), T(0)};
+            st4(&W[c][r], z);
         }
     }
     __syncthreads();
@@ -186,50 +249,115 @@ __global__ void __launch_bounds__(256)
         const int j0 = jb * 32;
         if (warp == 0) {
             int bad = 0;
-            warp_chol_inv<T, NB>(A, W, j0, lane, bad);
+            warp_chol_inv<T, NB>(A, W, col, j0, lane, bad);
             if (lane == 0 && bad && !bad_sh) bad_sh = bad;
         }
         __syncthreads();
         const int R = NB - j0 - 32;
         if (R > 0) {
             // rows below: X = B W_jj^T, in place over B
-            cta_prod<T>(R, 32, 32, false,
-                        [&](int r, int t) { return A[j0 + t][j0 + 32 + r]; },
-                        [&](int t, int c) { return W[j0 + t][j0 + c]; },  // W_jj(c, t)
-                        [&](int r, int c, T v) { A[j0 + c][j0 + 32 + r] = v; });
+            cta_prod<T>(
+                1, R, 32, 32, false,
+                [&](int, int r0, int t, T(&x)[4]) { ld4(&A[j0 + t][j0 + 32 + r0], x); },
+                [&](int, int t, int c0, T(&y)[4]) { ld4(&W[j0 + t][j0 + c0], y); },  // W_jj(c, t)
+                [&](int, int r0, int c0, T(&acc)[4][4]) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const T o[4] = {acc[0][q], acc[1][q], acc[2][q], acc[3][q]};
+                        st4(&A[j0 + c0 + q][j0 + 32 + r0], o);
+                    }
+                },
+                [](int, int, int c0, int &, int &t1) { t1 = c0 + 4; });  // W_jj(c, t) = 0 for t > c
             // trailing update: A(r, c) -= sum_t X(r, t) X(c, t) on the lower part
-            cta_prod<T>(R, R, 32, true,
-                        [&](int r, int t) { return A[j0 + t][j0 + 32 + r]; },
-                        [&](int t, int c) { return A[j0 + t][j0 + 32 + c]; },
-                        [&](int r, int c, T v) {
-                            if (r >= c) A[j0 + 32 + c][j0 + 32 + r] -= v;
-                        });
+            cta_prod<T>(
+                1, R, R, 32, true,
+                [&](int, int r0, int t, T(&x)[4]) { ld4(&A[j0 + t][j0 + 32 + r0], x); },
+                [&](int, int t, int c0, T(&y)[4]) { ld4(&A[j0 + t][j0 + 32 + c0], y); },
+                [&](int, int r0, int c0, T(&acc)[4][4]) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        T *col = &A[j0 + 32 + c0 + q][j0 + 32 + r0];
+                        T o[4];
+                        ld4(col, o);
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+                            if (r0 + p >= c0 + q) o[p] -= acc[p][q];
+                        st4(col, o);
+                    }
+                });
         }
     }
-    // off-diagonal blocks of W = L^-1, level by level: for sibling blocks a
-    // (at a0) and b (at b0 = a0 + sz) of size sz,  W_ba = -W_bb L_ba W_aa.
-    // T1 = L_ba W_aa is kept in the free upper block (rows a, columns b) of W.
+    // off-diagonal blocks of W = L^-1, level by level, all pairs of a level
+    // at once: T1 = L_ba W_aa goes to the free upper block (rows a, columns
+    // b) of W, then W_ba = -W_bb T1, then the scratch is cleared (it lies in
+    // the upper triangle of the next level's diagonal blocks).
     for (int sz = 32; sz < NB; sz *= 2) {
-        for (int a0 = 0; a0 < NB; a0 += 2 * sz) {
-            const int b0 = a0 + sz;
-            cta_prod<T>(sz, sz, sz, false,
-                        [&](int r, int t) { return A[a0 + t][b0 + r]; },   // L_ba(r, t)
-                        [&](int t, int c) { return W[a0 + c][a0 + t]; },   // W_aa(t, c)
-                        [&](int r, int c, T v) { W[b0 + r][a0 + c] = v; });  // T1(r, c) at (a0 + c, b0 + r)
-            cta_prod<T>(sz, sz, sz, false,
-                        [&](int r, int t) { return W[b0 + t][b0 + r]; },   // W_bb(r, t)
-                        [&](int t, int c) { return W[b0 + t][a0 + c]; },   // T1(t, c)
-                        [&](int r, int c, T v) { W[a0 + c][b0 + r] = -v; });  // W_ba(r, c)
-            // the scratch sits in the upper triangle of the next level's W_aa / W_bb
-            for (int e = tid; e < sz * sz; e += 256) W[b0 + e % sz][a0 + e / sz] = T(0);
-            __syncthreads();
+        const int npair = NB / (2 * sz);
+        cta_prod<T>(
+            npair, sz, sz, sz, false,
+            [&](int p, int r0, int t, T(&x)[4]) {  // L_ba(r, t)
+                const int a0 = 2 * sz * p, b0 = a0 + sz;
+                ld4(&A[a0 + t][b0 + r0], x);
+            },
+            [&](int p, int t, int c0, T(&y)[4]) {  // W_aa(t, c)
+                const int a0 = 2 * sz * p;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) y[q] = W[a0 + c0 + q][a0 + t];
+            },
+            [&](int p, int r0, int c0, T(&acc)[4][4]) {  // T1(r, c) at W[b0 + r][a0 + c]
+                const int a0 = 2 * sz * p, b0 = a0 + sz;
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) st4(&W[b0 + r0 + pp][a0 + c0], acc[pp]);
+            },
+            [](int, int, int c0, int &t0, int &) { t0 = c0; });  // W_aa(t, c) = 0 for t < c
+        cta_prod<T>(
+            npair, sz, sz, sz, false,
+            [&](int p, int r0, int t, T(&x)[4]) {  // W_bb(r, t)
+                const int b0 = 2 * sz * p + sz;
+                ld4(&W[b0 + t][b0 + r0], x);
+            },
+            [&](int p, int t, int c0, T(&y)[4]) {  // T1(t, c)
+                const int a0 = 2 * sz * p, b0 = a0 + sz;
+                ld4(&W[b0 + t][a0 + c0], y);
+            },
+            [&](int p, int r0, int c0, T(&acc)[4][4]) {  // W_ba(r, c) at W[a0 + c][b0 + r]
+                const int a0 = 2 * sz * p, b0 = a0 + sz;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const T o[4] = {-acc[0][q], -acc[1][q], -acc[2][q], -acc[3][q]};
+                    st4(&W[a0 + c0 + q][b0 + r0], o);
+                }
+                // and transposed into the strict upper triangle of A: S(a0 + c, b0 + r)
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    const T o[4] = {-acc[pp][0], -acc[pp][1], -acc[pp][2], -acc[pp][3]};
+                    st4(&A[b0 + r0 + pp][a0 + c0], o);
+                }
+            },
+            [](int, int r0, int, int &, int &t1) { t1 = r0 + 4; });  // W_bb(r, t) = 0 for t > r
+        for (int e = tid; e < npair * sz * sz / 4; e += 256) {
+            const int p = e / (sz * sz / 4), f = e % (sz * sz / 4);
+            const int a0 = 2 * sz * p, b0 = a0 + sz;
+            const T z[4] = {T(0), T(0), T(0), T(0)};
+            st4(&W[b0 + f / (sz / 4)][a0 + (f % (sz / 4)) * 4], z);
         }
+        __syncthreads();
     }
     if (tid == 0 && bad_sh && bad_sh <= kb && st->chol_info == 0) st->chol_info = (int32_t)(K + bad_sh);
-    // write back: L in the lower triangle, W^T in the strict upper triangle
-    for (int e = tid; e < NB * NB; e += 256) {
+    // write back the block as A now holds it: L in the lower triangle, W^T
+    // in the strict upper triangle (W(c, r) for r < c), in 4-row vectors; a
+    // vector that crosses kb is written element by element
+    for (int e = tid * 4; e < NB * NB; e += 256 * 4) {
         const int c = e / NB, r = e % NB;
-        if (r < kb && c < kb) S[(K + r) + (K + c) * lds] = r >= c ? A[c][r] : W[r][c];  // W(c, r) for r < c
+        if (c >= kb || r >= kb) continue;
+        T o[4];
+        ld4(&A[c][r], o);
+        T *dst = &S[(K + r) + (K + c) * lds];
+        if (r + 3 < kb) {
+            st4(dst, o);
+        } else {
+            for (int q = 0; q < 4 && r + q < kb; ++q) dst[q] = o[q];
+        }
     }
 }
 
@@ -249,35 +377,64 @@ __global__ void __launch_bounds__(256)
     const int64_t R0 = K + kb + (int64_t)blockIdx.x * 64;
     const int nr = (int)min((int64_t)64, k - R0);
     if (nr <= 0) return;
-    constexpr int LB = 16;  // loads in flight per thread
-    for (int e0 = 0; e0 < NB * NB; e0 += 256 * LB) {
-        T v[LB];
+    // W: thread -> column c of the stored block, 8 consecutive rows l (two
+    // 4-vectors, one 32-byte sector in FP32); column c holds W(c, l) for l < c
+    // and L(c, c) on the diagonal, so Wl[l][c] = W(c, l) with W(c, c) =
+    // 1 / L(c, c).  Rows stay below K + kb rounded up to 8 <= lds.
+    constexpr int NW = NB * NB / 8 / 256;  // 8-row chunks of W per thread
+    constexpr int NBV = NB * 64 / 4 / 256; // 4-row vectors of B per thread
+    {
+        T v[NW][8];
 #pragma unroll
-        for (int u = 0; u < LB; ++u) {
-            const int e = e0 + u * 256 + tid;
-            const int c = e / NB, l = e % NB;
-            // W(c, l) for l < c is stored transposed; W(c, c) = 1 / L(c, c)
-            v[u] = (c < kb && l <= c) ? S[(K + l) + (K + c) * lds] : T(0);
+        for (int u = 0; u < NW; ++u) {
+            const int e = u * 256 + tid;
+            const int c = e % NB, l0 = (e / NB) * 8;
+            if (c < kb && l0 <= c) {
+                const T *src = &S[(K + l0) + (K + c) * lds];
+                T lo4[4], hi4[4];
+                ld4(src, lo4);
+                ld4(src + 4, hi4);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v[u][q] = lo4[q];
+                    v[u][4 + q] = hi4[q];
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[u][q] = T(0);
+            }
+        }
+        // B: thread -> column l, 4 consecutive rows (coalesced down the column)
+        T bv[NBV][4];
+#pragma unroll
+        for (int u = 0; u < NBV; ++u) {
+            const int e = u * 256 + tid;
+            const int l = e / 16, r0 = (e % 16) * 4;
+            if (l < kb && r0 < nr) {
+                ld4(&S[(R0 + r0) + (K + l) * lds], bv[u]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) bv[u][q] = T(0);
+            }
         }
 #pragma unroll
-        for (int u = 0; u < LB; ++u) {
-            const int e = e0 + u * 256 + tid;
-            const int c = e / NB, l = e % NB;
-            Wl[l][c] = (l == c && c < kb) ? T(1) / v[u] : v[u];
-        }
-    }
-    for (int e0 = 0; e0 < NB * 64; e0 += 256 * LB) {
-        T v[LB];
+        for (int u = 0; u < NW; ++u) {
+            const int e = u * 256 + tid;
+            const int c = e % NB, l0 = (e / NB) * 8;
 #pragma unroll
-        for (int u = 0; u < LB; ++u) {
-            const int e = e0 + u * 256 + tid;
-            const int l = e / 64, r = e % 64;
-            v[u] = (r < nr && l < kb) ? S[(R0 + r) + (K + l) * lds] : T(0);
+            for (int q = 0; q < 8; ++q) {
+                const int l = l0 + q;
+                Wl[l][c] = (c >= kb || l > c) ? T(0) : (l == c ? T(1) / v[u][q] : v[u][q]);
+            }
         }
 #pragma unroll
-        for (int u = 0; u < LB; ++u) {
-            const int e = e0 + u * 256 + tid;
-            B[e / 64][e % 64] = v[u];
+        for (int u = 0; u < NBV; ++u) {
+            const int e = u * 256 + tid;
+            const int l = e / 16, r0 = (e % 16) * 4;
+            T o[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = r0 + q < nr ? bv[u][q] : T(0);
+            st4(&B[l][r0], o);
         }
     }
     __syncthreads();
@@ -306,14 +463,19 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int q = 0; q < CT; ++q) acc[p][q] += x[p] * w[q];
     }
+    const int r0 = tr * 4;
 #pragma unroll
     for (int q = 0; q < CT; ++q) {
         const int c = tc * CT + q;
         if (c >= kb) continue;
+        T *dst = &S[(R0 + r0) + (K + c) * lds];
+        const T o[4] = {acc[0][q], acc[1][q], acc[2][q], acc[3][q]};
+        if (r0 + 3 < nr) {
+            st4(dst, o);
+        } else {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int r = tr * 4 + p;
-            if (r < nr) S[(R0 + r) + (K + c) * lds] = acc[p][q];
+            for (int p = 0; p < 4; ++p)
+                if (r0 + p < nr) dst[p] = o[p];
         }
     }
     if (xhi) {
@@ -321,15 +483,19 @@ __global__ void __launch_bounds__(256)
         // top 10 mantissa bits (exact in TF32), lo = x - hi is exact in FP32
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-            const int r = tr * 4 + p;
+            const int r = r0 + p;
             if (r >= nr) continue;
 #pragma unroll
-            for (int q = 0; q < CT; ++q) {
-                const int c = tc * CT + q;
-                const float v = (float)acc[p][q];
-                const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-                xhi[(R0 + r) * 128 + c] = hi;
-                xlo[(R0 + r) * 128 + c] = v - hi;
+            for (int q = 0; q < CT; q += 4) {
+                float h4[4], l4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float v = (float)acc[p][q + u];
+                    h4[u] = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+                    l4[u] = v - h4[u];
+                }
+                st4(&xhi[(R0 + r) * 128 + tc * CT + q], h4);
+                st4(&xlo[(R0 + r) * 128 + tc * CT + q], l4);
             }
         }
     }
@@ -342,13 +508,13 @@ __global__ void __launch_bounds__(256)
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-    chol_update128_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, int kb) {
+    chol_update128_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, int kb, int64_t tile0) {
     constexpr int BM = 128, BK = 8;
     __shared__ __align__(16) T As[2][BK][BM];
     __shared__ __align__(16) T Bs[2][BK][BM];
     const int64_t T0 = K + kb;
     int64_t I, J;
-    tri_tile2(blockIdx.x, I, J);
+    tri_tile2(blockIdx.x + tile0, I, J);  // tiles before tile0 are done elsewhere
     const int64_t r0 = T0 + I * BM, c0 = T0 + J * BM;
     if (r0 >= k) return;
     const int tid = threadIdx.x;
@@ -410,10 +576,68 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ---------------------------------------------------------------------------
+// look-ahead: step K's contribution to the first 128 x 128 tile of the
+// trailing matrix (which holds the next diagonal block) alone,
+//     C(Kn.., Kn..) -= X X^T,  X = S(Kn .. Kn + 128, K .. K + NB)  (lower part),
+// so the next diagonal block can be factored while the update kernels, which
+// skip that tile, do the rest.  One CTA per lower 32 x 32 sub-block (10),
+// 2 x 2 outputs per thread.
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+    chol_tile_update_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, int64_t Kn) {
+    __shared__ __align__(16) T Xr[NB][36];  // Xr[t][r] = X(rb + r, t)
+    __shared__ __align__(16) T Xc[NB][36];  // Xc[t][c] = X(cb + c, t)
+    int64_t I, J;
+    tri_tile2(blockIdx.x, I, J);
+    const int kb = (int)min((int64_t)128, k - Kn);  // the update kernels' tile size
+    const int rb = (int)I * 32, cb = (int)J * 32;
+    if (rb >= kb) return;
+    const int tid = threadIdx.x;
+    constexpr int NL = NB * 32 / 256;  // elements of each operand per thread, all loads in flight
+    T vr[NL], vc[NL];
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+        const int e = u * 256 + tid;
+        const int t = e / 32, r = e % 32;
+        vr[u] = rb + r < kb ? S[(Kn + rb + r) + (K + t) * lds] : T(0);
+        vc[u] = cb + r < kb ? S[(Kn + cb + r) + (K + t) * lds] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+        const int e = u * 256 + tid;
+        Xr[e / 32][e % 32] = vr[u];
+        Xc[e / 32][e % 32] = vc[u];
+    }
+    __syncthreads();
+    const int rr = (tid % 16) * 2, cc = (tid / 16) * 2;
+    T a00 = T(0), a01 = T(0), a10 = T(0), a11 = T(0);
+#pragma unroll 8
+    for (int t = 0; t < NB; ++t) {
+        const T x0 = Xr[t][rr], x1 = Xr[t][rr + 1], y0 = Xc[t][cc], y1 = Xc[t][cc + 1];
+        a00 += x0 * y0;
+        a01 += x0 * y1;
+        a10 += x1 * y0;
+        a11 += x1 * y1;
+    }
+    const T acc[2][2] = {{a00, a01}, {a10, a11}};
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int gr = rb + rr + p, gc = cb + cc + q;
+            if (gr < kb && gc < kb && gr >= gc) S[(Kn + gr) + (Kn + gc) * lds] -= acc[p][q];
+        }
+}
+
 template <typename T>
 cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st,
-                            const TcPanel *tc, KernelTimer *kt) {
+                            const TcPanel *tc, KernelTimer *kt, const FactorStreams *fs) {
     constexpr int NB = FactorCfg<T>::NB;
+    // the kernels move 4-element vectors: columns must start 16-byte aligned
+    // and hold whole 32-row groups (reads run up to K + kb rounded up to 8)
+    if (k > 0 && (lds % 32 != 0 || (reinterpret_cast<uintptr_t>(S) & 15) != 0)) return cudaErrorInvalidValue;
     const size_t smem_diag = 2 * sizeof(T) * NB * (NB + 4);
     const size_t smem_panel = sizeof(T) * NB * (NB + 4) + sizeof(T) * NB * 68;
     cudaError_t e = cudaFuncSetAttribute(chol_diag_kernel<T, NB>,
@@ -422,15 +646,18 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
         e = cudaFuncSetAttribute(chol_panel_kernel<T, NB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel);
     if (e != cudaSuccess) return e;
+    const bool ahead = fs != nullptr && kt == nullptr;
     for (int64_t K = 0; K < k; K += NB) {
         const int kb = (int)std::min<int64_t>(NB, k - K);
         const int64_t below = k - K - kb;
         // algorithmic work of each kernel (for the optional per-kernel timing)
         const double kbd = kb, bel = (double)below;
-        if (kt) kt->begin(TSNNLS_PHASE_FACTOR_DIAG);
-        chol_diag_kernel<T, NB><<<1, 256, smem_diag, s>>>(S, k, lds, K, st);
-        note_launches(1);
-        if (kt) kt->end(2.0 * sizeof(T) * kbd * kbd, 2.0 * kbd * kbd * kbd / 3.0);
+        if (!ahead || K == 0) {  // with look-ahead, later diagonal blocks run on the side stream
+            if (kt) kt->begin(TSNNLS_PHASE_FACTOR_DIAG);
+            chol_diag_kernel<T, NB><<<1, 256, smem_diag, s>>>(S, k, lds, K, st);
+            note_launches(1);
+            if (kt) kt->end(2.0 * sizeof(T) * kbd * kbd, 2.0 * kbd * kbd * kbd / 3.0);
+        }
         if (below > 0) {
             const bool use_tc = NB == 128 && sizeof(T) == 4 && tc && tc->ok && tc->rows >= k;
             if (kt) kt->begin(TSNNLS_PHASE_FACTOR_PANEL);
@@ -440,40 +667,79 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
             // read B and W, write X (and its hi / lo copies)
             if (kt) kt->end(sizeof(T) * (2.0 * bel * kbd + kbd * kbd) + (use_tc ? 8.0 * bel * kbd : 0.0),
                             bel * kbd * kbd);
+            int64_t tile0 = 0;
+            if (ahead) {
+                // next diagonal block: its share of this step's update, then
+                // its factor, on the side stream; the trailing update skips it
+                const int64_t Kn = K + NB;
+                e = cudaEventRecord(fs->fork, s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(fs->side, fs->fork, 0);
+                if (e != cudaSuccess) return e;
+                chol_tile_update_kernel<T, NB><<<10, 256, 0, fs->side>>>(S, k, lds, K, Kn);
+                chol_diag_kernel<T, NB><<<1, 256, smem_diag, fs->side>>>(S, k, lds, Kn, st);
+                note_launches(2);
+                e = cudaEventRecord(fs->join, fs->side);
+                if (e != cudaSuccess) return e;
+                tile0 = 1;
+            }
             if (kt) kt->begin(TSNNLS_PHASE_FACTOR_UPDATE);
             if (use_tc) {
                 e = launch_tc_update(s, tc->map_hi, tc->map_lo, reinterpret_cast<float *>(S), k, lds,
-                                     K + kb, st);
+                                     K + kb, st, tile0);
                 if (e != cudaSuccess) return e;
             } else {
                 const int64_t t = cdiv(below, 128);
-                chol_update128_kernel<T><<<(unsigned)(t * (t + 1) / 2), 256, 0, s>>>(S, k, lds, K, kb);
-                note_launches(1);
+                const int64_t tiles = t * (t + 1) / 2 - tile0;
+                if (tiles > 0) {
+                    chol_update128_kernel<T><<<(unsigned)tiles, 256, 0, s>>>(S, k, lds, K, kb, tile0);
+                    note_launches(1);
+                }
             }
             // read and write the lower trailing matrix once, read the panel
             // (both copies for the tensor-core split); 2 kb flops per element
             if (kt) kt->end(2.0 * sizeof(T) * bel * (bel + 1.0) / 2.0 + (use_tc ? 8.0 : sizeof(T)) * bel * kbd,
                             bel * (bel + 1.0) * kbd);
+            if (ahead) {
+                e = cudaStreamWaitEvent(s, fs->join, 0);
+                if (e != cudaSuccess) return e;
+            }
         }
     }
     return cudaGetLastError();
 }
 
 template cudaError_t launch_cholesky<float>(cudaStream_t, float *, int64_t, int64_t, DevStatus *,
-                                            const TcPanel *, KernelTimer *);
+                                            const TcPanel *, KernelTimer *, const FactorStreams *);
 template cudaError_t launch_cholesky<double>(cudaStream_t, double *, int64_t, int64_t, DevStatus *,
-                                             const TcPanel *, KernelTimer *);
+                                             const TcPanel *, KernelTimer *, const FactorStreams *);
 
 // ---------------------------------------------------------------------------
 // Triangular solves: L z = r, then L^T w = z, in place on rhs.
 //
-// One CTA per NB-row block.  CTAs take their block from a ticket counter in
-// launch order, so a CTA only waits on blocks whose CTAs already run.  While
-// it waits for block j, a CTA already holds its tile of L for block j in
-// registers; when the flag appears it adds that product, and after the last
-// block it forms z_i = W_i (r_i - sum) with the stored inverse and publishes
-// z_i with a release flag.  Every wait is bounded: on timeout the CTA raises
-// the launch's abort flag and st->timeout and all CTAs return.
+// Block row i of a solve needs the m off-diagonal tiles of its row (L_ij,
+// j < i, forward; L_ji^T, j > i, backward) times the already solved blocks
+// z_j, then z_i = W_i (r_i - sum) with the stored diagonal-block inverse.
+// The row is shared out by distance d from the diagonal (d = 0 nearest):
+//   helpers    the far part of the row (d >= 4) in at most 8 contiguous
+//              segments; each multiplies its tiles as their z_j appear,
+//              writes its partial vector to its own slot and counts itself
+//              done;
+//   finisher   first collects the helpers' partials (their z_j are at least
+//              four links old, so this is off the chain), then takes d < 4
+//              as each z_j appears, solves the diagonal block and publishes
+//              z_i.
+// So the chain from z_{i-1} to z_i is one tile product and the diagonal
+// solve, and long rows stream through many SMs.  In FP32 a solved entry is
+// published as one 64-bit word (tag 1 in the high half, the value's bits in
+// the low half) in a buffer cleared before the launch: a consumer polls the
+// words it needs directly, one round trip, with no flag and no fence on the
+// chain.  FP64 values do not fit beside a tag; they go through rhs with a
+// fence and a per-block release flag.
+// CTAs draw tickets in launch order; every row's helpers come before its
+// finisher and rows come in solve order, so a CTA only ever waits on CTAs
+// with smaller tickets, which are running or done.  Every wait is bounded:
+// on timeout the CTA raises the launch's abort flag and st->timeout, and all
+// CTAs return.
 
 __device__ __forceinline__ int flag_load(const int32_t *p) {
     cuda::atomic_ref<const int32_t, cuda::thread_scope_device> a(*p);
@@ -483,13 +749,26 @@ __device__ __forceinline__ void flag_store(int32_t *p, int v) {
     cuda::atomic_ref<int32_t, cuda::thread_scope_device> a(*p);
     a.store(v, cuda::memory_order_release);
 }
+__device__ __forceinline__ void count_add(int32_t *p) {
+    cuda::atomic_ref<int32_t, cuda::thread_scope_device> a(*p);
+    a.fetch_add(1, cuda::memory_order_release);
+}
+__device__ __forceinline__ uint64_t word_load(const uint64_t *p) {
+    cuda::atomic_ref<const uint64_t, cuda::thread_scope_device> a(*p);
+    return a.load(cuda::memory_order_relaxed);
+}
+__device__ __forceinline__ void word_store(uint64_t *p, uint64_t v) {
+    cuda::atomic_ref<uint64_t, cuda::thread_scope_device> a(*p);
+    a.store(v, cuda::memory_order_relaxed);
+}
 
-__device__ __forceinline__ bool wait_flag(const int32_t *flags, int32_t *abort_flag, int j,
-                                          DevStatus *st, int *sh_ok) {
+// Thread 0 polls until *p >= target (bounded), the CTA learns the outcome.
+__device__ __forceinline__ bool wait_at_least(const int32_t *p, int target, int32_t *abort_flag,
+                                              DevStatus *st, int *sh_ok) {
     if (threadIdx.x == 0) {
         int ok = 1;
         int spins = 0;
-        while (flag_load(flags + j) == 0) {
+        while (flag_load(p) < target) {
             if (flag_load(abort_flag) != 0) { ok = 0; break; }
             if (++spins > kSpinLimit) {
                 flag_store(abort_flag, 1);
@@ -505,68 +784,244 @@ __device__ __forceinline__ bool wait_flag(const int32_t *flags, int32_t *abort_f
     return *sh_ok != 0;
 }
 
+constexpr int kTrsvSeg = 4;      // tiles kept by the finisher, and the helpers' target length
+constexpr int kTrsvHelpers = 8;  // helpers per row at most
+
+__host__ __device__ constexpr int trsv_helpers(int m) {
+    return m > kTrsvSeg ? ((m - kTrsvSeg + kTrsvSeg - 1) / kTrsvSeg < kTrsvHelpers
+                               ? (m - kTrsvSeg + kTrsvSeg - 1) / kTrsvSeg
+                               : kTrsvHelpers)
+                        : 0;
+}
+
+int64_t trsv_ctas(int64_t nblk) {
+    int64_t t = 0;
+    for (int64_t m = 0; m < nblk; ++m) t += 1 + trsv_helpers((int)m);
+    return t;
+}
+
+// Scratch: done[nblk], helper counts[nblk], ticket, abort, then (FP32) one
+// 64-bit word per row -- all zeroed before each launch -- then one NB-vector
+// partial slot per CTA.
+static int64_t trsv_zeroed_bytes(int64_t nblk, int64_t nb, size_t elem) {
+    const int64_t flags = round_up(4 * (2 * nblk + 2), 256);
+    return flags + (elem == sizeof(float) ? round_up(8 * nblk * nb, 256) : 0);
+}
+
+size_t chol_solve_scratch_bytes(int64_t k, size_t elem) {
+    const int64_t nb = elem == sizeof(float) ? FactorCfg<float>::NB : FactorCfg<double>::NB;
+    const int64_t nblk = cdiv(std::max<int64_t>(k, 1), nb);
+    return (size_t)trsv_zeroed_bytes(nblk, nb, elem) + (size_t)trsv_ctas(nblk) * (size_t)nb * elem;
+}
+
+struct TrsvRole {
+    int i;           // block row
+    int m;           // off-diagonal tiles in the row
+    int nh;          // helpers of the row
+    int d_lo, d_hi;  // this CTA's distances [d_lo, d_hi)
+    bool finisher;
+    int64_t base;    // ticket of the row's first CTA (the helpers' slots follow it)
+};
+
+__device__ __forceinline__ TrsvRole trsv_role(int64_t t, int nblk, bool fwd) {
+    TrsvRole r{};
+    int64_t base = 0;
+    for (int q = 0; q < nblk; ++q) {
+        const int i = fwd ? q : nblk - 1 - q;
+        const int m = fwd ? i : nblk - 1 - i;
+        const int nh = trsv_helpers(m);
+        if (t < base + nh + 1) {
+            const int mf = m < kTrsvSeg ? m : kTrsvSeg;
+            const int local = (int)(t - base);
+            r.i = i;
+            r.m = m;
+            r.nh = nh;
+            r.base = base;
+            r.finisher = local == nh;
+            if (r.finisher) {
+                r.d_lo = 0;
+                r.d_hi = mf;
+            } else {
+                const int rem = m - mf, lh = (rem + nh - 1) / nh;
+                const int h = nh - 1 - local;  // farthest segment first
+                r.d_lo = min(m, mf + h * lh);
+                r.d_hi = min(m, mf + (h + 1) * lh);
+            }
+            return r;
+        }
+        base += nh + 1;
+    }
+    r.i = -1;
+    return r;
+}
+
+template <typename T, int NB>
+struct TrsvScratch {
+    int32_t *done, *hcnt, *ticket, *abort_flag;
+    uint64_t *words;  // FP32: published entries (tag << 32 | bits)
+    T *part;
+    int nblk;
+};
+
+template <typename T, int NB>
+__host__ TrsvScratch<T, NB> trsv_scratch(void *base, int64_t k) {
+    TrsvScratch<T, NB> s;
+    s.nblk = (int)cdiv(k, NB);
+    s.done = static_cast<int32_t *>(base);
+    s.hcnt = s.done + s.nblk;
+    s.ticket = s.hcnt + s.nblk;
+    s.abort_flag = s.ticket + 1;
+    char *p = static_cast<char *>(base) + round_up(4 * (2 * (int64_t)s.nblk + 2), 256);
+    s.words = sizeof(T) == sizeof(float) ? reinterpret_cast<uint64_t *>(p) : nullptr;
+    s.part = reinterpret_cast<T *>(static_cast<char *>(base) + trsv_zeroed_bytes(s.nblk, NB, sizeof(T)));
+    return s;
+}
+
+// zs[0..NB) <- solved block j (nvalid entries, zeros beyond), once available.
+// Uniform across the CTA; false when the launch was aborted or a wait timed out.
+template <typename T, int NB>
+__device__ __forceinline__ bool trsv_get(const TrsvScratch<T, NB> &sc, const T *rhs, int j, int nvalid,
+                                         T *zs, DevStatus *st, int *sh_ok) {
+    const int tid = threadIdx.x;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        int ok = 1;
+        if (tid < NB) {
+            T v = T(0);
+            if (tid < nvalid) {
+                const uint64_t *w = sc.words + (int64_t)j * NB + tid;
+                uint64_t x;
+                int spins = 0;
+                while (((x = word_load(w)) >> 32) == 0) {
+                    if (++spins > kSpinLimit) {
+                        flag_store(sc.abort_flag, 1);
+                        st->timeout = 1;
+                        ok = 0;
+                        break;
+                    }
+                    if ((spins & 63) == 0) {
+                        if (flag_load(sc.abort_flag) != 0) { ok = 0; break; }
+                        __nanosleep(32);
+                    }
+                }
+                v = ok ? __uint_as_float((uint32_t)x) : T(0);
+            }
+            zs[tid] = v;
+        }
+        return __syncthreads_and(ok) != 0;
+    } else {
+        if (!wait_at_least(sc.done + j, 1, sc.abort_flag, st, sh_ok)) return false;
+        if (tid < NB) zs[tid] = tid < nvalid ? __ldcg(rhs + (int64_t)j * NB + tid) : T(0);
+        __syncthreads();
+        return true;
+    }
+}
+
+// Publish the nr entries of solved block i (thread tid holds entry tid).
+template <typename T, int NB>
+__device__ __forceinline__ void trsv_put(const TrsvScratch<T, NB> &sc, T *rhs, int i, int nr, T z) {
+    const int tid = threadIdx.x;
+    const int64_t row0 = (int64_t)i * NB;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (tid < nr) {
+            rhs[row0 + tid] = z;
+            word_store(sc.words + row0 + tid, (uint64_t(1) << 32) | __float_as_uint(z));
+        }
+    } else {
+        if (tid < nr) {
+            rhs[row0 + tid] = z;
+            __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0) flag_store(sc.done + i, 1);
+    }
+}
+
 // Forward: thread (r = tid % NB, part = tid / NB) owns row r and a slice of
 // NB / P columns of every tile, P = 256 / NB parts.
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
-    trsv_fwd_kernel(const T *__restrict__ L, int64_t k, int64_t lds, T *rhs, int32_t *flags,
-                    int32_t *ticket, int32_t *abort_flag, DevStatus *st) {
+    trsv_fwd_kernel(const T *__restrict__ L, int64_t k, int64_t lds, T *rhs, TrsvScratch<T, NB> sc,
+                    DevStatus *st) {
     constexpr int P = 256 / NB, CW = NB / P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T(*Ws)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);  // Ws[l][r] = W(r, l)
     __shared__ T zs[NB];
     __shared__ T red[P][NB];
-    __shared__ int blk_sh, ok_sh;
+    __shared__ int64_t tk_sh;
+    __shared__ int ok_sh;
     const int tid = threadIdx.x;
-    if (tid == 0) blk_sh = atomicAdd(ticket, 1);
+    if (tid == 0) tk_sh = atomicAdd(sc.ticket, 1);
     __syncthreads();
-    const int i = blk_sh;
+    const int64_t tk = tk_sh;
+    const TrsvRole ro = trsv_role(tk, sc.nblk, true);
+    if (ro.i < 0) return;
+    const int i = ro.i;
     const int64_t row0 = (int64_t)i * NB;
     const int nr = (int)min((int64_t)NB, k - row0);
     const int r = tid % NB, part = tid / NB;
-    for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {  // coalesced reads of the stored W^T
-        T v[8];
+    // tiles in the order their z_j appear: j = i - 1 - d, d from d_hi - 1 down
+    T tile[CW];
+    auto fetch = [&](int j) {
+        if (r < nr) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * 256 + tid;
-            const int rr = e / NB, l = e % NB;
-            v[u] = (rr < nr && l <= rr) ? L[(row0 + l) + (row0 + rr) * lds] : T(0);
+            for (int c = 0; c < CW; ++c) tile[c] = L[(row0 + r) + ((int64_t)j * NB + part * CW + c) * lds];
         }
+    };
+    if (ro.d_hi > ro.d_lo) fetch(i - ro.d_hi);
+    T ri = T(0), hsum = T(0);
+    if (ro.finisher) {
+        if (tid < nr) ri = rhs[row0 + tid];
+        for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {  // coalesced reads of the stored W^T
+            T v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * 256 + tid;
-            const int rr = e / NB, l = e % NB;
-            Ws[l][rr] = (l == rr && rr < nr) ? T(1) / v[u] : v[u];
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * 256 + tid;
+                const int rr = e / NB, l = e % NB;
+                v[u] = (rr < nr && l <= rr) ? L[(row0 + l) + (row0 + rr) * lds] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * 256 + tid;
+                const int rr = e / NB, l = e % NB;
+                Ws[l][rr] = (l == rr && rr < nr) ? T(1) / v[u] : v[u];
+            }
+        }
+        if (ro.nh > 0) {
+            if (!wait_at_least(sc.hcnt + i, ro.nh, sc.abort_flag, st, &ok_sh)) return;
+            if (tid < NB)
+                for (int h = 0; h < ro.nh; ++h) hsum += __ldcg(sc.part + (ro.base + h) * NB + tid);
         }
     }
     T acc = T(0);
-    T tile[CW];
-    if (i > 0 && r < nr) {
-#pragma unroll
-        for (int c = 0; c < CW; ++c) tile[c] = L[(row0 + r) + (int64_t)(part * CW + c) * lds];
-    }
-    for (int j = 0; j < i; ++j) {
-        if (!wait_flag(flags, abort_flag, j, st, &ok_sh)) return;
-        if (tid < NB) zs[tid] = __ldcg(rhs + (int64_t)j * NB + tid);
-        __syncthreads();
+    for (int d = ro.d_hi - 1; d >= ro.d_lo; --d) {
+        const int j = i - 1 - d;
+        if (!trsv_get<T, NB>(sc, rhs, j, NB, zs, st, &ok_sh)) return;
         if (r < nr) {
 #pragma unroll
             for (int c = 0; c < CW; ++c) acc += tile[c] * zs[part * CW + c];
-            if (j + 1 < i) {
-#pragma unroll
-                for (int c = 0; c < CW; ++c)
-                    tile[c] = L[(row0 + r) + ((int64_t)(j + 1) * NB + part * CW + c) * lds];
-            }
         }
+        if (d > ro.d_lo) fetch(j + 1);
         __syncthreads();
     }
     red[part][r] = acc;
     __syncthreads();
+    if (!ro.finisher) {
+        if (tid < NB) {
+            T sum = T(0);
+#pragma unroll
+            for (int q = 0; q < P; ++q) sum += red[q][tid];
+            sc.part[tk * NB + tid] = sum;
+            __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0) count_add(sc.hcnt + i);
+        return;
+    }
     if (tid < NB) {
-        T sum = T(0);
+        T sum = hsum;
 #pragma unroll
         for (int q = 0; q < P; ++q) sum += red[q][tid];
-        zs[tid] = tid < nr ? rhs[row0 + tid] - sum : T(0);
+        zs[tid] = tid < nr ? ri - sum : T(0);
     }
     __syncthreads();
     T z = T(0);
@@ -574,15 +1029,12 @@ __global__ void __launch_bounds__(256)
     for (int c = 0; c < CW; ++c) z += Ws[part * CW + c][r] * zs[part * CW + c];
     red[part][r] = z;
     __syncthreads();
+    T zi = T(0);
     if (tid < nr) {
-        T sum = T(0);
 #pragma unroll
-        for (int q = 0; q < P; ++q) sum += red[q][tid];
-        rhs[row0 + tid] = sum;
-        __threadfence();
+        for (int q = 0; q < P; ++q) zi += red[q][tid];
     }
-    __syncthreads();
-    if (tid == 0) flag_store(flags + i, 1);
+    trsv_put<T, NB>(sc, rhs, i, nr, zi);
 }
 
 // Backward: (L^T)(row0 + r, jr0 + c) = L(jr0 + c, row0 + r).  Warp w owns the
@@ -590,8 +1042,8 @@ __global__ void __launch_bounds__(256)
 // column (coalesced) and reduce by shuffles.
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
-    trsv_bwd_kernel(const T *__restrict__ L, int64_t k, int64_t lds, T *rhs, int32_t *flags,
-                    int32_t *ticket, int32_t *abort_flag, int nblk, DevStatus *st) {
+    trsv_bwd_kernel(const T *__restrict__ L, int64_t k, int64_t lds, T *rhs, TrsvScratch<T, NB> sc,
+                    DevStatus *st) {
     constexpr int CPW = NB / 8;   // columns per warp
     constexpr int RPL = NB / 32;  // rows per lane per column
     constexpr int P = 256 / NB, CW = NB / P;
@@ -600,31 +1052,17 @@ __global__ void __launch_bounds__(256)
     __shared__ T ws[NB];
     __shared__ T accs[NB];
     __shared__ T red[P][NB];
-    __shared__ int blk_sh, ok_sh;
+    __shared__ int64_t tk_sh;
+    __shared__ int ok_sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) blk_sh = nblk - 1 - atomicAdd(ticket, 1);
+    if (tid == 0) tk_sh = atomicAdd(sc.ticket, 1);
     __syncthreads();
-    const int i = blk_sh;
+    const int64_t tk = tk_sh;
+    const TrsvRole ro = trsv_role(tk, sc.nblk, false);
+    if (ro.i < 0) return;
+    const int i = ro.i;
     const int64_t row0 = (int64_t)i * NB;
     const int nr = (int)min((int64_t)NB, k - row0);
-    for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {  // coalesced reads of the stored W^T
-        T v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * 256 + tid;
-            const int rr = e / NB, l = e % NB;
-            v[u] = (rr < nr && l <= rr) ? L[(row0 + l) + (row0 + rr) * lds] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * 256 + tid;
-            const int rr = e / NB, l = e % NB;
-            Ws[l][rr] = (l == rr && rr < nr) ? T(1) / v[u] : v[u];
-        }
-    }
-    T acc[CPW];
-#pragma unroll
-    for (int q = 0; q < CPW; ++q) acc[q] = T(0);
     T tile[CPW][RPL];
     auto fetch = [&](int j) {
         const int64_t jr0 = (int64_t)j * NB;
@@ -639,13 +1077,39 @@ __global__ void __launch_bounds__(256)
             }
         }
     };
-    if (i + 1 < nblk) fetch(nblk - 1);
-    for (int j = nblk - 1; j > i; --j) {
-        if (!wait_flag(flags, abort_flag, j, st, &ok_sh)) return;
-        const int64_t jr0 = (int64_t)j * NB;
-        const int njr = (int)min((int64_t)NB, k - jr0);
-        if (tid < NB) ws[tid] = tid < njr ? __ldcg(rhs + jr0 + tid) : T(0);
-        __syncthreads();
+    // tiles in the order their w_j appear: j = i + 1 + d, d from d_hi - 1 down
+    if (ro.d_hi > ro.d_lo) fetch(i + ro.d_hi);
+    T ri = T(0), hsum = T(0);
+    if (ro.finisher) {
+        if (tid < nr) ri = rhs[row0 + tid];
+        for (int e0 = 0; e0 < NB * NB; e0 += 256 * 8) {  // coalesced reads of the stored W^T
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * 256 + tid;
+                const int rr = e / NB, l = e % NB;
+                v[u] = (rr < nr && l <= rr) ? L[(row0 + l) + (row0 + rr) * lds] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * 256 + tid;
+                const int rr = e / NB, l = e % NB;
+                Ws[l][rr] = (l == rr && rr < nr) ? T(1) / v[u] : v[u];
+            }
+        }
+        if (ro.nh > 0) {
+            if (!wait_at_least(sc.hcnt + i, ro.nh, sc.abort_flag, st, &ok_sh)) return;
+            if (tid < NB)
+                for (int h = 0; h < ro.nh; ++h) hsum += __ldcg(sc.part + (ro.base + h) * NB + tid);
+        }
+    }
+    T acc[CPW];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) acc[q] = T(0);
+    for (int d = ro.d_hi - 1; d >= ro.d_lo; --d) {
+        const int j = i + 1 + d;
+        const int njr = (int)min((int64_t)NB, k - (int64_t)j * NB);
+        if (!trsv_get<T, NB>(sc, rhs, j, njr, ws, st, &ok_sh)) return;
 #pragma unroll
         for (int q = 0; q < CPW; ++q) {
             T s = T(0);
@@ -653,7 +1117,7 @@ __global__ void __launch_bounds__(256)
             for (int t = 0; t < RPL; ++t) s += tile[q][t] * ws[lane + 32 * t];
             acc[q] += s;
         }
-        if (j - 1 > i) fetch(j - 1);
+        if (d > ro.d_lo) fetch(j - 1);
         __syncthreads();
     }
 #pragma unroll
@@ -664,7 +1128,16 @@ __global__ void __launch_bounds__(256)
         if (lane == 0) accs[warp + 8 * q] = s;
     }
     __syncthreads();
-    if (tid < NB) ws[tid] = tid < nr ? rhs[row0 + tid] - accs[tid] : T(0);
+    if (!ro.finisher) {
+        if (tid < NB) {
+            sc.part[tk * NB + tid] = accs[tid];
+            __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0) count_add(sc.hcnt + i);
+        return;
+    }
+    if (tid < NB) ws[tid] = tid < nr ? ri - (accs[tid] + hsum) : T(0);
     __syncthreads();
     // w_i = W^T ws: w(r) = sum_{l >= r} W(l, r) ws(l) = sum_l Ws[r][l] ws(l)
     const int r = tid % NB, part = tid / NB;
@@ -673,46 +1146,43 @@ __global__ void __launch_bounds__(256)
     for (int c = 0; c < CW; ++c) w += Ws[r][part * CW + c] * ws[part * CW + c];
     red[part][r] = w;
     __syncthreads();
+    T wi = T(0);
     if (tid < nr) {
-        T sum = T(0);
 #pragma unroll
-        for (int q = 0; q < P; ++q) sum += red[q][tid];
-        rhs[row0 + tid] = sum;
-        __threadfence();
+        for (int q = 0; q < P; ++q) wi += red[q][tid];
     }
-    __syncthreads();
-    if (tid == 0) flag_store(flags + i, 1);
+    trsv_put<T, NB>(sc, rhs, i, nr, wi);
 }
 
 template <typename T>
-cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs,
-                              int32_t *flags, DevStatus *st) {
+cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
+                              DevStatus *st) {
     constexpr int NB = FactorCfg<T>::NB;
     if (k <= 0) return cudaSuccess;
-    const int nblk = (int)cdiv(k, NB);
-    // flags[0..nblk) block done, flags[nblk] ticket, flags[nblk+1] abort
-    const size_t bytes = sizeof(int32_t) * (size_t)(nblk + 2);
+    const TrsvScratch<T, NB> sc = trsv_scratch<T, NB>(scratch, k);
+    const int64_t ctas = trsv_ctas(sc.nblk);
+    // flags, ticket, abort and the published words start at zero for each pass
+    const size_t bytes = (size_t)trsv_zeroed_bytes(sc.nblk, NB, sizeof(T));
     const size_t smem = sizeof(T) * NB * (NB + 1);
     cudaError_t e = cudaFuncSetAttribute(trsv_fwd_kernel<T, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(trsv_bwd_kernel<T, NB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc.done, 0, bytes, s);
     if (e != cudaSuccess) return e;
-    trsv_fwd_kernel<T, NB><<<nblk, 256, smem, s>>>(L, k, lds, rhs, flags, flags + nblk, flags + nblk + 1, st);
+    trsv_fwd_kernel<T, NB><<<(unsigned)ctas, 256, smem, s>>>(L, k, lds, rhs, sc, st);
     note_launches(1);
-    e = cudaMemsetAsync(flags, 0, bytes, s);
+    e = cudaMemsetAsync(sc.done, 0, bytes, s);
     if (e != cudaSuccess) return e;
-    trsv_bwd_kernel<T, NB><<<nblk, 256, smem, s>>>(L, k, lds, rhs, flags, flags + nblk, flags + nblk + 1,
-                                                   nblk, st);
+    trsv_bwd_kernel<T, NB><<<(unsigned)ctas, 256, smem, s>>>(L, k, lds, rhs, sc, st);
     note_launches(1);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_chol_solve<float>(cudaStream_t, const float *, int64_t, int64_t,
-                                              float *, int32_t *, DevStatus *);
+                                              float *, void *, DevStatus *);
 template cudaError_t launch_chol_solve<double>(cudaStream_t, const double *, int64_t, int64_t,
-                                               double *, int32_t *, DevStatus *);
+                                               double *, void *, DevStatus *);
 
 }  // namespace tsnnls

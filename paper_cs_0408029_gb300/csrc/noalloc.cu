@@ -1,11 +1,13 @@
 // Allocation-free variant of the factor solve (tsnnls_chol_solve_noalloc).
 //
-// The blocked triangular solves need a little global scratch: one "block
-// done" flag per 64-row block, a ticket counter and an abort flag, plus a
-// status word that records a timed-out wait.  tsnnls_chol_solve takes that
-// scratch from its context, which allocates device memory.  This variant
-// keeps it in a file-scope __device__ array instead, so a caller that must
-// not allocate device memory can still run the solve on its own buffers.
+// The blocked triangular solves need global scratch: per block row a "done"
+// flag and a helper count, a ticket counter and an abort flag, one partial
+// vector per CTA (chol_solve_scratch_bytes), plus a status word that records
+// a timed-out wait.  tsnnls_chol_solve takes that scratch from its context,
+// which allocates device memory.  This variant keeps it in a file-scope
+// __device__ array instead (about 5.3 MB, sized for the largest k accepted),
+// so a caller that must not allocate device memory can still run the solve
+// on its own buffers.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,11 +19,18 @@
 namespace tsnnls {
 namespace {
 
-// Largest k accepted: 65536 rows, i.e. 1024 blocks of 64 rows.
+// Largest k accepted: 65536 rows, i.e. 1024 blocks of 64 rows (FP64) or
+// 512 of 128 (FP32).  The solve's scratch for that k is bounded by the
+// flags, one 64-bit published word per row (FP32 only) and at most nine
+// CTAs (a finisher and eight helpers) per block row, each with one partial
+// vector of a block's rows (the FP64 partials bound the FP32 ones).
+// chol_solve_scratch_bytes gives the exact figure, checked against this
+// bound on every call.
 constexpr int64_t kNoAllocMaxK = TSNNLS_NOALLOC_MAX_K;
 constexpr int64_t kNoAllocBlocks = kNoAllocMaxK / 64;
-// flags[0..blocks) + ticket + abort, rounded up, then one DevStatus.
-constexpr size_t kFlagBytes = sizeof(int32_t) * (size_t)((kNoAllocBlocks + 2 + 63) / 64 * 64);
+constexpr size_t kFlagBytes = (size_t)((4 * (2 * kNoAllocBlocks + 2) + 255) / 256 * 256) +
+                              (size_t)kNoAllocMaxK * 8 +  // FP32: one published word per row
+                              (size_t)kNoAllocBlocks * 9 * 64 * sizeof(double);
 constexpr size_t kScratchBytes = kFlagBytes + sizeof(DevStatus);
 
 // Shared by every call on a device; it keeps the last call's contents.
@@ -64,7 +73,9 @@ extern "C" int tsnnls_chol_solve_noalloc(int32_t precision, const void *L, int64
     void *base = nullptr;
     int st = scratch_for_current_device(&base);
     if (st != TSNNLS_OK) return st;
-    int32_t *flags = static_cast<int32_t *>(base);
+    const size_t need = chol_solve_scratch_bytes(k, precision == TSNNLS_FP64 ? sizeof(double) : sizeof(float));
+    if (need > kFlagBytes) return TSNNLS_EINVAL;
+    void *flags = base;
     DevStatus *status = reinterpret_cast<DevStatus *>(static_cast<char *>(base) + kFlagBytes);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The flags are cleared by the solve launcher itself; the status word

@@ -138,7 +138,7 @@ constexpr int kSmemBytes = 4 * kBoxBytes + 1024;  // A hi/lo, B hi/lo of one sta
 __global__ void __launch_bounds__(128, 3)
     tc_update_kernel(const __grid_constant__ CUtensorMap map_hi,
                      const __grid_constant__ CUtensorMap map_lo, float *__restrict__ S, int64_t k,
-                     int64_t lds, int64_t T0, DevStatus *st) {
+                     int64_t lds, int64_t T0, DevStatus *st, int64_t tile0) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t bar_tma, bar_mma;
     __shared__ uint32_t tmem_sh;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(128, 3)
     unsigned char *sAh = base, *sAl = base + kBoxBytes, *sBh = base + 2 * kBoxBytes,
                   *sBl = base + 3 * kBoxBytes;
     int64_t I, J;
-    tri_tile_tc(blockIdx.x, I, J);
+    tri_tile_tc(blockIdx.x + tile0, I, J);  // tiles before tile0 are done elsewhere
     const int64_t r0 = T0 + I * kTile, c0 = T0 + J * kTile;
     if (r0 >= k) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -171,6 +171,19 @@ __global__ void __launch_bounds__(128, 3)
     tc_fence_after();
     const uint32_t tmem = tmem_sh;
     constexpr uint32_t idesc = idesc_tf32(kTile, kTile);
+    // Each thread owns one row of the tile in the epilogue; its first 16
+    // values of C are loaded now, so their latency hides behind the MMAs
+    // (this CTA is the only writer of its tile while the kernel runs).
+    const int64_t row = r0 + 32 * warp + lane;
+    auto load_c = [&](int cc, float (&cv)[16]) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int64_t col = c0 + cc * 16 + j;
+            cv[j] = (row < k && col < k && row >= col) ? S[row + col * lds] : 0.f;
+        }
+    };
+    float cur[16];
+    load_c(0, cur);
 
     uint32_t parity = 0;
     for (int h = 0; h < kStages && !fail_sh; ++h) {
@@ -216,26 +229,24 @@ __global__ void __launch_bounds__(128, 3)
         mbar_wait(&bar_mma, parity);
     } else {
         tc_fence_after();
-        const int64_t row = r0 + 32 * warp + lane;
+        // chunk cc + 1 of C is loaded before chunk cc is stored: all loads of
+        // a chunk are issued ahead of stores that, as far as the compiler can
+        // tell, could alias them
 #pragma unroll 1
         for (int cc = 0; cc < 8; ++cc) {
+            float nxt[16];
+            if (cc + 1 < 8) load_c(cc + 1, nxt);
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cc * 16), v);
             if (row < k) {
-                // all loads first: the stores below could alias them as far as
-                // the compiler can tell, which would serialise every update
-                float cv[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int64_t col = c0 + cc * 16 + j;
-                    cv[j] = (col < k && row >= col) ? S[row + col * lds] : 0.f;
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int64_t col = c0 + cc * 16 + j;
-                    if (col < k && row >= col) S[row + col * lds] = cv[j] - v[j];
+                    if (col < k && row >= col) S[row + col * lds] = cur[j] - v[j];
                 }
             }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) cur[j] = nxt[j];
         }
     }
     tc_fence_before();
@@ -294,7 +305,7 @@ bool tc_panel_init(TcPanel &tc, float *xhi, float *xlo, int64_t rows) {
 }
 
 cudaError_t launch_tc_update(cudaStream_t s, const CUtensorMap &hi, const CUtensorMap &lo, float *S,
-                             int64_t k, int64_t lds, int64_t T0, DevStatus *st) {
+                             int64_t k, int64_t lds, int64_t T0, DevStatus *st, int64_t tile0) {
     const int64_t rem = k - T0;
     if (rem <= 0) return cudaSuccess;
     static bool attr = false;
@@ -305,7 +316,9 @@ cudaError_t launch_tc_update(cudaStream_t s, const CUtensorMap &hi, const CUtens
         attr = true;
     }
     const int64_t t = cdiv(rem, kTile);
-    tc_update_kernel<<<(unsigned)(t * (t + 1) / 2), 128, kSmemBytes, s>>>(hi, lo, S, k, lds, T0, st);
+    const int64_t tiles = t * (t + 1) / 2 - tile0;
+    if (tiles <= 0) return cudaSuccess;
+    tc_update_kernel<<<(unsigned)tiles, 128, kSmemBytes, s>>>(hi, lo, S, k, lds, T0, st, tile0);
     note_launches(1);
     return cudaGetLastError();
 }

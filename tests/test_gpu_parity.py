@@ -186,6 +186,29 @@ def test_solve_is_deterministic(ts, ctx):
     assert np.array_equal(x1, x2)
 
 
+def test_in_order_factor_matches_look_ahead(ts, ctx, oracle_mod):
+    """Kernel-by-kernel timing runs the factorisation in order, without the
+    look-ahead side stream: both schedules must meet the oracle bar and give
+    the same pivot trace, and the timing must see all three factor kernels."""
+    p = workloads.random_sparse(2600, 1300, 0.004, seed=3, zero_frac=0.4, noise=0.05)
+    ref = oracle_mod.bpp_solve(p)
+    A = ts.HostCSR.from_problem(p)
+    for precision in ("mixed", "fp64"):
+        x1, _, inF1, tr1, _ = ctx.solve_ex(A, p.b, precision=precision)
+        ctx.profile(True, kernels=True)
+        try:
+            x2, _, inF2, tr2, _ = ctx.solve_ex(A, p.b, precision=precision)
+            stats = ctx.profile_read()
+        finally:
+            ctx.profile(False)
+        for x, inF in ((x1, inF1), (x2, inF2)):
+            _check_solution(p, ref, x, inF)
+        assert np.array_equal(tr1, tr2) and np.array_equal(tr1, ref.trace)
+        for ph in ("factor_diag", "factor_panel", "factor_update"):
+            assert stats[ph]["launches"] > 0, ph
+        assert stats["factor"]["launches"] == 0
+
+
 # ---------------------------------------------------------------------------
 # degenerate and special cases
 
