@@ -174,9 +174,20 @@ KERNEL_NAMES = {"factor_diag": "chol_diag_kernel", "factor_panel": "chol_panel_k
                 "factor_update": "tc_update_kernel (tcgen05 3xTF32)", "trsv": "trsv_fwd/bwd_kernel",
                 "gather": "gather_kernel", "spmv": "spmv_kernel", "gram": "gram_kernel"}
 
-# DRAM bytes per launch from one ncu capture of the kernel on this workload
-# (profiles/): None until a capture of the current kernel exists.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel on
+# this workload (profiles/factor_kernels_*.md, profiles/solve_kernels_*.md):
+# the diagonal kernel's launches all have the same size; the others are the
+# captured launch of the first factorisation (k = 5987), so they are
+# representative, not averages.  Set an entry to None when its kernel changes.
+NCU_TRAFFIC = {
+    "factor_diag": 107_520,
+    "factor_panel": 2_751_232,
+    "factor_update": 63_651_584 + 4_804_608,
+    "trsv": (72_849_408 + 841_728 + 72_859_648 + 779_520) // 2,
+    "gather": 96_256_512 + 39_016_192,
+    "gram": 10_614_016 + 70_490_112,
+    "spmv": (5_290_240 + 5_130_240) // 2,
+}
 
 
 def kkt_violation(prob, x):
@@ -265,6 +276,156 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _common_line(metric, value, unit, ws, args, ms, dtype, config, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+    line.update(extra)
+    return line
+
+
+def run_batched(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, peaks):
+    """512 uneven dense problems per step through the batched persistent path."""
+    import workloads
+
+    probs = workloads.batched_uneven()
+    a = [torch.as_tensor(p.a, device=dev) for p in probs]
+    b = [torch.as_tensor(p.b, device=dev) for p in probs]
+    x = [torch.empty(p.n, dtype=torch.float64, device=dev) for p in probs]
+    ctx.batch_autotune(ts.MIXED)
+    for _ in range(args.warmup):
+        ctx.solve_batch_dense(a, b, x, precision="mixed")
+    barrier()
+    ctx.profile(True)
+    dev_ms = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            st, stat, info = ctx.solve_batch_dense(a, b, x, precision="mixed")
+            assert st == ts.OK, stat
+            dev_ms.append(info.time_ms)
+        barrier()
+    stats = ctx.profile_read()["factor"]
+    ctx.profile(False)
+    xs = [t.cpu().numpy() for t in x]
+    ms64 = []
+    for _ in range(max(1, args.fp64_steps)):
+        st, stat, info64 = ctx.solve_batch_dense(a, b, x, precision="fp64")
+        ms64.append(info64.time_ms)
+    x64 = [t.cpu().numpy() for t in x]
+    dev_s = max_over_ranks(sum(dev_ms) * 1e-3)
+    if rank != 0:
+        return None
+    rel = max(np.linalg.norm(u - v) / max(np.linalg.norm(v), 1e-300) for u, v in zip(xs, x64))
+    kkt = 0.0
+    for p, u in zip(probs, xs):
+        a64 = p.a.astype(np.float64)
+        y = a64.T @ (a64 @ u - p.b)
+        atb = np.linalg.norm(a64.T @ p.b)
+        kkt = max(kkt, max(0.0, -u.min(), -y.min(), np.max(np.abs(u * y) / np.maximum(1, np.abs(u)))) / atb)
+    clock = (clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = 152 * 128 * 2 * clock / 1e12
+    ach = stats["flops"] / (stats["ms"] * 1e-3) / 1e12
+    n_tot = len(probs)
+    return _common_line(
+        "batched NNLS solves/s (512 uneven dense problems per step)", ws * n_tot * args.steps / dev_s,
+        "solves/s", ws, args, dev_s * 1e3 / args.steps, "f32+f64",
+        {"workload": "batched_uneven: 512 dense problems, n log-uniform in [32,1024], m = 1.5n, "
+                     "A FP32 N(0,1), x* 30% zeros, noise 1e-3, seed 20040812",
+         "precision": "mixed (FP32 precompute/factor, FP64 refinement)",
+         "l2": "no flush: A of the batch is 464 MB", "path": "batched gram + persistent kernel, "
+                                                           "one CUDA graph per call"},
+        fp64_plain={"value": n_tot / (np.mean(ms64) * 1e-3), "unit": "solves/s",
+                    "ms_per_step": float(np.mean(ms64))},
+        accuracy={"max_rel_diff_mixed_vs_fp64": float(rel), "max_kkt_viol_over_atb": float(kkt)},
+        roofline={"kernel": "batch_gram + batch_bpp (whole graph)", "bound": "alu",
+                  "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                  "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 flops x sampled SM clock",
+                  "flops_per_step": stats["flops"] / args.steps},
+        pivots_per_step=int(info.iters), refine_steps_per_step=int(info.refine_steps),
+        gpu_launches=int(stats["launches"]), clocks=clk.summary())
+
+
+def run_lsqr(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, peaks):
+    """One 2,000,000 x 200,000 sparse solve per step through the LSQR path."""
+    import workloads
+
+    prob = workloads.lsqr_large()
+    A = ts.DeviceCSR.from_problem(prob, device=dev)
+    bt = torch.as_tensor(prob.b, device=dev)
+    x = torch.empty(prob.n, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        ctx.solve(A, bt, x_out=x, path="lsqr")
+    barrier()
+    ctx.profile(True)
+    dev_ms = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            _, info = ctx.solve(A, bt, x_out=x, path="lsqr")
+            dev_ms.append(info.time_ms)
+        barrier()
+    stats = ctx.profile_read()
+    ctx.profile(False)
+    xs = x.cpu().numpy()
+    _, info64 = ctx.solve(A, bt, x_out=x, path="lsqr", precision="fp64")
+    x64 = x.cpu().numpy()
+    dev_s = max_over_ranks(sum(dev_ms) * 1e-3)
+    if rank != 0:
+        return None
+    lq = stats["lsqr"]
+    gbs = lq["bytes"] / (lq["ms"] * 1e-3) / 1e9
+    return _common_line(
+        "large sparse NNLS solves/s through the LSQR path", ws * args.steps / dev_s, "solves/s", ws, args,
+        dev_s * 1e3 / args.steps, "f32+f64",
+        {"workload": "lsqr_large: A 2,000,000x200,000 CSR, 8 nnz/row N(0,1), columns scaled by "
+                     "10^U(-2,2), x* 60% zeros, noise 1e-3, seed 20040813",
+         "precision": "mixed (FP32 LSQR inner iterations, FP64 residual correction)",
+         "l2": "no flush: the CSR alone is 192 MB"},
+        fp64_plain={"value": 1e3 / info64.time_ms, "unit": "solves/s", "ms_per_step": info64.time_ms},
+        accuracy={"kkt_viol_over_atb": kkt_violation(prob, xs),
+                  "rel_diff_mixed_vs_fp64": float(np.linalg.norm(xs - x64) / np.linalg.norm(x64))},
+        roofline={"kernel": "lsqr_av + lsqr_atu + lsqr_update (inner iterations)", "bound": "hbm",
+                  "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                  "traffic": None, "peak_source": "hbm_gbs of measured"},
+        pivots=int(info.iters), lsqr_phase_ms_per_step=lq["ms"] / args.steps,
+        gpu_launches=int(info.kernel_launches), clocks=clk.summary())
+
+
+def run_serving(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, peaks):
+    """A Poisson trace of mixed-size requests through submit/poll (continuous batching)."""
+    import workloads
+    from paper_cs_0408029_gb300 import serving
+
+    count = args.requests
+    probs = [workloads.serving_request(i) for i in range(count)]
+    arrivals = workloads.serving_arrivals(count, rate_per_s=args.rate)
+    serving.replay(ctx, probs[:8], np.zeros(8))  # warm-up: pools, lanes
+    barrier()
+    with ClockSampler(dev.index) as clk:
+        out = serving.replay(ctx, probs, arrivals, precision="mixed")
+    out64 = serving.replay(ctx, probs, arrivals, precision="fp64")
+    wall = max_over_ranks(out["wall_s"])
+    if rank != 0:
+        return None
+    assert (out["status"] == ts.OK).all() and (out64["status"] == ts.OK).all()
+    lat, lat64 = out["latency_s"] * 1e3, out64["latency_s"] * 1e3
+    rel = max(np.linalg.norm(u - v) / max(np.linalg.norm(v), 1e-300) for u, v in zip(out["x"], out64["x"]))
+    return _common_line(
+        "served NNLS solves/s and p50/p99 latency (Poisson arrivals)", ws * count / wall, "solves/s", ws,
+        args, 1e3 * wall / count, "f32+f64",
+        {"workload": f"serving: {count} requests, n log-uniform in [64,8192], m = 2n, density U(1%,5%), "
+                     f"Poisson arrivals at {args.rate}/s, request i drawn with seed (20040814, i)",
+         "precision": "mixed", "lanes": out["queue"]["lanes"]},
+        p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+        fp64_plain={"value": count / out64["wall_s"], "unit": "solves/s",
+                    "p50_ms": float(np.percentile(lat64, 50)), "p99_ms": float(np.percentile(lat64, 99))},
+        accuracy={"max_rel_diff_mixed_vs_fp64": float(rel)},
+        queue={k: int(v) for k, v in out["queue"].items()},
+        device_ms_sum=float(np.nansum(out["device_ms"])), clocks=clk.summary())
+
+
+EXTRA_WORKLOADS = {"batched": run_batched, "lsqr": run_lsqr, "serving": run_serving}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +434,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--profile-steps", type=int, default=1)
+    ap.add_argument("--workload", default="larger_sparse",
+                    choices=("larger_sparse",) + tuple(EXTRA_WORKLOADS))
+    ap.add_argument("--requests", type=int, default=200, help="serving workload: requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per second")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -305,6 +470,20 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    peaks, peak_kind = load_peaks()
+    if args.workload != "larger_sparse":
+        ctx = ts.Context(local)
+        line = EXTRA_WORKLOADS[args.workload](args, ts, torch, ctx, dev, ws, rank, barrier,
+                                              max_over_ranks, peaks)
+        ctx.close()
+        if line is not None:
+            if "roofline" in line:
+                line["roofline"]["peak_kind"] = peak_kind
+            print(json.dumps(line), flush=True)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
     prob = workloads.larger_sparse()
     ctx = ts.Context(local)
     A = ts.DeviceCSR.from_problem(prob, device=dev)
@@ -315,7 +494,6 @@ def main():
 
     for _ in range(args.warmup):
         ctx.solve(A, b, x_out=x, opts=mixed)
-    peaks, peak_kind = load_peaks()
 
     # ---- timed region: mixed precision, inputs resident in HBM ----
     lat, launches = [], 0
@@ -335,7 +513,7 @@ def main():
 
     # ---- per-kernel device time (separate pass: events around every kernel) ----
     ctx.profile(True, kernels=True)
-    for _ in range(args.profile_steps):
+    for _ in range(max(1, args.profile_steps)):
         ctx.solve(A, b, x_out=x, opts=mixed)
     stats = ctx.profile_read()
     ctx.profile(False)
@@ -344,7 +522,7 @@ def main():
     ctx.solve(A, b, x_out=x, opts=fp64)
     lat64 = []
     barrier()
-    for _ in range(args.fp64_steps):
+    for _ in range(max(1, args.fp64_steps)):
         _, info64 = ctx.solve(A, b, x_out=x, opts=fp64)
         lat64.append(info64.time_ms)
     barrier()
@@ -394,17 +572,17 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "pivots": int(info.iters), "final_F": int(info.nF),
                    "refine_steps": int(info.refine_steps)},
-        "fp64_plain": {"value": ws * args.fp64_steps / dev64, "unit": "solves/s",
-                       "ms_per_step": dev64 * 1e3 / args.fp64_steps,
-                       "p99_ms": float(np.percentile(lat64, 99)), "steps": args.fp64_steps},
-        "speedup_vs_fp64": (ws * args.steps / dev_s) / (ws * args.fp64_steps / dev64),
+        "fp64_plain": {"value": ws * len(lat64) / dev64, "unit": "solves/s",
+                       "ms_per_step": dev64 * 1e3 / len(lat64),
+                       "p99_ms": float(np.percentile(lat64, 99)), "steps": len(lat64)},
+        "speedup_vs_fp64": (ws * args.steps / dev_s) / (ws * len(lat64) / dev64),
         "accuracy": acc,
         "wall_ms_per_step": wall * 1e3 / args.steps,
         "roofline": rf,
         "kernels": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in r.items()
                         if kk != "peak_source"}
                     for k, r in per_kernel.items()},
-        "profile_steps": args.profile_steps,
+        "profile_steps": max(1, args.profile_steps),
         "e2e": {"value": ws * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),

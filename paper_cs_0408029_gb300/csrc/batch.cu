@@ -41,6 +41,7 @@ struct BatchProb {
 
 struct BatchOut {
     int32_t status, iters, refine, nF;
+    double flops;  // algorithmic flops of the pivot loop (factors, solves, residuals)
 };
 
 struct BatchParams {
@@ -437,6 +438,7 @@ __global__ void __launch_bounds__(kBT, 1)
         T *rhs = static_cast<T *>(P.rhs);
         const T *Gsrc = prm.mixed ? reinterpret_cast<const T *>(P.G) : reinterpret_cast<const T *>(P.Gd);
         int status = TSNNLS_OK, refine = 0;
+        double flops = 0.0;  // the same value in every thread
         // F = {}, x = 0, y = -A^T b
         for (int j = tid; j < n; j += kBT) {
             P.x[j] = 0.0;
@@ -527,6 +529,7 @@ __global__ void __launch_bounds__(kBT, 1)
                 for (int a = tid; a < k; a += kBT) rhs[a] = (T)P.c[P.F[a]];
                 __syncthreads();
                 cta_chol_solve<T>(S, k, lds, rhs);
+                flops += (double)k * k * k / 3.0 + 2.0 * (double)k * k;
                 for (int a = tid; a < k; a += kBT) P.x[P.F[a]] = (double)rhs[a];
                 __syncthreads();
                 ++refine;
@@ -537,10 +540,12 @@ __global__ void __launch_bounds__(kBT, 1)
             for (;;) {
                 cta_residual(P, k);
                 cta_atr(P);
+                flops += 2.0 * P.m * ((double)k + n);
                 if (conv) break;
                 for (int a = tid; a < k; a += kBT) rhs[a] = (T)P.s[P.F[a]];
                 __syncthreads();
                 cta_chol_solve<T>(S, k, lds, rhs);
+                flops += 2.0 * (double)k * k;
                 double dm = 0.0, xm = 0.0;
                 for (int a = tid; a < k; a += kBT) {
                     const int j = P.F[a];
@@ -572,6 +577,7 @@ __global__ void __launch_bounds__(kBT, 1)
             out[p].iters = sh_iters;
             out[p].refine = refine;
             out[p].nF = k;
+            out[p].flops = flops;
         }
         __syncthreads();
     }
@@ -741,6 +747,7 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
     cudaFreeAsync(arena, s);
     cudaStreamSynchronize(s);
     int32_t iters = 0, refine = 0;
+    double flops = 0.0, bytes = 0.0;
     if (status == TSNNLS_OK) {
         for (int q = 0; q < count; ++q) {
             const int i = order[q];
@@ -748,6 +755,19 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
             if (hout[q].status != TSNNLS_OK && status == TSNNLS_OK) status = hout[q].status;
             iters += hout[q].iters;
             refine += hout[q].refine;
+            // precompute: lower A^T A and A^T b; then the pivot loop
+            const double mq = hp[q].m, nq = hp[q].n;
+            flops += mq * nq * (nq + 1.0) + 2.0 * mq * nq + hout[q].flops;
+            bytes += 4.0 * mq * nq + (mixed ? 4.0 : 8.0) * nq * (nq + 1.0) / 2.0 + 8.0 * (mq + 2.0 * nq);
+        }
+        // the whole graph (precompute + persistent kernel) is accounted as
+        // one FACTOR phase of the profiling API
+        if (lane.prof) {
+            tsnnls_phase_stat &ps = lane.stats[TSNNLS_PHASE_FACTOR];
+            ps.ms += ms;
+            ps.launches += launches_so_far() - launch0;
+            ps.flops += flops;
+            ps.bytes += bytes;
         }
     }
     if (info) {

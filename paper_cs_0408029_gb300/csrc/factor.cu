@@ -84,8 +84,8 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
 template <typename T, int J>
-__device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, T (*col)[32], int lane, int &bad, int base) {
-    T d = __shfl_sync(0xffffffffu, s.a[J], J);
+__device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, T (*col)[32], int lane, int &bad, int base,
+                                               T d) {
     if (!(d > T(0))) {
         if (!bad) bad = base + J + 1;
         d = T(1);
@@ -96,6 +96,9 @@ __device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, T (*col)[32], int
     const T wj = (J >= lane) ? (((J == lane) ? T(1) : T(0)) - s.w[J]) * inv : T(0);
     s.w[J] = wj;
     if constexpr (J + 1 < 32) {
+        // the next pivot first: lane J + 1 finishes its diagonal entry with its
+        // own L(J + 1, J), so the pivot chain skips the shared-memory broadcast
+        const T dn = __shfl_sync(0xffffffffu, s.a[J + 1] - lij * lij, J + 1);
         col[J & 1][lane] = lij;
         __syncwarp();
 #pragma unroll
@@ -111,7 +114,7 @@ __device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, T (*col)[32], int
                 }
             }
         }
-        warp_chol_step<T, J + 1>(s, col, lane, bad, base);
+        warp_chol_step<T, J + 1>(s, col, lane, bad, base, dn);
     }
 }
 
@@ -127,7 +130,7 @@ __device__ __forceinline__ void warp_chol_inv(T (*A)[NB + 4], T (*W)[NB + 4], T 
         s.a[c] = c <= lane ? A[j0 + c][j0 + lane] : T(0);
         s.w[c] = T(0);
     }
-    warp_chol_step<T, 0>(s, col, lane, bad, j0);
+    warp_chol_step<T, 0>(s, col, lane, bad, j0, __shfl_sync(0xffffffffu, s.a[0], 0));
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
         A[j0 + c][j0 + lane] = c <= lane ? s.a[c] : s.w[c];  // L, and W(c, lane) above the diagonal
@@ -362,27 +365,32 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// panel: X = B W^T for the rows below the diagonal block: 64 rows per CTA,
-// each thread a 4 x (NB/16) register tile of X
+// panel: X = B W^T for the rows below the diagonal block: kPanelRows rows per
+// CTA (enough CTAs to cover the SMs for the panel heights that occur), each
+// thread a (kPanelRows/16) x (NB/16) register tile of X
+
+constexpr int kPanelRows = 32;
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
     chol_panel_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, float *__restrict__ xhi,
                       float *__restrict__ xlo) {
+    constexpr int PR = kPanelRows, RT = PR / 16, BP = PR + 4;  // rows, rows per thread, B pitch
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T(*Wl)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);  // Wl[l][c] = W(c, l)
-    T(*B)[68] = reinterpret_cast<T(*)[68]>(smem_raw + sizeof(T) * NB * (NB + 4));  // B[l][row]
+    T(*B)[BP] = reinterpret_cast<T(*)[BP]>(smem_raw + sizeof(T) * NB * (NB + 4));  // B[l][row]
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, k - K);
-    const int64_t R0 = K + kb + (int64_t)blockIdx.x * 64;
-    const int nr = (int)min((int64_t)64, k - R0);
+    const int64_t R0 = K + kb + (int64_t)blockIdx.x * PR;
+    const int nr = (int)min((int64_t)PR, k - R0);
     if (nr <= 0) return;
     // W: thread -> column c of the stored block, 8 consecutive rows l (two
     // 4-vectors, one 32-byte sector in FP32); column c holds W(c, l) for l < c
     // and L(c, c) on the diagonal, so Wl[l][c] = W(c, l) with W(c, c) =
     // 1 / L(c, c).  Rows stay below K + kb rounded up to 8 <= lds.
-    constexpr int NW = NB * NB / 8 / 256;  // 8-row chunks of W per thread
-    constexpr int NBV = NB * 64 / 4 / 256; // 4-row vectors of B per thread
+    constexpr int NW = NB * NB / 8 / 256;   // 8-row chunks of W per thread
+    constexpr int NBV = NB * PR / 4 / 256;  // 4-row vectors of B per thread
+    constexpr int VPC = PR / 4;             // 4-row vectors per column of B
     {
         T v[NW][8];
 #pragma unroll
@@ -409,7 +417,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int u = 0; u < NBV; ++u) {
             const int e = u * 256 + tid;
-            const int l = e / 16, r0 = (e % 16) * 4;
+            const int l = e / VPC, r0 = (e % VPC) * 4;
             if (l < kb && r0 < nr) {
                 ld4(&S[(R0 + r0) + (K + l) * lds], bv[u]);
             } else {
@@ -424,13 +432,15 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int l = l0 + q;
-                Wl[l][c] = (c >= kb || l > c) ? T(0) : (l == c ? T(1) / v[u][q] : v[u][q]);
+                if (l != c) Wl[l][c] = (c >= kb || l > c) ? T(0) : v[u][q];
             }
         }
+        // the diagonal of W (written by no one else), one reciprocal per thread
+        if (tid < NB) Wl[tid][tid] = tid < kb ? T(1) / S[(K + tid) + (K + tid) * lds] : T(0);
 #pragma unroll
         for (int u = 0; u < NBV; ++u) {
             const int e = u * 256 + tid;
-            const int l = e / 16, r0 = (e % 16) * 4;
+            const int l = e / VPC, r0 = (e % VPC) * 4;
             T o[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) o[q] = r0 + q < nr ? bv[u][q] : T(0);
@@ -439,14 +449,14 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     constexpr int CT = NB / 16;              // columns per thread
-    const int tr = tid & 15, tc = tid >> 4;  // rows tr*4 .. +4, columns tc*CT .. +CT
-    T acc[4][CT] = {};
+    const int tr = tid & 15, tc = tid >> 4;  // rows tr*RT .. +RT, columns tc*CT .. +CT
+    T acc[RT][CT] = {};
 #pragma unroll 4
     for (int l = 0; l < NB; ++l) {
-        T x[4], w[CT];
+        T x[RT], w[CT];
+#pragma unroll
+        for (int p = 0; p < RT; ++p) x[p] = B[l][tr * RT + p];
         if constexpr (sizeof(T) == 4) {  // 16-byte shared loads (rows are 16-byte aligned)
-            const float4 xv = *reinterpret_cast<const float4 *>(&B[l][tr * 4]);
-            x[0] = xv.x; x[1] = xv.y; x[2] = xv.z; x[3] = xv.w;
 #pragma unroll
             for (int q = 0; q < CT; q += 4) {
                 const float4 wv = *reinterpret_cast<const float4 *>(&Wl[l][tc * CT + q]);
@@ -454,35 +464,28 @@ __global__ void __launch_bounds__(256)
             }
         } else {
 #pragma unroll
-            for (int p = 0; p < 4; ++p) x[p] = B[l][tr * 4 + p];
-#pragma unroll
             for (int q = 0; q < CT; ++q) w[q] = Wl[l][tc * CT + q];
         }
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < RT; ++p)
 #pragma unroll
             for (int q = 0; q < CT; ++q) acc[p][q] += x[p] * w[q];
     }
-    const int r0 = tr * 4;
+    const int r0 = tr * RT;
 #pragma unroll
     for (int q = 0; q < CT; ++q) {
         const int c = tc * CT + q;
         if (c >= kb) continue;
         T *dst = &S[(R0 + r0) + (K + c) * lds];
-        const T o[4] = {acc[0][q], acc[1][q], acc[2][q], acc[3][q]};
-        if (r0 + 3 < nr) {
-            st4(dst, o);
-        } else {
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
-                if (r0 + p < nr) dst[p] = o[p];
-        }
+        for (int p = 0; p < RT; ++p)
+            if (r0 + p < nr) dst[p] = acc[p][q];
     }
     if (xhi) {
         // K-major hi / lo split of X for the tensor-core update: hi keeps the
         // top 10 mantissa bits (exact in TF32), lo = x - hi is exact in FP32
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < RT; ++p) {
             const int r = r0 + p;
             if (r >= nr) continue;
 #pragma unroll
@@ -639,7 +642,7 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
     // and hold whole 32-row groups (reads run up to K + kb rounded up to 8)
     if (k > 0 && (lds % 32 != 0 || (reinterpret_cast<uintptr_t>(S) & 15) != 0)) return cudaErrorInvalidValue;
     const size_t smem_diag = 2 * sizeof(T) * NB * (NB + 4);
-    const size_t smem_panel = sizeof(T) * NB * (NB + 4) + sizeof(T) * NB * 68;
+    const size_t smem_panel = sizeof(T) * NB * (NB + 4) + sizeof(T) * NB * (kPanelRows + 4);
     cudaError_t e = cudaFuncSetAttribute(chol_diag_kernel<T, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
     if (e == cudaSuccess)
@@ -661,7 +664,7 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
         if (below > 0) {
             const bool use_tc = NB == 128 && sizeof(T) == 4 && tc && tc->ok && tc->rows >= k;
             if (kt) kt->begin(TSNNLS_PHASE_FACTOR_PANEL);
-            chol_panel_kernel<T, NB><<<(unsigned)cdiv(below, 64), 256, smem_panel, s>>>(
+            chol_panel_kernel<T, NB><<<(unsigned)cdiv(below, kPanelRows), 256, smem_panel, s>>>(
                 S, k, lds, K, use_tc ? tc->xhi : nullptr, use_tc ? tc->xlo : nullptr);
             note_launches(1);
             // read B and W, write X (and its hi / lo copies)
@@ -983,9 +986,11 @@ __global__ void __launch_bounds__(256)
             for (int u = 0; u < 8; ++u) {
                 const int e = e0 + u * 256 + tid;
                 const int rr = e / NB, l = e % NB;
-                Ws[l][rr] = (l == rr && rr < nr) ? T(1) / v[u] : v[u];
+                if (l != rr) Ws[l][rr] = v[u];
             }
         }
+        // the diagonal of W (written by no one else), one reciprocal per thread
+        if (tid < NB) Ws[tid][tid] = tid < nr ? T(1) / L[(row0 + tid) + (row0 + tid) * lds] : T(0);
         if (ro.nh > 0) {
             if (!wait_at_least(sc.hcnt + i, ro.nh, sc.abort_flag, st, &ok_sh)) return;
             if (tid < NB)
@@ -1094,9 +1099,11 @@ __global__ void __launch_bounds__(256)
             for (int u = 0; u < 8; ++u) {
                 const int e = e0 + u * 256 + tid;
                 const int rr = e / NB, l = e % NB;
-                Ws[l][rr] = (l == rr && rr < nr) ? T(1) / v[u] : v[u];
+                if (l != rr) Ws[l][rr] = v[u];
             }
         }
+        // the diagonal of W (written by no one else), one reciprocal per thread
+        if (tid < NB) Ws[tid][tid] = tid < nr ? T(1) / L[(row0 + tid) + (row0 + tid) * lds] : T(0);
         if (ro.nh > 0) {
             if (!wait_at_least(sc.hcnt + i, ro.nh, sc.abort_flag, st, &ok_sh)) return;
             if (tid < NB)
