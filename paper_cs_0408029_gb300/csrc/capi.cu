@@ -391,7 +391,7 @@ int tsnnls_cholesky(tsnnls_ctx *ctx, int32_t precision, void *S, int64_t k, int6
         e = cudaMallocAsync(reinterpret_cast<void **>(&panel), sizeof(float) * (size_t)k * 256, l.stream);
         if (e == cudaSuccess) tc_panel_init(tc, panel, panel + (size_t)k * 128, k);
     }
-    const FactorStreams fs{l.side, l.fork, l.join};
+    const FactorStreams fs{l.side, l.fork, l.head, l.join};
     if (e == cudaSuccess)
         e = precision == TSNNLS_FP64
                 ? launch_cholesky<double>(l.stream, (double *)work, k, ldw, l.st_dev, nullptr, nullptr, &fs)

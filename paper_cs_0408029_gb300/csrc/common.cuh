@@ -87,13 +87,14 @@ struct KernelTimer {
 // tc (FP32 only, may be NULL) selects the tensor-core trailing update.
 // S must be 16-byte aligned and lds a multiple of 32 (cudaErrorInvalidValue
 // otherwise, nothing launched).
-// fs (may be NULL): a second stream and two events for look-ahead, i.e. the
-// next diagonal block is updated and factored on fs->side while the rest of
-// the trailing update runs on s.  Ignored when kt is given (kernels timed one
+// fs (may be NULL): a second stream and three events for look-ahead, i.e.
+// the panel rows of the next diagonal block, that block's update and its
+// factor run on fs->side while the rest of the panel and of the trailing
+// update run on s.  Ignored when kt is given (kernels timed one
 // by one, in order).
 struct FactorStreams {
     cudaStream_t side;
-    cudaEvent_t fork, join;
+    cudaEvent_t fork, head, join;
 };
 template <typename T>
 cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevStatus *st,

@@ -91,6 +91,7 @@ int lane_create(Lane &l) {
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&l.side, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.head, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.join, cudaEventDisableTiming);
     return status_from_cuda(e);
 }
@@ -99,6 +100,7 @@ void lane_destroy(Lane &l) {
     if (l.stream) cudaStreamSynchronize(l.stream);
     if (l.side) cudaStreamSynchronize(l.side);
     if (l.fork) cudaEventDestroy(l.fork);
+    if (l.head) cudaEventDestroy(l.head);
     if (l.join) cudaEventDestroy(l.join);
     if (l.side) cudaStreamDestroy(l.side);
     if (l.ev0) cudaEventDestroy(l.ev0);
@@ -316,7 +318,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                     TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, &lt));
                 } else {
                     prof_begin(lane, TSNNLS_PHASE_FACTOR);
-                    const FactorStreams fs{lane.side, lane.fork, lane.join};
+                    const FactorStreams fs{lane.side, lane.fork, lane.head, lane.join};
                     TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, nullptr, &fs));
                     prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
                 }

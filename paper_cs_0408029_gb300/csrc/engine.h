@@ -31,9 +31,9 @@ struct PhaseMark {
 struct Lane {
     cudaStream_t stream = nullptr;
     // look-ahead of the factorisation: high-priority side stream and its
-    // fork / join events
+    // fork / head / join events
     cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork = nullptr, head = nullptr, join = nullptr;
     DevStatus *st_dev = nullptr;
     DevStatus *st_host = nullptr;  // pinned mirror
     int32_t *bad_dev = nullptr;

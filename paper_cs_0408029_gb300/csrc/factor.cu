@@ -365,24 +365,25 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// panel: X = B W^T for the rows below the diagonal block: kPanelRows rows per
-// CTA (enough CTAs to cover the SMs for the panel heights that occur), each
-// thread a (kPanelRows/16) x (NB/16) register tile of X
+// panel: X = B W^T for rows [r_begin, r_end) below the diagonal block (a
+// multiple of 4 apart from k): kPanelRows rows per CTA (enough CTAs to cover
+// the SMs for the panel heights that occur), each thread a (kPanelRows/16) x
+// (NB/16) register tile of X
 
 constexpr int kPanelRows = 32;
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
-    chol_panel_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, float *__restrict__ xhi,
-                      float *__restrict__ xlo) {
+    chol_panel_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, int64_t r_begin, int64_t r_end,
+                      float *__restrict__ xhi, float *__restrict__ xlo) {
     constexpr int PR = kPanelRows, RT = PR / 16, BP = PR + 4;  // rows, rows per thread, B pitch
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T(*Wl)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);  // Wl[l][c] = W(c, l)
     T(*B)[BP] = reinterpret_cast<T(*)[BP]>(smem_raw + sizeof(T) * NB * (NB + 4));  // B[l][row]
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, k - K);
-    const int64_t R0 = K + kb + (int64_t)blockIdx.x * PR;
-    const int nr = (int)min((int64_t)PR, k - R0);
+    const int64_t R0 = r_begin + (int64_t)blockIdx.x * PR;  // rows [r_begin, r_end) below the block
+    const int nr = (int)min((int64_t)PR, r_end - R0);
     if (nr <= 0) return;
     // W: thread -> column c of the stored block, 8 consecutive rows l (two
     // 4-vectors, one 32-byte sector in FP32); column c holds W(c, l) for l < c
@@ -650,63 +651,81 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel);
     if (e != cudaSuccess) return e;
     const bool ahead = fs != nullptr && kt == nullptr;
-    for (int64_t K = 0; K < k; K += NB) {
-        const int kb = (int)std::min<int64_t>(NB, k - K);
-        const int64_t below = k - K - kb;
-        // algorithmic work of each kernel (for the optional per-kernel timing)
-        const double kbd = kb, bel = (double)below;
-        if (!ahead || K == 0) {  // with look-ahead, later diagonal blocks run on the side stream
+    const bool use_tc = NB == 128 && sizeof(T) == 4 && tc && tc->ok && tc->rows >= k;
+    auto panel = [&](cudaStream_t st_, int64_t K, int64_t r0, int64_t r1) {
+        if (r1 > r0)
+            chol_panel_kernel<T, NB><<<(unsigned)cdiv(r1 - r0, kPanelRows), 256, smem_panel, st_>>>(
+                S, k, lds, K, r0, r1, use_tc ? tc->xhi : nullptr, use_tc ? tc->xlo : nullptr);
+        note_launches(r1 > r0 ? 1 : 0);
+    };
+    auto update = [&](int64_t K, int kb, int64_t tile0) -> cudaError_t {
+        if (use_tc)
+            return launch_tc_update(s, tc->map_hi, tc->map_lo, reinterpret_cast<float *>(S), k, lds, K + kb,
+                                    st, tile0);
+        const int64_t t = cdiv(k - K - kb, 128);
+        const int64_t tiles = t * (t + 1) / 2 - tile0;
+        if (tiles > 0) {
+            chol_update128_kernel<T><<<(unsigned)tiles, 256, 0, s>>>(S, k, lds, K, kb, tile0);
+            note_launches(1);
+        }
+        return cudaSuccess;
+    };
+    if (!ahead) {
+        // in order: diagonal block, panel, trailing update (optionally each timed)
+        for (int64_t K = 0; K < k; K += NB) {
+            const int kb = (int)std::min<int64_t>(NB, k - K);
+            const int64_t below = k - K - kb;
+            // algorithmic work of each kernel (for the optional per-kernel timing)
+            const double kbd = kb, bel = (double)below;
             if (kt) kt->begin(TSNNLS_PHASE_FACTOR_DIAG);
             chol_diag_kernel<T, NB><<<1, 256, smem_diag, s>>>(S, k, lds, K, st);
             note_launches(1);
             if (kt) kt->end(2.0 * sizeof(T) * kbd * kbd, 2.0 * kbd * kbd * kbd / 3.0);
-        }
-        if (below > 0) {
-            const bool use_tc = NB == 128 && sizeof(T) == 4 && tc && tc->ok && tc->rows >= k;
+            if (below == 0) break;
             if (kt) kt->begin(TSNNLS_PHASE_FACTOR_PANEL);
-            chol_panel_kernel<T, NB><<<(unsigned)cdiv(below, kPanelRows), 256, smem_panel, s>>>(
-                S, k, lds, K, use_tc ? tc->xhi : nullptr, use_tc ? tc->xlo : nullptr);
-            note_launches(1);
+            panel(s, K, K + kb, k);
             // read B and W, write X (and its hi / lo copies)
             if (kt) kt->end(sizeof(T) * (2.0 * bel * kbd + kbd * kbd) + (use_tc ? 8.0 * bel * kbd : 0.0),
                             bel * kbd * kbd);
-            int64_t tile0 = 0;
-            if (ahead) {
-                // next diagonal block: its share of this step's update, then
-                // its factor, on the side stream; the trailing update skips it
-                const int64_t Kn = K + NB;
-                e = cudaEventRecord(fs->fork, s);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(fs->side, fs->fork, 0);
-                if (e != cudaSuccess) return e;
-                chol_tile_update_kernel<T, NB><<<10, 256, 0, fs->side>>>(S, k, lds, K, Kn);
-                chol_diag_kernel<T, NB><<<1, 256, smem_diag, fs->side>>>(S, k, lds, Kn, st);
-                note_launches(2);
-                e = cudaEventRecord(fs->join, fs->side);
-                if (e != cudaSuccess) return e;
-                tile0 = 1;
-            }
             if (kt) kt->begin(TSNNLS_PHASE_FACTOR_UPDATE);
-            if (use_tc) {
-                e = launch_tc_update(s, tc->map_hi, tc->map_lo, reinterpret_cast<float *>(S), k, lds,
-                                     K + kb, st, tile0);
-                if (e != cudaSuccess) return e;
-            } else {
-                const int64_t t = cdiv(below, 128);
-                const int64_t tiles = t * (t + 1) / 2 - tile0;
-                if (tiles > 0) {
-                    chol_update128_kernel<T><<<(unsigned)tiles, 256, 0, s>>>(S, k, lds, K, kb, tile0);
-                    note_launches(1);
-                }
-            }
+            e = update(K, kb, 0);
+            if (e != cudaSuccess) return e;
             // read and write the lower trailing matrix once, read the panel
             // (both copies for the tensor-core split); 2 kb flops per element
             if (kt) kt->end(2.0 * sizeof(T) * bel * (bel + 1.0) / 2.0 + (use_tc ? 8.0 : sizeof(T)) * bel * kbd,
                             bel * (bel + 1.0) * kbd);
-            if (ahead) {
-                e = cudaStreamWaitEvent(s, fs->join, 0);
-                if (e != cudaSuccess) return e;
-            }
         }
+        return cudaGetLastError();
+    }
+    // Look-ahead.  Step K, after the main stream has finished step K - 1:
+    //   side:  panel rows of the first trailing tile (its 128 rows) -> "head"
+    //          event; that tile's share of this step's update; the next
+    //          diagonal block -> "join" event
+    //   main:  panel of the remaining rows; wait "head"; trailing update
+    //          without the first tile; wait "join"
+    // so the chain from one diagonal block to the next is a short panel, the
+    // tile update and the diagonal kernel, while the long panel and the
+    // trailing update run beside it.
+    chol_diag_kernel<T, NB><<<1, 256, smem_diag, s>>>(S, k, lds, 0, st);
+    note_launches(1);
+    for (int64_t K = 0; K + NB < k; K += NB) {
+        const int64_t Kn = K + NB, head_end = std::min<int64_t>(Kn + 128, k);
+        e = cudaEventRecord(fs->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fs->side, fs->fork, 0);
+        if (e != cudaSuccess) return e;
+        panel(fs->side, K, Kn, head_end);
+        e = cudaEventRecord(fs->head, fs->side);
+        if (e != cudaSuccess) return e;
+        chol_tile_update_kernel<T, NB><<<10, 256, 0, fs->side>>>(S, k, lds, K, Kn);
+        chol_diag_kernel<T, NB><<<1, 256, smem_diag, fs->side>>>(S, k, lds, Kn, st);
+        note_launches(2);
+        e = cudaEventRecord(fs->join, fs->side);
+        if (e != cudaSuccess) return e;
+        panel(s, K, head_end, k);
+        e = cudaStreamWaitEvent(s, fs->head, 0);
+        if (e == cudaSuccess) e = update(K, NB, 1);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fs->join, 0);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -779,7 +798,7 @@ __device__ __forceinline__ bool wait_at_least(const int32_t *p, int target, int3
                 ok = 0;
                 break;
             }
-            if (spins > 64) __nanosleep(32);
+            if (spins > 8) __nanosleep(32);
         }
         *sh_ok = ok;
     }
@@ -887,10 +906,29 @@ __device__ __forceinline__ bool trsv_get(const TrsvScratch<T, NB> &sc, const T *
                                          T *zs, DevStatus *st, int *sh_ok) {
     const int tid = threadIdx.x;
     if constexpr (sizeof(T) == sizeof(float)) {
-        int ok = 1;
+        // one thread watches the block's first word, so waiting CTAs leave the
+        // memory system to the others; once it is there the rest follow
+        // within a few polls each
+        if (tid == 0) {
+            const uint64_t *w0 = sc.words + (int64_t)j * NB;
+            int ok = 1, spins = 0;
+            while ((word_load(w0) >> 32) == 0) {
+                if (++spins > kSpinLimit) {
+                    flag_store(sc.abort_flag, 1);
+                    st->timeout = 1;
+                    ok = 0;
+                    break;
+                }
+                if ((spins & 15) == 0 && flag_load(sc.abort_flag) != 0) { ok = 0; break; }
+                if (spins > 8) __nanosleep(32);
+            }
+            *sh_ok = ok;
+        }
+        __syncthreads();
+        int ok = *sh_ok;
         if (tid < NB) {
             T v = T(0);
-            if (tid < nvalid) {
+            if (ok && tid < nvalid) {
                 const uint64_t *w = sc.words + (int64_t)j * NB + tid;
                 uint64_t x;
                 int spins = 0;
@@ -901,10 +939,8 @@ __device__ __forceinline__ bool trsv_get(const TrsvScratch<T, NB> &sc, const T *
                         ok = 0;
                         break;
                     }
-                    if ((spins & 63) == 0) {
-                        if (flag_load(sc.abort_flag) != 0) { ok = 0; break; }
-                        __nanosleep(32);
-                    }
+                    if ((spins & 15) == 0 && flag_load(sc.abort_flag) != 0) { ok = 0; break; }
+                    __nanosleep(32);
                 }
                 v = ok ? __uint_as_float((uint32_t)x) : T(0);
             }

@@ -8,10 +8,14 @@
 // in the value type V (FP32 for MIXED, FP64 for FP64), and x_F += D z, until
 // the correction is below rel_tol * ||x_F||.  One inner iteration is three
 // kernels:
-//   av:  u^ = A D v - (alpha / beta_prev) u^_prev   (CSR, rows)   + partial ||u^||^2
+//   av:  u^ = A (D v) - (alpha / beta_prev) u^_prev  (CSR, rows; D v kept as
+//        its own vector, so one gather per nonzero)   + partial ||u^||^2
 //   atu: v^ = D A^T (u^ / beta) - beta v            (CSC, columns, F only) + partial ||v^||^2
-//   upd: alpha = ||v^||, v = v^ / alpha, plane rotation, z += (phi/rho) w,
+//   upd: alpha = ||v^||, v = v^ / alpha, D v, plane rotation, z += (phi/rho) w,
 //        w = v - (theta/rho) w
+// Short rows (the usual case) get one thread each with all their loads in
+// flight at once; the FP64 scalar recurrences are evaluated by one thread
+// per CTA (FP64 issue is scarce) and broadcast through shared memory.
 // Norms are reduced through per-CTA partials that every consumer CTA sums in
 // the same order, so the result is deterministic and needs no atomics and no
 // extra launch.  The scalar recurrences live in device memory, double-buffered
@@ -70,6 +74,17 @@ __device__ __forceinline__ void write_partial(double v, double *part, double *sh
 
 __device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
 
+// Per-CTA broadcast of a scalar computed by thread 0.
+__device__ __forceinline__ double cta_bcast(double v, double *sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) sh[0] = v;
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+
 // Column scale D_j = 1 / ||a_j|| (1 for an empty column) and value copies in V.
 template <typename V>
 __global__ void lsqr_prep_kernel(int64_t n, const int64_t *__restrict__ col_ptr,
@@ -123,9 +138,10 @@ __global__ void __launch_bounds__(kLT)
                        const double *__restrict__ part_u, int n_part_u, LsqrScalars *nxt,
                        double *__restrict__ part_v) {
     __shared__ double sh[kLT / 32];
-    const double beta = sqrt(sum_partials(part_u, n_part_u, sh));
+    const double ssq = sum_partials(part_u, n_part_u, sh);
+    const double beta = cta_bcast(threadIdx.x == 0 ? sqrt(ssq) : 0.0, sh);
     if (blockIdx.x == 0 && threadIdx.x == 0) nxt->beta = beta;
-    const double inv_beta = safe_div(1.0, beta);
+    const double inv_beta = cta_bcast(threadIdx.x == 0 ? safe_div(1.0, beta) : 0.0, sh);
     double acc = 0.0;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -136,36 +152,69 @@ __global__ void __launch_bounds__(kLT)
     write_partial(acc, part_v, sh);
 }
 
-// av: u^ <- A (D v) - (alpha / beta) u^   (TPR lanes per row)
+// av: u^ <- A dv - (alpha / beta) u^, dv = D v   (TPR lanes per row; TPR = 1:
+// one row per thread, its nonzeros loaded eight at a time)
 template <typename V, int TPR>
 __global__ void __launch_bounds__(kLT)
     lsqr_av_kernel(int64_t m, const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                   const V *__restrict__ val, const V *__restrict__ D, const V *__restrict__ v,
-                   V *__restrict__ u, const LsqrScalars *__restrict__ cur,
-                   double *__restrict__ part_u) {
+                   const V *__restrict__ val, const V *__restrict__ dv, V *__restrict__ u,
+                   const LsqrScalars *__restrict__ cur, double *__restrict__ part_u) {
     __shared__ double sh[kLT / 32];
-    const double scale = safe_div(cur->alpha, cur->beta);
+    const double scale = cta_bcast(threadIdx.x == 0 ? safe_div(cur->alpha, cur->beta) : 0.0, sh);
+    const V vscale = (V)scale;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride_rows = ((int64_t)gridDim.x * blockDim.x) / TPR;
-    const int sub = threadIdx.x % TPR;
-    const int64_t warp_row0 = ((gtid >> 5) << 5) / TPR;
-    const int64_t my_off = (gtid / TPR) - warp_row0;
     double acc = 0.0;
-    for (int64_t r0 = warp_row0; r0 < m; r0 += stride_rows) {
-        const int64_t r = r0 + my_off;
-        V s = V(0);
-        if (r < m) {
-            for (int64_t p = ptr[r] + sub; p < ptr[r + 1]; p += TPR) {
-                const int32_t c = idx[p];
-                s += val[p] * (D[c] * v[c]);
-            }
-        }
+    if constexpr (TPR == 1) {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t r = gtid; r < m; r += stride) {
+            const int64_t p0 = ptr[r], p1 = ptr[r + 1];
+            V s = V(0);
+            for (int64_t p = p0; p < p1; p += 8) {
+                int32_t c[8];
+                V a[8];
 #pragma unroll
-        for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
-        if (sub == 0 && r < m) {
-            const V un = s - (V)scale * u[r];
+                for (int q = 0; q < 8; ++q) {
+                    const bool in = p + q < p1;
+                    c[q] = in ? idx[p + q] : 0;
+                    a[q] = in ? val[p + q] : V(0);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s += a[q] * dv[c[q]];
+            }
+            const V un = s - vscale * u[r];
             u[r] = un;
             acc += (double)un * (double)un;
+        }
+    } else {
+        const int64_t stride_rows = ((int64_t)gridDim.x * blockDim.x) / TPR;
+        const int sub = threadIdx.x % TPR;
+        const int64_t warp_row0 = ((gtid >> 5) << 5) / TPR;
+        const int64_t my_off = (gtid / TPR) - warp_row0;
+        for (int64_t r0 = warp_row0; r0 < m; r0 += stride_rows) {
+            const int64_t r = r0 + my_off;
+            V s = V(0);
+            if (r < m) {
+                const int64_t p1 = ptr[r + 1];
+                for (int64_t p = ptr[r] + sub; p < p1; p += 4 * TPR) {
+                    int32_t c[4];
+                    V a[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool in = p + q * TPR < p1;
+                        c[q] = in ? idx[p + q * TPR] : 0;
+                        a[q] = in ? val[p + q * TPR] : V(0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) s += a[q] * dv[c[q]];
+                }
+            }
+#pragma unroll
+            for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+            if (sub == 0 && r < m) {
+                const V un = s - vscale * u[r];
+                u[r] = un;
+                acc += (double)un * (double)un;
+            }
         }
     }
     write_partial(acc, part_u, sh);
@@ -181,9 +230,11 @@ __global__ void __launch_bounds__(kLT)
                     const double *__restrict__ part_u, int n_part_u, LsqrScalars *nxt,
                     double *__restrict__ part_v) {
     __shared__ double sh[kLT / 32];
-    const double beta = sqrt(sum_partials(part_u, n_part_u, sh));
+    const double ssq = sum_partials(part_u, n_part_u, sh);
+    const double beta = cta_bcast(threadIdx.x == 0 ? sqrt(ssq) : 0.0, sh);
     if (blockIdx.x == 0 && threadIdx.x == 0) nxt->beta = beta;
-    const V inv_beta = (V)safe_div(1.0, beta);
+    const V inv_beta = (V)cta_bcast(threadIdx.x == 0 ? safe_div(1.0, beta) : 0.0, sh);
+    const V vbeta = (V)beta;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride_rows = ((int64_t)gridDim.x * blockDim.x) / TPR;
     const int sub = threadIdx.x % TPR;
@@ -194,12 +245,25 @@ __global__ void __launch_bounds__(kLT)
         const int64_t j = j0 + my_off;
         const bool active = j < n && inF[j];
         V s = V(0);
-        if (active)
-            for (int64_t p = ptr[j] + sub; p < ptr[j + 1]; p += TPR) s += val[p] * u[idx[p]];
+        if (active) {
+            const int64_t p1 = ptr[j + 1];
+            for (int64_t p = ptr[j] + sub; p < p1; p += 4 * TPR) {
+                int32_t c[4];
+                V a[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool in = p + q * TPR < p1;
+                    c[q] = in ? idx[p + q * TPR] : 0;
+                    a[q] = in ? val[p + q * TPR] : V(0);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s += a[q] * u[c[q]];
+            }
+        }
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
         if (sub == 0 && j < n) {
-            const V vn = active ? D[j] * (s * inv_beta) - (V)beta * v[j] : V(0);
+            const V vn = active ? D[j] * (s * inv_beta) - vbeta * v[j] : V(0);
             v[j] = vn;
             acc += (double)vn * (double)vn;
         }
@@ -212,44 +276,49 @@ __global__ void __launch_bounds__(kLT)
 template <typename V>
 __global__ void __launch_bounds__(kLT)
     lsqr_update_kernel(int64_t n, V *__restrict__ v, V *__restrict__ w, V *__restrict__ z,
-                       const double *__restrict__ part_v, int n_part_v,
-                       const LsqrScalars *__restrict__ cur, LsqrScalars *nxt, int init) {
+                       const V *__restrict__ D, V *__restrict__ dv, const double *__restrict__ part_v,
+                       int n_part_v, const LsqrScalars *__restrict__ cur, LsqrScalars *nxt, int init) {
     __shared__ double sh[kLT / 32];
-    const double alpha = sqrt(sum_partials(part_v, n_part_v, sh));
-    const double inv_alpha = safe_div(1.0, alpha);
-    if (init) {
-        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-             j += (int64_t)gridDim.x * blockDim.x) {
-            const V vn = v[j] * (V)inv_alpha;
-            v[j] = vn;
-            w[j] = vn;
+    __shared__ double scal[6];  // alpha, 1/alpha, f1, f2, next rhobar, next phibar
+    const double ssq = sum_partials(part_v, n_part_v, sh);
+    if (threadIdx.x == 0) {
+        const double alpha = sqrt(ssq);
+        scal[0] = alpha;
+        scal[1] = safe_div(1.0, alpha);
+        if (init) {
+            scal[2] = scal[3] = 0.0;
+            scal[4] = alpha;
+            scal[5] = nxt->beta;
+        } else {
+            const double beta = nxt->beta;  // written by the preceding atu launch
+            const double rhobar = cur->rhobar, phibar = cur->phibar;
+            const double rho = sqrt(rhobar * rhobar + beta * beta);
+            const double c = safe_div(rhobar, rho), s = safe_div(beta, rho);
+            scal[2] = safe_div(c * phibar, rho);  // phi / rho
+            scal[3] = safe_div(s * alpha, rho);   // theta / rho
+            scal[4] = -c * alpha;
+            scal[5] = s * phibar;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            nxt->alpha = alpha;
-            nxt->rhobar = alpha;
-            nxt->phibar = nxt->beta;
-        }
-        return;
     }
-    const double beta = nxt->beta;  // written by the preceding atu launch
-    const double rhobar = cur->rhobar, phibar = cur->phibar;
-    const double rho = sqrt(rhobar * rhobar + beta * beta);
-    const double c = safe_div(rhobar, rho), s = safe_div(beta, rho);
-    const double theta = s * alpha;
-    const double phi = c * phibar;
-    const V f1 = (V)safe_div(phi, rho), f2 = (V)safe_div(theta, rho);
+    __syncthreads();
+    const V inv_alpha = (V)scal[1], f1 = (V)scal[2], f2 = (V)scal[3];
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const V vn = v[j] * (V)inv_alpha;
+        const V vn = v[j] * inv_alpha;
         v[j] = vn;
-        const V wj = w[j];
-        z[j] += f1 * wj;
-        w[j] = vn - f2 * wj;
+        dv[j] = D[j] * vn;
+        if (init) {
+            w[j] = vn;
+        } else {
+            const V wj = w[j];
+            z[j] += f1 * wj;
+            w[j] = vn - f2 * wj;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        nxt->alpha = alpha;
-        nxt->rhobar = -c * alpha;
-        nxt->phibar = s * phibar;
+        nxt->alpha = scal[0];
+        nxt->rhobar = scal[4];
+        nxt->phibar = scal[5];
     }
 }
 
@@ -309,14 +378,14 @@ struct LsqrLaunch {
     const V *val, *cval;
     const V *D;
     const uint8_t *inF;
-    V *u, *v, *w, *z;
+    V *u, *v, *w, *z, *dv;
     double *part_u, *part_v;
     LsqrScalars *sc;  // [2]
     int tpr_r, tpr_c;
 
     template <int TPR>
     void av(const LsqrScalars *cur) {
-        lsqr_av_kernel<V, TPR><<<grid_for(m, TPR), kLT, 0, s>>>(m, row_ptr, col, val, D, v, u, cur, part_u);
+        lsqr_av_kernel<V, TPR><<<grid_for(m, TPR), kLT, 0, s>>>(m, row_ptr, col, val, dv, u, cur, part_u);
         note_launches(1);
     }
     template <int TPR>
@@ -327,6 +396,7 @@ struct LsqrLaunch {
     }
     void av_any(const LsqrScalars *cur) {
         switch (tpr_r) {
+            case 1: av<1>(cur); break;
             case 4: av<4>(cur); break;
             case 8: av<8>(cur); break;
             case 16: av<16>(cur); break;
@@ -351,12 +421,15 @@ struct LsqrLaunch {
     void upd(const LsqrScalars *cur, LsqrScalars *nxt, int init) {
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kLT), kMaxPartials));
         const int nparts = init ? vstart_grid : grid_for(n, tpr_c);
-        lsqr_update_kernel<V><<<g, kLT, 0, s>>>(n, v, w, z, part_v, nparts, cur, nxt, init);
+        lsqr_update_kernel<V><<<g, kLT, 0, s>>>(n, v, w, z, D, dv, part_v, nparts, cur, nxt, init);
         note_launches(1);
     }
 };
 
-inline int tpr_for(double avg) { return avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32; }
+// lanes per row (column) of a sparse product by the average row length;
+// rows of up to 16 nonzeros get a thread each
+inline int tpr_for(double avg) { return avg <= 16 ? 1 : avg <= 24 ? 16 : 32; }
+inline int tpr_for_cols(double avg) { return avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32; }
 
 #define TRY_CUDA_L(expr)                   \
     do {                                   \
@@ -375,7 +448,7 @@ size_t lsqr_layout(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     b += up(8 * (n + 1)) + up(4 * nnz) + up(8 * nnz) + up(4 * (n + 1)) + up(8 * (n + 1));  // CSC
     b += 2 * up(sizeof(V) * nnz) + up(sizeof(V) * n);  // value copies, D
     b += 5 * up(8 * n) + up(8 * m);                     // c, x, y, s, xprev; r
-    b += up(sizeof(V) * m) + 3 * up(sizeof(V) * n);     // u; v, w, z
+    b += up(sizeof(V) * m) + 4 * up(sizeof(V) * n);     // u; v, w, z, D v
     b += up(n) + up(4 * n) + 2 * up(8 * kMaxPartials) + up(2 * sizeof(LsqrScalars));
     return b + 256;
 }
@@ -461,6 +534,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         V *v = (V *)take(sizeof(V) * n);
         V *w = (V *)take(sizeof(V) * n);
         V *z = (V *)take(sizeof(V) * n);
+        V *dv = (V *)take(sizeof(V) * n);
         uint8_t *inF = (uint8_t *)take(n);
         int32_t *F = (int32_t *)take(4 * n);
         double *part_u = (double *)take(8 * kMaxPartials);
@@ -470,7 +544,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         const double csr_bytes = 12.0 * nnz + 8.0 * (m + 1);
         const double csc_bytes = 12.0 * nnz + 8.0 * (n + 1);
         LsqrLaunch<V> L{s, m, n, row_ptr, col_ptr, col, row_idx, val_v, cval_v, D, inF,
-                        u, v, w, z, part_u, part_v, sc, tpr_for(avg_row), tpr_for(avg_col)};
+                        u, v, w, z, dv, part_u, part_v, sc, tpr_for(avg_row), tpr_for_cols(avg_col)};
         const int gconv = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nnz, 256), 152 * 8));
 
         TRY_CUDA_L(cudaEventRecord(lane.ev0, s));

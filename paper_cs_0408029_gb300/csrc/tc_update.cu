@@ -10,9 +10,9 @@
 // The panel kernel writes X twice more in K-major form (row i holds its 128
 // values contiguously), as hi and lo copies; TMA brings 128-row boxes of them
 // into shared memory with the 128-byte swizzle the MMA descriptors expect.
-// One thread issues the TMA copies and the MMAs; all four warps then read the
-// accumulator out of tensor memory (tcgen05.ld, one row per thread) and
-// subtract it from C.  Every wait on an mbarrier is bounded: on timeout the
+// One thread issues the TMA copies and the MMAs and alone waits on the stage
+// barriers; all four warps then read the accumulator out of tensor memory
+// (tcgen05.ld, one row per thread) and subtract it from C.  Every wait on an mbarrier is bounded: on timeout the
 // CTA records st->timeout, waits (bounded) for its own copies, frees its
 // tensor memory and returns.
 #include <cuda.h>
@@ -185,22 +185,25 @@ __global__ void __launch_bounds__(128, 3)
     float cur[16];
     load_c(0, cur);
 
+    // Only the issuing thread waits on the stage barriers: a thread that
+    // polled them alongside it could be overtaken by a full phase (thread 0
+    // re-arms the barrier for the next stage as soon as the MMAs are done)
+    // and then wait for a parity that never comes.  The others meet it at
+    // the barrier after the last stage.
     uint32_t parity = 0;
-    for (int h = 0; h < kStages && !fail_sh; ++h) {
-        if (tid == 0) {
+    if (tid == 0) {
+        for (int h = 0; h < kStages; ++h) {
             mbar_expect_tx(&bar_tma, 4 * kBoxBytes);
             const int x = 32 * h;
             tma_load_2d(sAh, &map_hi, x, (int)r0, &bar_tma);
             tma_load_2d(sAl, &map_lo, x, (int)r0, &bar_tma);
             tma_load_2d(sBh, &map_hi, x, (int)c0, &bar_tma);
             tma_load_2d(sBl, &map_lo, x, (int)c0, &bar_tma);
-        }
-        if (!mbar_wait(&bar_tma, parity)) {
-            if (tid == 0) fail_sh = 1;
-            break;
-        }
-        tc_fence_after();
-        if (tid == 0) {
+            if (!mbar_wait(&bar_tma, parity)) {
+                fail_sh = 1;
+                break;
+            }
+            tc_fence_after();
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t off = kk * 32;  // 8 TF32 = 32 bytes of K
@@ -213,20 +216,24 @@ __global__ void __launch_bounds__(128, 3)
                 mma_tf32(tmem, al, bh, idesc, 1);
             }
             mma_commit(&bar_mma);
+            // the MMAs must be done with this stage's operands before the
+            // next TMA overwrites them (and, after the last stage, before the
+            // accumulator is read)
+            if (!mbar_wait(&bar_mma, parity)) {
+                fail_sh = 1;
+                break;
+            }
+            parity ^= 1;
         }
-        // the MMAs must be done with this stage's operands before the next TMA overwrites them
-        if (!mbar_wait(&bar_mma, parity)) {
-            if (tid == 0) fail_sh = 1;
-            break;
-        }
-        parity ^= 1;
     }
     __syncthreads();
     if (fail_sh) {
-        if (tid == 0) st->timeout = 1;
-        // bounded wait for copies that may still be in flight before the CTA goes away
-        mbar_wait(&bar_tma, parity);
-        mbar_wait(&bar_mma, parity);
+        if (tid == 0) {
+            st->timeout = 1;
+            // bounded wait for copies that may still be in flight before the CTA goes away
+            mbar_wait(&bar_tma, parity);
+            mbar_wait(&bar_mma, parity);
+        }
     } else {
         tc_fence_after();
         // chunk cc + 1 of C is loaded before chunk cc is stored: all loads of

@@ -59,3 +59,17 @@ def test_admission_respects_budget(env):
         t = ctx.submit(big_A, big.b, big_x)
         st, info = ctx.wait(t)
         assert st == ts.OK and info.path_used == ts.PATH_LSQR
+
+
+def test_burst_of_factor_solves_has_no_stall(env):
+    """A burst of mid-size requests keeps every lane in the tensor-core
+    factorisation at once; each solve must stay far below the seconds-long
+    bound of the device-side waits (a wait that misses its barrier phase
+    would sit out that bound and still return a correct result)."""
+    ts, serving = env
+    probs = [workloads.serving_request(300 + i, n_lo=1500, n_hi=3500) for i in range(24)]
+    with ts.Context(0) as ctx:
+        for _ in range(2):
+            out = serving.replay(ctx, probs, np.zeros(len(probs)))
+            assert (out["status"] == ts.OK).all(), out["status"]
+            assert np.nanmax(out["device_ms"]) < 2000.0, np.nanmax(out["device_ms"])
