@@ -293,8 +293,11 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
         if (nr > 0) {
             const int t64 = (nr + 63) / 64;
             const int ntiles = t64 * (t64 + 1) / 2;
-            const int sub = tid & 255, half = tid >> 8;  // two 256-thread halves, one tile each
-            const int tx = sub & 15, ty = sub >> 4;
+            // two 256-thread halves, one tile each; consecutive lanes take
+            // consecutive rows, so the column-major read-modify-write of S
+            // is coalesced
+            const int sub = tid & 255, half = tid >> 8;
+            const int tx = sub >> 4, ty = sub & 15;
             for (int tb = half; tb < ntiles; tb += 2) {
                 int I = (int)((sqrtf(8.f * tb + 1.f) - 1.f) * 0.5f);
                 while (I * (I + 1) / 2 > tb) --I;
@@ -385,6 +388,79 @@ __device__ void cta_chol_solve(const T *L, int k, int lds, T *rhs) {
         }
         __syncthreads();
     }
+}
+
+// ---- FP64-accurate dense products on the FP32 pipes (mixed path) ---------
+// GB300 issues FP64 at a small fraction of its FP32 rate, and the
+// refinement's dense residual b - A_F x_F and A^T r would be bound by it.
+// A is exactly FP32; an FP64 operand v is split into vh = (float)v and
+// vl = (float)(v - vh) (v = vh + vl to about 2^-48 relative), the product
+// a * vh is formed exactly as ph + pl (pl = fma(a, vh, -ph)), and the sum
+// is carried as an unevaluated pair (h, l) with Knuth's two-sum: about 48
+// significant bits instead of FP64's 53, enough for the refinement to reach
+// the 1e-9 target with a residual floor near 1e-12.
+__device__ __forceinline__ void ff_acc(float &h, float &l, float a, float vh, float vl) {
+    const float ph = a * vh;
+    const float pl = fmaf(a, vh, -ph);
+    const float s = h + ph;
+    const float bb = s - h;
+    const float e = (h - (s - bb)) + (ph - bb);
+    h = s;
+    l += e + fmaf(a, vl, pl);
+}
+__device__ __forceinline__ void ff_add(float &h, float &l, float h2, float l2) {
+    const float s = h + h2;
+    const float bb = s - h;
+    const float e = (h - (s - bb)) + (h2 - bb);
+    h = s;
+    l = (l + l2) + e;
+}
+__device__ __forceinline__ float2 ff_split(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+// r = b - A_F x_F with the double-float products above; x_F is split once
+// into P.y (free during the refinement) and r is stored split into P.r.
+__device__ void cta_residual_ff(const BatchProb &P, int k) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 *xs = reinterpret_cast<float2 *>(P.y);
+    for (int a = threadIdx.x; a < k; a += kBT) xs[a] = ff_split(P.x[P.F[a]]);
+    __syncthreads();
+    float2 *rs = reinterpret_cast<float2 *>(P.r);
+    for (int i = warp; i < P.m; i += kBWarps) {
+        float h = 0.f, l = 0.f;
+        const float *row = P.A + (int64_t)i * P.n;
+        for (int a = lane; a < k; a += 32) {
+            const float2 v = xs[a];
+            ff_acc(h, l, row[P.F[a]], v.x, v.y);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            ff_add(h, l, h2, l2);
+        }
+        if (lane == 0) rs[i] = ff_split(P.b[i] - ((double)h + (double)l));
+    }
+    __syncthreads();
+}
+
+// s_j = (A^T r)_j with r split in P.r; only the F columns unless all_cols.
+__device__ void cta_atr_ff(const BatchProb &P, bool all_cols) {
+    const float2 *rs = reinterpret_cast<const float2 *>(P.r);
+    for (int j = threadIdx.x; j < P.n; j += kBT) {
+        if (!all_cols && !P.inF[j]) continue;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;  // two chains for ILP
+        int i = 0;
+        for (; i + 1 < P.m; i += 2) {
+            const float2 v0 = rs[i], v1 = rs[i + 1];
+            ff_acc(h0, l0, P.A[(int64_t)i * P.n + j], v0.x, v0.y);
+            ff_acc(h1, l1, P.A[(int64_t)(i + 1) * P.n + j], v1.x, v1.y);
+        }
+        if (i < P.m) ff_acc(h0, l0, P.A[(int64_t)i * P.n + j], rs[i].x, rs[i].y);
+        ff_add(h0, l0, h1, l1);
+        P.s[j] = (double)h0 + (double)l0;
+    }
+    __syncthreads();
 }
 
 // r = b - A x (x zero outside F): warps over rows, lanes over the F list.
@@ -538,9 +614,16 @@ __global__ void __launch_bounds__(kBT, 1)
             bool conv = !prm.mixed || k == 0;
             int steps = 1;
             for (;;) {
-                cta_residual(P, k);
-                cta_atr(P);
-                flops += 2.0 * P.m * ((double)k + n);
+                if (prm.mixed) {
+                    // in-loop steps need s on F only; the last pass all of it (y_G)
+                    cta_residual_ff(P, k);
+                    cta_atr_ff(P, conv);
+                    flops += 2.0 * P.m * ((double)k + (conv ? n : k));
+                } else {
+                    cta_residual(P, k);
+                    cta_atr(P);
+                    flops += 2.0 * P.m * ((double)k + n);
+                }
                 if (conv) break;
                 for (int a = tid; a < k; a += kBT) rhs[a] = (T)P.s[P.F[a]];
                 __syncthreads();
