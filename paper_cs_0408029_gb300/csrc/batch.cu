@@ -47,6 +47,7 @@ struct BatchOut {
 struct BatchParams {
     double zero_tol, rel_tol;
     int32_t p_max, max_iter, max_refine, mixed;
+    int32_t scratch_bytes;  // bytes of the panel area free outside the factorisation
 };
 
 // ---------------------------------------------------------------------------
@@ -279,14 +280,16 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
         }
         // panel: X L_KK^T = B for rows below, one thread per row, into smem
         const int R0 = K + kb, nr = k - R0;
+        // (the row's kb entries are loaded into the panel first, all in flight)
         for (int r = tid; r < nr; r += kBT) {
+            for (int c = 0; c < kb; ++c) panel[r * (nb + 1) + c] = S[(R0 + r) + (int64_t)(K + c) * lds];
             for (int c = 0; c < kb; ++c) {
-                T s = S[(R0 + r) + (int64_t)(K + c) * lds];
+                T s = panel[r * (nb + 1) + c];
                 for (int l = 0; l < c; ++l) s -= panel[r * (nb + 1) + l] * diag[l * 65 + c];
                 s /= diag[c * 65 + c];
                 panel[r * (nb + 1) + c] = s;
-                S[(R0 + r) + (int64_t)(K + c) * lds] = s;
             }
+            for (int c = 0; c < kb; ++c) S[(R0 + r) + (int64_t)(K + c) * lds] = panel[r * (nb + 1) + c];
         }
         __syncthreads();
         // trailing update of the lower triangle, 4 x 4 register tiles over 64 x 64 tiles
@@ -326,6 +329,20 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
 #pragma unroll
                         for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
                 }
+                // all 16 loads of C before any store: the stores could alias
+                // them as far as the compiler can tell, which would serialise
+                // every read-modify-write on its memory latency
+                T cv[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int rr = ri + ty + 16 * a;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int cc = cj + tx + 16 * b;
+                        cv[a][b] = (rr < nr && cc < nr && rr >= cc) ? S[(R0 + rr) + (int64_t)(R0 + cc) * lds]
+                                                                    : T(0);
+                    }
+                }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     const int rr = ri + ty + 16 * a;
@@ -333,7 +350,7 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
                     for (int b = 0; b < 4; ++b) {
                         const int cc = cj + tx + 16 * b;
                         if (rr < nr && cc < nr && rr >= cc)
-                            S[(R0 + rr) + (int64_t)(R0 + cc) * lds] -= acc[a][b];
+                            S[(R0 + rr) + (int64_t)(R0 + cc) * lds] = cv[a][b] - acc[a][b];
                     }
                 }
             }
@@ -351,18 +368,31 @@ __device__ void cta_chol_solve(const T *L, int k, int lds, T *rhs) {
     for (int B0 = 0; B0 < k; B0 += 32) {  // L z = rhs
         const int nb = min(32, k - B0);
         if (tid < 32) {
+            // lane = row of the 32 x 32 diagonal block, loaded before the
+            // serial steps (l[c] = L(B0 + lane, B0 + c)); d = its diagonal entry
+            T l[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) l[c] = (c < nb && lane < nb) ? L[(B0 + lane) + (int64_t)(B0 + c) * lds] : T(0);
+            const T inv = lane < nb ? T(1) / L[(B0 + lane) + (int64_t)(B0 + lane) * lds] : T(0);
             T v = lane < nb ? rhs[B0 + lane] : T(0);
-            for (int c = 0; c < nb; ++c) {
-                const T zc = __shfl_sync(0xffffffffu, v, c) / L[(B0 + c) + (int64_t)(B0 + c) * lds];
-                if (lane == c) v = zc;
-                if (lane > c && lane < nb) v -= L[(B0 + lane) + (int64_t)(B0 + c) * lds] * zc;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                if (c < nb) {
+                    const T zc = __shfl_sync(0xffffffffu, v * inv, c);
+                    if (lane == c) v = zc;
+                    if (lane > c) v -= l[c] * zc;
+                }
             }
             if (lane < nb) rhs[B0 + lane] = v;
         }
         __syncthreads();
         for (int r = B0 + nb + tid; r < k; r += kBT) {
+            T lv[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) lv[c] = c < nb ? L[r + (int64_t)(B0 + c) * lds] : T(0);
             T s = T(0);
-            for (int c = 0; c < nb; ++c) s += L[r + (int64_t)(B0 + c) * lds] * rhs[B0 + c];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) s += lv[c] * rhs[B0 + c];
             rhs[r] -= s;
         }
         __syncthreads();
@@ -371,19 +401,31 @@ __device__ void cta_chol_solve(const T *L, int k, int lds, T *rhs) {
     for (int bi = nblk - 1; bi >= 0; --bi) {  // L^T w = z
         const int B0 = bi * 32, nb = min(32, k - B0);
         if (tid < 32) {
+            // lane = column of the block: lt[c] = L(B0 + c, B0 + lane)
+            T lt[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) lt[c] = (c < nb && lane < nb) ? L[(B0 + c) + (int64_t)(B0 + lane) * lds] : T(0);
+            const T inv = lane < nb ? T(1) / L[(B0 + lane) + (int64_t)(B0 + lane) * lds] : T(0);
             T v = lane < nb ? rhs[B0 + lane] : T(0);
-            for (int c = nb - 1; c >= 0; --c) {
-                const T wc = __shfl_sync(0xffffffffu, v, c) / L[(B0 + c) + (int64_t)(B0 + c) * lds];
-                if (lane == c) v = wc;
-                if (lane < c) v -= L[(B0 + c) + (int64_t)(B0 + lane) * lds] * wc;
+#pragma unroll
+            for (int c = 31; c >= 0; --c) {
+                if (c < nb) {
+                    const T wc = __shfl_sync(0xffffffffu, v * inv, c);
+                    if (lane == c) v = wc;
+                    if (lane < c) v -= lt[c] * wc;
+                }
             }
             if (lane < nb) rhs[B0 + lane] = v;
         }
         __syncthreads();
         // rows above: rhs[r] -= sum_c L(B0 + c, r) w_c for r < B0 (L^T row r)
         for (int r = tid; r < B0; r += kBT) {
+            T lv[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) lv[c] = c < nb ? L[(B0 + c) + (int64_t)r * lds] : T(0);
             T s = T(0);
-            for (int c = 0; c < nb; ++c) s += L[(B0 + c) + (int64_t)r * lds] * rhs[B0 + c];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) s += lv[c] * rhs[B0 + c];
             rhs[r] -= s;
         }
         __syncthreads();
@@ -420,33 +462,59 @@ __device__ __forceinline__ float2 ff_split(double v) {
     return make_float2(h, (float)(v - (double)h));
 }
 
-// r = b - A_F x_F with the double-float products above; x_F is split once
-// into P.y (free during the refinement) and r is stored split into P.r.
-__device__ void cta_residual_ff(const BatchProb &P, int k) {
+// r = b - A_F x_F with the double-float products above; x_F (split) and F
+// are staged in shared memory (the factorisation's panel area, free here)
+// when they fit, and r is stored split into P.r.
+__device__ void cta_residual_ff(const BatchProb &P, int k, void *scr, int scr_bytes) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2 *xs = reinterpret_cast<float2 *>(P.y);
-    for (int a = threadIdx.x; a < k; a += kBT) xs[a] = ff_split(P.x[P.F[a]]);
+    const bool staged = 12 * k <= scr_bytes;
+    float2 *xs = staged ? static_cast<float2 *>(scr) : reinterpret_cast<float2 *>(P.y);
+    const int32_t *F = P.F;
+    if (staged) {
+        int32_t *Fs = reinterpret_cast<int32_t *>(static_cast<float2 *>(scr) + k);
+        for (int a = threadIdx.x; a < k; a += kBT) {
+            const int j = P.F[a];
+            Fs[a] = j;
+            xs[a] = ff_split(P.x[j]);
+        }
+        F = Fs;
+    } else {
+        for (int a = threadIdx.x; a < k; a += kBT) xs[a] = ff_split(P.x[P.F[a]]);
+    }
     __syncthreads();
     float2 *rs = reinterpret_cast<float2 *>(P.r);
     for (int i = warp; i < P.m; i += kBWarps) {
-        float h = 0.f, l = 0.f;
+        float h = 0.f, l = 0.f, h2 = 0.f, l2 = 0.f;
         const float *row = P.A + (int64_t)i * P.n;
-        for (int a = lane; a < k; a += 32) {
-            const float2 v = xs[a];
-            ff_acc(h, l, row[P.F[a]], v.x, v.y);
+        int a = lane;
+        for (; a + 32 < k; a += 64) {  // two gathers in flight per lane
+            const float2 v0 = xs[a], v1 = xs[a + 32];
+            const float a0 = row[F[a]], a1 = row[F[a + 32]];
+            ff_acc(h, l, a0, v0.x, v0.y);
+            ff_acc(h2, l2, a1, v1.x, v1.y);
         }
+        if (a < k) ff_acc(h, l, row[F[a]], xs[a].x, xs[a].y);
+        ff_add(h, l, h2, l2);
         for (int o = 16; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
-            ff_add(h, l, h2, l2);
+            const float hh = __shfl_xor_sync(0xffffffffu, h, o), ll = __shfl_xor_sync(0xffffffffu, l, o);
+            ff_add(h, l, hh, ll);
         }
         if (lane == 0) rs[i] = ff_split(P.b[i] - ((double)h + (double)l));
     }
     __syncthreads();
 }
 
-// s_j = (A^T r)_j with r split in P.r; only the F columns unless all_cols.
-__device__ void cta_atr_ff(const BatchProb &P, bool all_cols) {
+// s_j = (A^T r)_j with r split in P.r (staged in shared memory when it
+// fits); only the F columns unless all_cols.
+__device__ void cta_atr_ff(const BatchProb &P, bool all_cols, void *scr, int scr_bytes) {
+    const bool staged = 8 * P.m <= scr_bytes;
     const float2 *rs = reinterpret_cast<const float2 *>(P.r);
+    if (staged) {
+        float2 *rsm = static_cast<float2 *>(scr);
+        for (int i = threadIdx.x; i < P.m; i += kBT) rsm[i] = rs[i];
+        __syncthreads();
+        rs = rsm;
+    }
     for (int j = threadIdx.x; j < P.n; j += kBT) {
         if (!all_cols && !P.inF[j]) continue;
         float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;  // two chains for ILP
@@ -616,8 +684,8 @@ __global__ void __launch_bounds__(kBT, 1)
             for (;;) {
                 if (prm.mixed) {
                     // in-loop steps need s on F only; the last pass all of it (y_G)
-                    cta_residual_ff(P, k);
-                    cta_atr_ff(P, conv);
+                    cta_residual_ff(P, k, panel, prm.scratch_bytes);
+                    cta_atr_ff(P, conv, panel, prm.scratch_bytes);
                     flops += 2.0 * P.m * ((double)k + (conv ? n : k));
                 } else {
                     cta_residual(P, k);
@@ -763,7 +831,8 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
     int32_t *d_queue = reinterpret_cast<int32_t *>(arena + total + desc_bytes + out_bytes + item_bytes);
     std::vector<BatchOut> hout(count);
     BatchParams prm{o.zero_tol, o.rel_tol, o.p_max,
-                    o.max_iter > 0 ? o.max_iter : 0, o.max_refine, mixed ? 1 : 0};
+                    o.max_iter > 0 ? o.max_iter : 0, o.max_refine, mixed ? 1 : 0,
+                    (int32_t)((mixed ? sizeof(float) : sizeof(double)) * (size_t)kMaxPanelRows * (max_nb + 1))};
     int status = TSNNLS_OK;
     const size_t smem = batch_smem_bytes(mixed, max_nb);
     cudaGraph_t graph = nullptr;
