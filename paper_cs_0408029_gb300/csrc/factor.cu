@@ -901,15 +901,18 @@ __host__ TrsvScratch<T, NB> trsv_scratch(void *base, int64_t k) {
 
 // zs[0..NB) <- solved block j (nvalid entries, zeros beyond), once available.
 // Uniform across the CTA; false when the launch was aborted or a wait timed out.
+// tight: every thread polls its own word from the start (one round trip; used
+// for the link on the chain, where the block is due any moment).
 template <typename T, int NB>
 __device__ __forceinline__ bool trsv_get(const TrsvScratch<T, NB> &sc, const T *rhs, int j, int nvalid,
-                                         T *zs, DevStatus *st, int *sh_ok) {
+                                         T *zs, DevStatus *st, int *sh_ok, bool tight = false) {
     const int tid = threadIdx.x;
     if constexpr (sizeof(T) == sizeof(float)) {
-        // one thread watches the block's first word, so waiting CTAs leave the
-        // memory system to the others; once it is there the rest follow
-        // within a few polls each
-        if (tid == 0) {
+        // otherwise one thread watches the block's first word, so waiting
+        // CTAs leave the memory system to the others; once it is there the
+        // rest follow within a few polls each
+        if (tid == 0 && tight) *sh_ok = 1;
+        if (tid == 0 && !tight) {
             const uint64_t *w0 = sc.words + (int64_t)j * NB;
             int ok = 1, spins = 0;
             while ((word_load(w0) >> 32) == 0) {
@@ -1036,7 +1039,7 @@ __global__ void __launch_bounds__(256)
     T acc = T(0);
     for (int d = ro.d_hi - 1; d >= ro.d_lo; --d) {
         const int j = i - 1 - d;
-        if (!trsv_get<T, NB>(sc, rhs, j, NB, zs, st, &ok_sh)) return;
+        if (!trsv_get<T, NB>(sc, rhs, j, NB, zs, st, &ok_sh, ro.finisher && d == 0)) return;
         if (r < nr) {
 #pragma unroll
             for (int c = 0; c < CW; ++c) acc += tile[c] * zs[part * CW + c];
@@ -1152,7 +1155,7 @@ __global__ void __launch_bounds__(256)
     for (int d = ro.d_hi - 1; d >= ro.d_lo; --d) {
         const int j = i + 1 + d;
         const int njr = (int)min((int64_t)NB, k - (int64_t)j * NB);
-        if (!trsv_get<T, NB>(sc, rhs, j, njr, ws, st, &ok_sh)) return;
+        if (!trsv_get<T, NB>(sc, rhs, j, njr, ws, st, &ok_sh, ro.finisher && d == 0)) return;
 #pragma unroll
         for (int q = 0; q < CPW; ++q) {
             T s = T(0);
