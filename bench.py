@@ -180,13 +180,13 @@ KERNEL_NAMES = {"factor_diag": "chol_diag_kernel", "factor_panel": "chol_panel_k
 # captured launch of the first factorisation (k = 5987), so they are
 # representative, not averages.  Set an entry to None when its kernel changes.
 NCU_TRAFFIC = {
-    "factor_diag": 107_520,
-    "factor_panel": 2_751_232,
-    "factor_update": 63_651_584 + 4_804_608,
-    "trsv": (72_849_408 + 841_728 + 72_859_648 + 779_520) // 2,
-    "gather": 96_256_512 + 39_016_192,
-    "gram": 10_614_016 + 70_490_112,
-    "spmv": (5_290_240 + 5_130_240) // 2,
+    "factor_diag": 107_008,
+    "factor_panel": None,  # only the 4-CTA head launch was captured for the current kernel
+    "factor_update": 66_578_944 + 6_349_056,
+    "trsv": (72_824_320 + 819_968 + 72_833_024 + 732_160) // 2,
+    "gather": 96_258_560 + 39_352_320,
+    "gram": 10_600_704 + 70_255_104,
+    "spmv": (5_289_984 + 5_129_984) // 2,
 }
 
 
