@@ -44,6 +44,37 @@ def dist_env():
     return ws, rank, local
 
 
+class Ranks:
+    """The replicas' host-side coordination: one rank per GPU, each solving
+    its own copy of the workload, no collective on the data path.  barrier()
+    brackets the timed region; max_over_ranks() takes the slowest rank's
+    time; value() is the whole-job rate (weak scaling: work grows with the
+    ranks).  device: the rank's GPU (NCCL), or the CPU (gloo, in tests)."""
+
+    def __init__(self, ws, rank, device):
+        self.ws, self.rank, self.device = ws, rank, device
+
+    def barrier(self):
+        import torch
+
+        if self.ws > 1:
+            torch.distributed.barrier()
+        if self.device.type == "cuda":
+            torch.cuda.synchronize(self.device)
+
+    def max_over_ranks(self, v):
+        import torch
+
+        if self.ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def value(self, units_per_rank, seconds):
+        return self.ws * units_per_rank / seconds
+
+
 def load_peaks():
     try:
         with open(PEAKS) as f:
@@ -457,18 +488,8 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(ws, rank, dev)
+    barrier, max_over_ranks = ranks.barrier, ranks.max_over_ranks
 
     peaks, peak_kind = load_peaks()
     if args.workload != "larger_sparse":
@@ -508,7 +529,7 @@ def main():
         wall = time.perf_counter() - t0
     clocks = clk.summary()
     dev_s = max_over_ranks(sum(lat) * 1e-3)
-    value = ws * args.steps / dev_s
+    value = ranks.value(args.steps, dev_s)
     xs = x.cpu().numpy()
 
     # ---- per-kernel device time (separate pass: events around every kernel) ----
