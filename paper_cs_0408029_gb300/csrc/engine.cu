@@ -92,6 +92,7 @@ int lane_create(Lane &l) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&l.side, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.head, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.ev_status, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.join, cudaEventDisableTiming);
     return status_from_cuda(e);
 }
@@ -101,6 +102,7 @@ void lane_destroy(Lane &l) {
     if (l.side) cudaStreamSynchronize(l.side);
     if (l.fork) cudaEventDestroy(l.fork);
     if (l.head) cudaEventDestroy(l.head);
+    if (l.ev_status) cudaEventDestroy(l.ev_status);
     if (l.join) cudaEventDestroy(l.join);
     if (l.side) cudaStreamDestroy(l.side);
     if (l.ev0) cudaEventDestroy(l.ev0);
@@ -174,6 +176,15 @@ struct Sync {
         if (e != cudaSuccess) return e;
         return cudaStreamSynchronize(l.stream);
     }
+    // copy the status now, wait for that copy later: work queued in between
+    // keeps the device busy while the host waits
+    cudaError_t post() {
+        cudaError_t e = cudaMemcpyAsync(l.st_host, l.st_dev, sizeof(DevStatus),
+                                        cudaMemcpyDeviceToHost, l.stream);
+        if (e != cudaSuccess) return e;
+        return cudaEventRecord(l.ev_status, l.stream);
+    }
+    cudaError_t wait() { return cudaEventSynchronize(l.ev_status); }
 };
 
 #define TRY_CUDA(expr)                          \
@@ -332,7 +343,24 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
                 TRY_CUDA(launch_update_x<T>(s, rhs, F, k, x, lane.st_dev));
                 prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
-                TRY_CUDA(sync.read());
+                TRY_CUDA(sync.post());
+            }
+            // FP64 residual r = b - A_F x_F and s = A^T r (x_G = 0) for the
+            // current x.  Whether the refinement goes on or not this pass is
+            // needed (at the end it gives y_G), so it is queued before the
+            // host reads the status of the last update.
+            auto residual = [&]() -> cudaError_t {
+                prof_begin(lane, TSNNLS_PHASE_SPMV);
+                cudaError_t e = launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row);
+                if (e == cudaSuccess)
+                    e = launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col);
+                prof_end(lane, 2.0 * 12.0 * nnz + 8.0 * (m + 1) + 8.0 * (n + 1) + 8.0 * (3.0 * m + 2.0 * n),
+                         4.0 * nnz);
+                return e;
+            };
+            TRY_CUDA(residual());
+            if (k > 0) {
+                TRY_CUDA(sync.wait());
                 if (lane.st_host->chol_info) { status = TSNNLS_ENOTPD; break; }
                 if (lane.st_host->timeout) { status = TSNNLS_ETIMEOUT; break; }
                 ++refine_total;
@@ -340,14 +368,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             double prev = lane.st_host->dnorm;
             bool converged = !mixed || k == 0;
             int steps = 1;
-            for (;;) {
-                // FP64 residual r = b - A_F x_F and s = A^T r (x_G = 0)
-                prof_begin(lane, TSNNLS_PHASE_SPMV);
-                TRY_CUDA(launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row));
-                TRY_CUDA(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col));
-                prof_end(lane, 2.0 * 12.0 * nnz + 8.0 * (m + 1) + 8.0 * (n + 1) + 8.0 * (3.0 * m + 2.0 * n),
-                         4.0 * nnz);
-                if (converged) break;
+            while (!converged) {
                 const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
                 TRY_CUDA(launch_gather_rhs<T>(s, sv, F, k, rhs));
@@ -358,14 +379,16 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
                 TRY_CUDA(launch_update_x<T>(s, rhs, F, k, x, lane.st_dev));
                 prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
-                TRY_CUDA(sync.read());
+                TRY_CUDA(sync.post());
+                TRY_CUDA(residual());
+                TRY_CUDA(sync.wait());
                 if (lane.st_host->timeout) { status = TSNNLS_ETIMEOUT; goto cleanup; }
                 ++steps;
                 ++refine_total;
                 const double d = lane.st_host->dnorm, xn = lane.st_host->xnorm;
                 last_rel = xn > 0 ? d / xn : 0.0;
                 if (d <= o.rel_tol * xn) {
-                    converged = true;  // one more pass computes r, s for this x
+                    converged = true;  // the pass queued above has r, s for this x
                 } else if (d > 0.5 * prev && d <= 1e-9 * xn) {
                     converged = true;  // at the rounding floor, already below the target
                 } else if (steps >= o.max_refine || (steps > 4 && d > prev)) {

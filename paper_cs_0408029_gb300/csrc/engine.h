@@ -39,6 +39,7 @@ struct Lane {
     int32_t *bad_dev = nullptr;
     int32_t *bad_host = nullptr;   // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev_status = nullptr;  // a status copy the host waits for later
     // per-phase accounting (tsnnls_profile_*)
     bool prof = false;
     bool prof_kernels = false;  // time the factorisation's kernels one by one
