@@ -986,8 +986,8 @@ __global__ void __launch_bounds__(256)
                     DevStatus *st) {
     constexpr int P = 256 / NB, CW = NB / P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*Ws)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);  // Ws[l][r] = W(r, l)
-    __shared__ T zs[NB];
+    T(*Wr)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);  // Wr[r][l] = W(r, l)
+    __shared__ __align__(16) T zs[NB];
     __shared__ T red[P][NB];
     __shared__ int64_t tk_sh;
     __shared__ int ok_sh;
@@ -1025,28 +1025,36 @@ __global__ void __launch_bounds__(256)
             for (int u = 0; u < 8; ++u) {
                 const int e = e0 + u * 256 + tid;
                 const int rr = e / NB, l = e % NB;
-                if (l != rr) Ws[l][rr] = v[u];
+                if (l != rr) Wr[rr][l] = v[u];
             }
         }
         // the diagonal of W (written by no one else), one reciprocal per thread
-        if (tid < NB) Ws[tid][tid] = tid < nr ? T(1) / L[(row0 + tid) + (row0 + tid) * lds] : T(0);
+        if (tid < NB) Wr[tid][tid] = tid < nr ? T(1) / L[(row0 + tid) + (row0 + tid) * lds] : T(0);
         if (ro.nh > 0) {
             if (!wait_at_least(sc.hcnt + i, ro.nh, sc.abort_flag, st, &ok_sh)) return;
             if (tid < NB)
                 for (int h = 0; h < ro.nh; ++h) hsum += __ldcg(sc.part + (ro.base + h) * NB + tid);
         }
     }
-    T acc = T(0);
+    // four partial sums per product (short dependency chains), z read as
+    // 4-vectors (broadcast shared loads)
+    T acc4[4] = {T(0), T(0), T(0), T(0)};
     for (int d = ro.d_hi - 1; d >= ro.d_lo; --d) {
         const int j = i - 1 - d;
         if (!trsv_get<T, NB>(sc, rhs, j, NB, zs, st, &ok_sh, ro.finisher && d == 0)) return;
         if (r < nr) {
 #pragma unroll
-            for (int c = 0; c < CW; ++c) acc += tile[c] * zs[part * CW + c];
+            for (int c = 0; c < CW; c += 4) {
+                T zv[4];
+                ld4(&zs[part * CW + c], zv);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc4[u] += tile[c + u] * zv[u];
+            }
         }
         if (d > ro.d_lo) fetch(j + 1);
         __syncthreads();
     }
+    const T acc = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
     red[part][r] = acc;
     __syncthreads();
     if (!ro.finisher) {
@@ -1068,10 +1076,16 @@ __global__ void __launch_bounds__(256)
         zs[tid] = tid < nr ? ri - sum : T(0);
     }
     __syncthreads();
-    T z = T(0);
-#pragma unroll 8
-    for (int c = 0; c < CW; ++c) z += Ws[part * CW + c][r] * zs[part * CW + c];
-    red[part][r] = z;
+    T z4[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
+    for (int c = 0; c < CW; c += 4) {
+        T wv[4], zv[4];
+        ld4(&Wr[r][part * CW + c], wv);
+        ld4(&zs[part * CW + c], zv);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) z4[u] += wv[u] * zv[u];
+    }
+    red[part][r] = (z4[0] + z4[1]) + (z4[2] + z4[3]);
     __syncthreads();
     T zi = T(0);
     if (tid < nr) {
@@ -1092,8 +1106,8 @@ __global__ void __launch_bounds__(256)
     constexpr int RPL = NB / 32;  // rows per lane per column
     constexpr int P = 256 / NB, CW = NB / P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*Ws)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);  // Ws[l][r] = W(r, l)
-    __shared__ T ws[NB];
+    T(*Ws)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);  // Ws[l][r] = W(r, l)
+    __shared__ __align__(16) T ws[NB];
     __shared__ T accs[NB];
     __shared__ T red[P][NB];
     __shared__ int64_t tk_sh;
@@ -1187,10 +1201,16 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     // w_i = W^T ws: w(r) = sum_{l >= r} W(l, r) ws(l) = sum_l Ws[r][l] ws(l)
     const int r = tid % NB, part = tid / NB;
-    T w = T(0);
-#pragma unroll 8
-    for (int c = 0; c < CW; ++c) w += Ws[r][part * CW + c] * ws[part * CW + c];
-    red[part][r] = w;
+    T w4[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
+    for (int c = 0; c < CW; c += 4) {
+        T wv[4], zv[4];
+        ld4(&Ws[r][part * CW + c], wv);
+        ld4(&ws[part * CW + c], zv);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w4[u] += wv[u] * zv[u];
+    }
+    red[part][r] = (w4[0] + w4[1]) + (w4[2] + w4[3]);
     __syncthreads();
     T wi = T(0);
     if (tid < nr) {
@@ -1209,7 +1229,7 @@ cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds
     const int64_t ctas = trsv_ctas(sc.nblk);
     // flags, ticket, abort and the published words start at zero for each pass
     const size_t bytes = (size_t)trsv_zeroed_bytes(sc.nblk, NB, sizeof(T));
-    const size_t smem = sizeof(T) * NB * (NB + 1);
+    const size_t smem = sizeof(T) * NB * (NB + 4);
     cudaError_t e = cudaFuncSetAttribute(trsv_fwd_kernel<T, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
