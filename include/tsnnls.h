@@ -86,7 +86,10 @@ typedef struct {
     int32_t precision;   /* TSNNLS_MIXED (default) or TSNNLS_FP64 */
     int32_t path;        /* TSNNLS_PATH_* (default AUTO) */
     int32_t max_refine;  /* refinement steps per pivot before TSNNLS_ENOCONV (default 30) */
-    int32_t reserved;
+    int32_t full_refine; /* 0 (default): a pivot's refinement may stop before rel_tol once no
+                            sign or zeroing decision of the next exchange can change (only signs
+                            matter before the last pivot, Section 3; the last pivot is always
+                            refined to rel_tol); 1: refine every pivot to rel_tol */
 } tsnnls_opts;
 
 typedef struct {

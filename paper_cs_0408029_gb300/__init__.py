@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("zero_tol", ctypes.c_double),
                 ("p_max", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("max_refine", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_refine", ctypes.c_int32), ("full_refine", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -25,7 +25,7 @@ struct DevStatus {
     int32_t chol_info;  // 0, or 1 + column of the first non-positive pivot
     int32_t timeout;    // 1 if a bounded device wait gave up
     int32_t maxiter_hit;
-    int32_t pad;
+    int32_t unsettled;  // entries whose sign / zeroing decision the last check left open
     double dnorm;       // ||dx_F||_inf of the last refinement step
     double xnorm;       // ||x_F||_inf after it
 };
@@ -127,6 +127,14 @@ cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, const int32_t *F,
 template <typename T>
 cudaError_t launch_update_x(cudaStream_t s, const T *delta, const int32_t *F, int64_t k,
                             double *x, DevStatus *st);
+// c = |A|^T (|A| 1): c_i bounds sum_f |(A^T A)_if| (t: m doubles of scratch).
+cudaError_t launch_gram_row_bound(cudaStream_t s, int64_t m, int64_t n, const int64_t *row_ptr,
+                                  const double *val, const int64_t *col_ptr, const int32_t *row_idx,
+                                  const double *cval, double *t, double *c);
+// st->unsettled = entries of x_F (error <= E) and y_G = -s_G (error <= c_j E)
+// that may still fall on either side of 0 or +-zero_tol.
+cudaError_t launch_settled(cudaStream_t s, int64_t n, const uint8_t *inF, const double *x,
+                           const double *sv, const double *c, double E, double zero_tol, DevStatus *st);
 cudaError_t launch_y_from_s(cudaStream_t s, int64_t n, const double *sv, const uint8_t *inF,
                             double *y);
 

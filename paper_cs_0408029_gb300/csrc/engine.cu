@@ -148,7 +148,7 @@ size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     c.take<int64_t>(n + 1);
     c.take<T>((size_t)n * ldg);  // G
     c.take<T>((size_t)n * ldg);  // S / L
-    for (int i = 0; i < 4; ++i) c.take<double>(n);  // c, x, y, s
+    for (int i = 0; i < 5; ++i) c.take<double>(n);  // c, x, y, s, settled-test bound
     c.take<double>(m);                              // r
     c.take<T>(n);                                   // rhs
     c.take<uint8_t>(n);
@@ -258,6 +258,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         double *x = cv.take<double>(n);
         double *y = cv.take<double>(n);
         double *sv = cv.take<double>(n);
+        double *cbound = cv.take<double>(n);
         double *r = cv.take<double>(m);
         T *rhs = cv.take<T>(n);
         uint8_t *inF = cv.take<uint8_t>(n);
@@ -290,6 +291,12 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         TRY_CUDA(launch_csr_to_csc(s, m, n, nnz, row_ptr, col, val, col_ptr, row_idx, cval, cnt,
                                    next));
         prof_end(lane, csr_bytes + csc_bytes, 0.0);
+        if (mixed && o.full_refine == 0) {
+            // bound for the settled test (r serves as scratch until the first residual)
+            prof_begin(lane, TSNNLS_PHASE_SETUP);
+            TRY_CUDA(launch_gram_row_bound(s, m, n, row_ptr, val, col_ptr, row_idx, cval, r, cbound));
+            prof_end(lane, csr_bytes + csc_bytes + 8.0 * (2.0 * m + n), 2.0 * nnz);
+        }
         prof_begin(lane, TSNNLS_PHASE_GRAM);
         TRY_CUDA(launch_gram<T>(s, m, n, row_ptr, col, val, col_ptr, row_idx, cval, bd, G, ldg, c));
         prof_end(lane, csr_bytes + csc_bytes + 0.5 * (double)n * (n + 1) * sizeof(T) + 8.0 * (m + n), 0.0);
@@ -298,6 +305,67 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         TRY_CUDA(launch_init_state(s, n, c, x, y, inF, o.p_max, lane.st_dev));
         prof_end(lane, 25.0 * n, 0.0);
 
+        // FP64 residual r = b - A_F x_F and s = A^T r (x_G = 0) for the current x
+        auto residual = [&]() -> cudaError_t {
+            prof_begin(lane, TSNNLS_PHASE_SPMV);
+            cudaError_t e = launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row);
+            if (e == cudaSuccess) e = launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col);
+            prof_end(lane, 2.0 * 12.0 * nnz + 8.0 * (m + 1) + 8.0 * (n + 1) + 8.0 * (3.0 * m + 2.0 * n),
+                     4.0 * nnz);
+            return e;
+        };
+        // Refinement of the current pivot's x_F on the factor in S (Section 3:
+        // FP32 solves, FP64 residuals), from `steps` solves done and the last
+        // correction `prev`.  allow_settle: stop before rel_tol once the
+        // settled test passes (*settled is then set).
+        int64_t k = 0, lds = 32;
+        auto refine = [&](int steps, double prev, bool allow_settle, bool *settled) -> int {
+            *settled = false;
+            for (;;) {
+                const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
+                prof_begin(lane, TSNNLS_PHASE_VECTOR);
+                cudaError_t e = launch_gather_rhs<T>(s, sv, F, k, rhs);
+                prof_end(lane, (12.0 + sizeof(T)) * k, 0.0);
+                prof_begin(lane, TSNNLS_PHASE_TRSV);
+                if (e == cudaSuccess) e = launch_chol_solve<T>(s, S, k, lds, rhs, trsv_scratch, lane.st_dev);
+                prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * k, 2.0 * (double)k * (double)k);
+                prof_begin(lane, TSNNLS_PHASE_VECTOR);
+                if (e == cudaSuccess) e = launch_update_x<T>(s, rhs, F, k, x, lane.st_dev);
+                prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
+                if (e == cudaSuccess) e = sync.post();
+                if (e == cudaSuccess) e = residual();
+                if (e == cudaSuccess) e = sync.wait();
+                if (e != cudaSuccess) return status_from_cuda(e);
+                if (lane.st_host->timeout) return TSNNLS_ETIMEOUT;
+                ++steps;
+                ++refine_total;
+                const double d = lane.st_host->dnorm, xn = lane.st_host->xnorm;
+                last_rel = xn > 0 ? d / xn : 0.0;
+                if (d <= o.rel_tol * xn) return TSNNLS_OK;  // the residual queued above is for this x
+                if (d > 0.5 * prev && d <= 1e-9 * xn) return TSNNLS_OK;  // rounding floor, below target
+                if (steps >= o.max_refine || (steps > 4 && d > prev))
+                    return d <= 1e-9 * xn ? TSNNLS_OK : TSNNLS_ENOCONV;
+                if (allow_settle && d <= 0.1 * prev) {
+                    // contraction <= 0.1 observed: the error left in x is below
+                    // d / 9 in the max norm; E allows a factor of 4.5 on that
+                    const double E = 0.5 * d + 1e-15 * xn;
+                    prof_begin(lane, TSNNLS_PHASE_VECTOR);
+                    e = launch_settled(s, n, inF, x, sv, cbound, E, o.zero_tol, lane.st_dev);
+                    prof_end(lane, 25.0 * n, 0.0);
+                    if (e == cudaSuccess) e = sync.read();
+                    if (e != cudaSuccess) return status_from_cuda(e);
+                    if (lane.st_host->unsettled == 0) {
+                        *settled = true;
+                        return TSNNLS_OK;
+                    }
+                }
+                prev = d;
+            }
+        };
+        bool open_pivot = false;  // the last pivot stopped at the settled test
+        int open_steps = 0;
+        double open_prev = 0.0;
+
         for (;;) {
             prof_begin(lane, TSNNLS_PHASE_EXCHANGE);
             TRY_CUDA(launch_exchange(s, n, x, y, inF, F, o.zero_tol, o.p_max, max_iter,
@@ -305,6 +373,20 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             prof_end(lane, 17.0 * n + 17.0 * n + 4.0 * n, 0.0);
             TRY_CUDA(sync.read());
             const DevStatus st = *lane.st_host;
+            if (st.done && open_pivot && !st.maxiter_hit) {
+                // x_F, y_G are feasible: this was the last pivot, so its
+                // refinement goes on to rel_tol (the decisions were settled,
+                // so the exchange will find the same sets again)
+                open_pivot = false;
+                TRY_CUDA(residual());
+                bool settled_unused = false;
+                status = refine(open_steps, open_prev, false, &settled_unused);
+                if (status != TSNNLS_OK) goto cleanup;
+                prof_begin(lane, TSNNLS_PHASE_VECTOR);
+                TRY_CUDA(launch_y_from_s(s, n, sv, inF, y));
+                prof_end(lane, 17.0 * n, 0.0);
+                continue;
+            }
             if (st.done) {
                 if (st.maxiter_hit) status = TSNNLS_EMAXITER;
                 break;
@@ -317,8 +399,8 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 t[3] = st.branch;
                 t[4] = st.k;
             }
-            const int64_t k = st.k;
-            const int64_t lds = round_up(std::max<int64_t>(k, 1), 32);
+            k = st.k;
+            lds = round_up(std::max<int64_t>(k, 1), 32);
             if (k > 0) {
                 const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
                 prof_begin(lane, TSNNLS_PHASE_GATHER);
@@ -345,19 +427,9 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
                 TRY_CUDA(sync.post());
             }
-            // FP64 residual r = b - A_F x_F and s = A^T r (x_G = 0) for the
-            // current x.  Whether the refinement goes on or not this pass is
-            // needed (at the end it gives y_G), so it is queued before the
-            // host reads the status of the last update.
-            auto residual = [&]() -> cudaError_t {
-                prof_begin(lane, TSNNLS_PHASE_SPMV);
-                cudaError_t e = launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row);
-                if (e == cudaSuccess)
-                    e = launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col);
-                prof_end(lane, 2.0 * 12.0 * nnz + 8.0 * (m + 1) + 8.0 * (n + 1) + 8.0 * (3.0 * m + 2.0 * n),
-                         4.0 * nnz);
-                return e;
-            };
+            // the residual of the new x is needed whether the refinement goes
+            // on or not (at the end it gives y_G), so it is queued before the
+            // host reads the status of the update
             TRY_CUDA(residual());
             if (k > 0) {
                 TRY_CUDA(sync.wait());
@@ -365,41 +437,16 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 if (lane.st_host->timeout) { status = TSNNLS_ETIMEOUT; break; }
                 ++refine_total;
             }
-            double prev = lane.st_host->dnorm;
-            bool converged = !mixed || k == 0;
-            int steps = 1;
-            while (!converged) {
-                const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
-                prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                TRY_CUDA(launch_gather_rhs<T>(s, sv, F, k, rhs));
-                prof_end(lane, (12.0 + sizeof(T)) * k, 0.0);
-                prof_begin(lane, TSNNLS_PHASE_TRSV);
-                TRY_CUDA(launch_chol_solve<T>(s, S, k, lds, rhs, trsv_scratch, lane.st_dev));
-                prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * k, 2.0 * (double)k * (double)k);
-                prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                TRY_CUDA(launch_update_x<T>(s, rhs, F, k, x, lane.st_dev));
-                prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
-                TRY_CUDA(sync.post());
-                TRY_CUDA(residual());
-                TRY_CUDA(sync.wait());
-                if (lane.st_host->timeout) { status = TSNNLS_ETIMEOUT; goto cleanup; }
-                ++steps;
-                ++refine_total;
-                const double d = lane.st_host->dnorm, xn = lane.st_host->xnorm;
-                last_rel = xn > 0 ? d / xn : 0.0;
-                if (d <= o.rel_tol * xn) {
-                    converged = true;  // the pass queued above has r, s for this x
-                } else if (d > 0.5 * prev && d <= 1e-9 * xn) {
-                    converged = true;  // at the rounding floor, already below the target
-                } else if (steps >= o.max_refine || (steps > 4 && d > prev)) {
-                    if (d <= 1e-9 * xn) {
-                        converged = true;
-                    } else {
-                        status = TSNNLS_ENOCONV;
-                        goto cleanup;
-                    }
+            if (mixed && k > 0) {
+                bool settled = false;
+                const double prev0 = lane.st_host->dnorm;
+                status = refine(1, prev0, o.full_refine == 0, &settled);
+                if (status != TSNNLS_OK) goto cleanup;
+                open_pivot = settled;
+                if (settled) {
+                    open_steps = 0;  // refine() does not report its count: restart the limits
+                    open_prev = lane.st_host->dnorm;
                 }
-                prev = d;
             }
             // Eq. 5: y_G = A_G^T (A_F x_F - b) = -s_G
             prof_begin(lane, TSNNLS_PHASE_VECTOR);

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kExThreads)
 
     if (tid == 0) {
         st->n_inf = (int32_t)n_inf;
+        st->done = 0;
         int32_t d;
         if (n_inf == 0) {
             st->done = 1;
@@ -270,6 +271,78 @@ template cudaError_t launch_update_x<float>(cudaStream_t, const float *, const i
                                             int64_t, double *, DevStatus *);
 template cudaError_t launch_update_x<double>(cudaStream_t, const double *, const int32_t *,
                                              int64_t, double *, DevStatus *);
+
+// ---------------------------------------------------------------------------
+// Settled decisions.  Before the last pivot only the signs of x_F and y_G
+// (after the 1e-12 zeroing) enter the method (Section 3), so refinement may
+// stop once no entry can change its side of the thresholds 0 and +-zero_tol.
+// With x known to within E in the max norm, s_i = a_i^T (b - A x) is known
+// to within c_i E, c_i = sum_r |a_ri| sum_j |a_rj| >= sum_f |(A^T A)_if|.
+
+__global__ void abs_row_sum_kernel(int64_t m, const int64_t *__restrict__ row_ptr,
+                                   const double *__restrict__ val, double *__restrict__ t) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) a += fabs(val[e]);
+        t[r] = a;
+    }
+}
+
+__global__ void abs_col_dot_kernel(int64_t n, const int64_t *__restrict__ col_ptr,
+                                   const int32_t *__restrict__ row_idx, const double *__restrict__ cval,
+                                   const double *__restrict__ t, double *__restrict__ c) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) a += fabs(cval[e]) * t[row_idx[e]];
+        c[j] = a;
+    }
+}
+
+cudaError_t launch_gram_row_bound(cudaStream_t s, int64_t m, int64_t n, const int64_t *row_ptr,
+                                  const double *val, const int64_t *col_ptr, const int32_t *row_idx,
+                                  const double *cval, double *t, double *c) {
+    const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 256), 152 * 8));
+    const int gn = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 8));
+    abs_row_sum_kernel<<<gm, 256, 0, s>>>(m, row_ptr, val, t);
+    abs_col_dot_kernel<<<gn, 256, 0, s>>>(n, col_ptr, row_idx, cval, t, c);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+__global__ void settled_kernel(int64_t n, const uint8_t *__restrict__ inF, const double *__restrict__ x,
+                               const double *__restrict__ sv, const double *__restrict__ c, double E,
+                               double zero_tol, DevStatus *st) {
+    __shared__ int32_t sh[32];
+    int32_t cnt = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const bool f = inF[j] != 0;
+        const double v = fabs(f ? x[j] : sv[j]);  // |x_j| on F, |y_j| = |s_j| on G
+        const double e = f ? E : c[j] * E;
+        if (!(v >= zero_tol + e || v + e < zero_tol)) ++cnt;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) sh[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        cnt = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt > 0) atomicAdd(&st->unsettled, cnt);
+    }
+}
+
+cudaError_t launch_settled(cudaStream_t s, int64_t n, const uint8_t *inF, const double *x,
+                           const double *sv, const double *c, double E, double zero_tol, DevStatus *st) {
+    cudaError_t e = cudaMemsetAsync(&st->unsettled, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 2));
+    settled_kernel<<<g, 256, 0, s>>>(n, inF, x, sv, c, E, zero_tol, st);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 // Eq. 5 from s = A^T (b - A x): y_G = -s_G, y_F = 0.
 __global__ void y_from_s_kernel(int64_t n, const double *__restrict__ sv,

@@ -209,6 +209,24 @@ def test_in_order_factor_matches_look_ahead(ts, ctx, oracle_mod):
         assert stats["factor"]["launches"] == 0
 
 
+def test_settle_stop_matches_full_refinement(ts, ctx, oracle_mod):
+    """Before the last pivot only the signs of x_F and y_G matter (Section 3):
+    a pivot's refinement may stop once no decision of the next exchange can
+    change.  The pivots, the split and x must be those of refinement to
+    rel_tol at every pivot, and the oracle's."""
+    p = workloads.random_sparse(2600, 1300, 0.004, seed=3, zero_frac=0.4, noise=0.05)
+    ref = oracle_mod.bpp_solve(p)
+    A = ts.HostCSR.from_problem(p)
+    x1, _, inF1, tr1, i1 = ctx.solve_ex(A, p.b, full_refine=1)
+    x2, _, inF2, tr2, i2 = ctx.solve_ex(A, p.b, full_refine=0)
+    for x, inF in ((x1, inF1), (x2, inF2)):
+        _check_solution(p, ref, x, inF)
+    assert np.array_equal(tr1, tr2) and np.array_equal(tr1, ref.trace)
+    assert np.array_equal(inF1, inF2)
+    assert i2.refine_steps <= i1.refine_steps
+    assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x1)
+
+
 # ---------------------------------------------------------------------------
 # degenerate and special cases
 
