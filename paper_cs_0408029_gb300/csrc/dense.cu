@@ -8,45 +8,72 @@
 
 namespace tsnnls {
 
-// Map a linear block index onto the lower-triangular tile (I, J), I >= J.
-__device__ __forceinline__ void tri_tile(int64_t b, int64_t &I, int64_t &J) {
-    int64_t i = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-    while (i * (i + 1) / 2 > b) --i;
-    while ((i + 1) * (i + 2) / 2 <= b) ++i;
-    I = i;
-    J = b - i * (i + 1) / 2;
-}
-
 // ---------------------------------------------------------------------------
-// Gather S = G_FF (lower).  32 x 32 tiles of S; the F indices of the tile's
-// rows and columns are staged in shared memory.
+// Gather S = G_FF (lower).  One CTA per 128 x 64 tile of S (tiles wholly
+// above the diagonal return at once); the F indices of the tile's rows and
+// columns are staged in shared memory.  Thread (tx, ty) owns rows
+// a0 + 4 tx .. + 3 of the columns b0 + ty + 8 j, j < 8: its 32 gathered
+// loads are all in flight before the first store, and each column's 4 rows
+// go out as one vector store when VEC (S 16-byte aligned, lds % 4 == 0).
 
 template <typename T>
+__device__ __forceinline__ void st_vec4(T *p, const T (&v)[4]);
+template <>
+__device__ __forceinline__ void st_vec4<float>(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st_vec4<double>(double *p, const double (&v)[4]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+}
+
+constexpr int kGatherRows = 128, kGatherCols = 64;
+
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(256)
     gather_kernel(const T *__restrict__ G, int64_t ldg, const int32_t *__restrict__ F,
                   const int32_t *__restrict__ k_dev, int64_t k_host, T *__restrict__ S,
                   int64_t lds) {
-    __shared__ int32_t fr[32], fc[32];
+    __shared__ int32_t fr[kGatherRows], fc[kGatherCols];
     const int64_t k = k_dev ? (int64_t)*k_dev : k_host;
-    const int64_t T_ = cdiv(k, 32);
-    int64_t I, J;
-    tri_tile(blockIdx.x, I, J);
-    if (I >= T_) return;
-    const int64_t a0 = I * 32, b0 = J * 32;
-    if (threadIdx.x < 32) {
-        int64_t a = a0 + threadIdx.x;
-        fr[threadIdx.x] = a < k ? F[a] : 0;
-    } else if (threadIdx.x < 64) {
-        int64_t b = b0 + threadIdx.x - 32;
-        fc[threadIdx.x - 32] = b < k ? F[b] : 0;
+    const int64_t a0 = (int64_t)blockIdx.x * kGatherRows, b0 = (int64_t)blockIdx.y * kGatherCols;
+    if (a0 >= k || b0 >= k || b0 > a0 + kGatherRows - 1) return;  // outside, or above the diagonal
+    const int tid = threadIdx.x;
+    if (tid < kGatherRows) {
+        const int64_t a = a0 + tid;
+        fr[tid] = a < k ? F[a] : 0;
+    } else if (tid < kGatherRows + kGatherCols) {
+        const int64_t b = b0 + tid - kGatherRows;
+        fc[tid - kGatherRows] = b < k ? F[b] : 0;
     }
     __syncthreads();
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t a = a0 + tx;
-    for (int q = ty; q < 32; q += 8) {
-        const int64_t bcol = b0 + q;
-        if (a < k && bcol < k && a >= bcol)
-            S[a + bcol * lds] = G[(int64_t)fr[tx] + (int64_t)fc[q] * ldg];
+    const int tx = tid & 31, ty = tid >> 5;
+    const int64_t a = a0 + 4 * tx;
+    T v[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int q = ty + 8 * j;
+        const int64_t b = b0 + q;
+        const T *gc = G + (int64_t)fc[q] * ldg;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t au = a + u;
+            v[j][u] = (au < k && b < k && au >= b) ? gc[fr[4 * tx + u]] : T(0);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int64_t b = b0 + ty + 8 * j;
+        if (b >= k) continue;
+        T *dst = S + a + b * lds;
+        if (VEC && a + 3 < k && a >= b) {
+            st_vec4<T>(dst, v[j]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (a + u < k && a + u >= b) dst[u] = v[j][u];
+        }
     }
 }
 
@@ -54,8 +81,11 @@ template <typename T>
 cudaError_t launch_gather(cudaStream_t s, const T *G, int64_t ldg, const int32_t *F,
                           const int32_t *k_dev, int64_t k_max, T *S, int64_t lds) {
     if (k_max <= 0) return cudaSuccess;
-    const int64_t t = cdiv(k_max, 32);
-    gather_kernel<T><<<(unsigned)(t * (t + 1) / 2), 256, 0, s>>>(G, ldg, F, k_dev, k_max, S, lds);
+    const dim3 grid((unsigned)cdiv(k_max, kGatherRows), (unsigned)cdiv(k_max, kGatherCols));
+    if (lds % 4 == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0)
+        gather_kernel<T, true><<<grid, 256, 0, s>>>(G, ldg, F, k_dev, k_max, S, lds);
+    else
+        gather_kernel<T, false><<<grid, 256, 0, s>>>(G, ldg, F, k_dev, k_max, S, lds);
     note_launches(1);
     return cudaGetLastError();
 }
