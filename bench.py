@@ -454,7 +454,62 @@ def run_serving(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, pe
         device_ms_sum=float(np.nansum(out["device_ms"])), clocks=clk.summary())
 
 
-EXTRA_WORKLOADS = {"batched": run_batched, "lsqr": run_lsqr, "serving": run_serving}
+def run_kappa_sweep(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, peaks):
+    """Accuracy against conditioning (the experiment of Fig. 1, on our own
+    known-solution generator): for kappa(A) = 1e1 .. 1e7, the error of x
+    against the planted x* for the mixed path (FP32 factor + FP64 refinement,
+    with its FP64 fallback), the plain FP64 normal equations (the paper's
+    method before its final LSQR recompute) and the LSQR path."""
+    import workloads
+
+    eps = float(np.finfo(float).eps)
+    rows, total_ms, total = [], 0.0, 0
+    barrier()
+    with ClockSampler(dev.index) as clk:
+        for e in range(1, 8):
+            kappa = 10.0 ** e
+            prob, xs, _ = workloads.conditioned_dense(args.sweep_m, args.sweep_n, kappa, seed=20040815 + e)
+            p = workloads.dense_to_csr(prob.a, prob.b)
+            A = ts.DeviceCSR.from_problem(p, device=dev)
+            bt = torch.as_tensor(p.b, device=dev)
+            x = torch.empty(p.n, dtype=torch.float64, device=dev)
+            row = {"kappa": kappa, "model_ne_err": kappa * kappa * eps / 10.0}
+            for name, kw in (("mixed", {}), ("fp64_ne", {"precision": "fp64"}), ("lsqr", {"path": "lsqr"})):
+                ctx.solve(A, bt, x_out=x, raise_on_error=False, **kw)
+                ms = []
+                for _ in range(max(1, args.steps // 5)):
+                    _, info = ctx.solve(A, bt, x_out=x, raise_on_error=False, **kw)
+                    ms.append(info.time_ms)
+                ok = info.status == ts.OK  # x_out is written only on success
+                xv = x.cpu().numpy()
+                row[name] = {"status": int(info.status),
+                             "rel_err": float(np.linalg.norm(xv - xs) / np.linalg.norm(xs)) if ok else None,
+                             "ms": float(np.median(ms)) if ok else None}
+                if name == "mixed":
+                    row[name]["fallback_used"] = int(info.fallback_used)
+                    if ok:
+                        total_ms += sum(ms)
+                        total += len(ms)
+            _, info = ctx.solve(A, bt, x_out=x, raise_on_error=False, cond_est=1)
+            row["cond_est_FF"] = float(info.cond_est) if info.status == ts.OK else None
+            rows.append(row)
+        barrier()
+    dev_s = max_over_ranks(total_ms * 1e-3)
+    if rank != 0:
+        return None
+    return _common_line(
+        "NNLS accuracy vs condition number (Fig. 1): rel. error of x per path", ws * total / dev_s, "solves/s",
+        ws, args, dev_s * 1e3 / total, "f32+f64",
+        {"workload": f"kappa_sweep: dense {args.sweep_m}x{args.sweep_n}, A = U diag(sigma) V^T with sigma "
+                     f"geometric from 1 to 1/kappa, kappa = 1e1..1e7, known solution x* (30% zeros, half "
+                     f"of them active with y* ~ U(0.1,1)/kappa), seeds 20040816..20040822",
+         "precision": "mixed (FP64 fallback when the FP32 factor fails); fp64_ne and lsqr alongside",
+         "l2": "not relevant: an accuracy sweep; value = mixed-path solves/s over its successful solves"},
+        sweep=rows, clocks=clk.summary(), gpu_launches=int(info.kernel_launches))
+
+
+EXTRA_WORKLOADS = {"batched": run_batched, "lsqr": run_lsqr, "serving": run_serving,
+                   "kappa_sweep": run_kappa_sweep}
 
 
 def main():
@@ -469,6 +524,8 @@ def main():
                     choices=("larger_sparse",) + tuple(EXTRA_WORKLOADS))
     ap.add_argument("--requests", type=int, default=200, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per second")
+    ap.add_argument("--sweep-m", type=int, default=1200, help="kappa_sweep workload: rows")
+    ap.add_argument("--sweep-n", type=int, default=800, help="kappa_sweep workload: columns")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -90,6 +90,13 @@ typedef struct {
                             sign or zeroing decision of the next exchange can change (only signs
                             matter before the last pivot, Section 3; the last pivot is always
                             refined to rel_tol); 1: refine every pivot to rel_tol */
+    int32_t no_fallback; /* MIXED: 0 (default): if the refinement on the FP32 factor stagnates
+                            (the factor is too inaccurate for this conditioning), the solve is
+                            redone with an FP64 factor and FP64 refinement (info.fallback_used);
+                            1: return TSNNLS_ENOCONV instead */
+    int32_t cond_est;    /* 1: estimate kappa_1((A^T A)_FF) at the last pivot into info.cond_est
+                            (a dpocon-style 1-norm estimate, Section 3; a few extra solves);
+                            0 (default): skip */
 } tsnnls_opts;
 
 typedef struct {
@@ -102,6 +109,9 @@ typedef struct {
     double last_rel_step;    /* ||dx_F||_inf / ||x_F||_inf of the last refinement step */
     double time_ms;          /* device time of the solve, CUDA events */
     int64_t kernel_launches; /* kernels this call launched */
+    double cond_est;         /* opts.cond_est: estimated kappa_1((A^T A)_FF) at the last pivot, else 0 */
+    int32_t fallback_used;   /* 1 if a MIXED solve was redone in FP64 (opts.no_fallback) */
+    int32_t reserved;
 } tsnnls_info;
 
 typedef struct tsnnls_ctx tsnnls_ctx;

@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("zero_tol", ctypes.c_double),
                 ("p_max", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("max_refine", ctypes.c_int32), ("full_refine", ctypes.c_int32)]
+                ("max_refine", ctypes.c_int32), ("full_refine", ctypes.c_int32),
+                ("no_fallback", ctypes.c_int32), ("cond_est", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +58,8 @@ class Info(ctypes.Structure):
                 ("refine_steps", ctypes.c_int32), ("nF", ctypes.c_int32),
                 ("path_used", ctypes.c_int32), ("precision_used", ctypes.c_int32),
                 ("last_rel_step", ctypes.c_double), ("time_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("cond_est", ctypes.c_double),
+                ("fallback_used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -135,6 +135,22 @@ cudaError_t launch_gram_row_bound(cudaStream_t s, int64_t m, int64_t n, const in
 // that may still fall on either side of 0 or +-zero_tol.
 cudaError_t launch_settled(cudaStream_t s, int64_t n, const uint8_t *inF, const double *x,
                            const double *sv, const double *c, double E, double zero_tol, DevStatus *st);
+// 1-norm estimate helpers (see exchange.cu): probe fill (mode 0 uniform
+// 1/k, 1 unit vector e_j, 2 alternating (-1)^i (1 + i/(k-1))), ||y||_1 and
+// sign(y) into out[0] / xi, max |z_i| / first argmax / z^T x (x uniform for
+// mode 0, e_jprev for mode 1) into out[1..3].
+template <typename T>
+cudaError_t launch_est_fill(cudaStream_t s, T *v, int64_t k, int32_t mode, int64_t j);
+template <typename T>
+cudaError_t launch_est_norm_sign(cudaStream_t s, const T *y, int64_t k, T *xi, double *out);
+template <typename T>
+cudaError_t launch_est_argmax(cudaStream_t s, const T *z, int64_t k, int32_t mode, int64_t jprev, double *out);
+// *out = ||G_FF||_1 for the symmetric block whose lower triangle G (ldg) holds;
+// scratch: gram_norm_scratch_bytes(k) bytes.
+size_t gram_norm_scratch_bytes(int64_t k);
+template <typename T>
+cudaError_t launch_gram_norm1(cudaStream_t s, const T *G, int64_t ldg, const int32_t *F, int64_t k,
+                              double *scratch, double *out);
 cudaError_t launch_y_from_s(cudaStream_t s, int64_t n, const double *sv, const uint8_t *inF,
                             double *y);
 

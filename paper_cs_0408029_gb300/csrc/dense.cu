@@ -90,6 +90,104 @@ cudaError_t launch_gather(cudaStream_t s, const T *G, int64_t ldg, const int32_t
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// ||G_FF||_1 of the symmetric block whose lower triangle G holds: column j
+// sums |G(F_i, F_j)| over i >= j (its own column) and over i < j (row j of
+// the lower triangle).  Per 128 x 64 tile: column sums over the tile's rows
+// go to colpart[I][b], row sums over its strictly lower entries to
+// rowpart[J][a] (fixed slots, so the totals are reduced in a fixed order).
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    gram_norm_part_kernel(const T *__restrict__ G, int64_t ldg, const int32_t *__restrict__ F, int64_t k,
+                          double *__restrict__ colpart, double *__restrict__ rowpart) {
+    __shared__ int32_t fr[kGatherRows], fc[kGatherCols];
+    __shared__ double rs[8][kGatherRows];
+    const int64_t a0 = (int64_t)blockIdx.x * kGatherRows, b0 = (int64_t)blockIdx.y * kGatherCols;
+    if (a0 >= k || b0 >= k || b0 > a0 + kGatherRows - 1) return;
+    const int tid = threadIdx.x;
+    if (tid < kGatherRows) {
+        const int64_t a = a0 + tid;
+        fr[tid] = a < k ? F[a] : 0;
+    } else if (tid < kGatherRows + kGatherCols) {
+        const int64_t b = b0 + tid - kGatherRows;
+        fc[tid - kGatherRows] = b < k ? F[b] : 0;
+    }
+    __syncthreads();
+    const int tx = tid & 31, ty = tid >> 5;
+    const int64_t a = a0 + 4 * tx;
+    double row[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int q = ty + 8 * j;
+        const int64_t b = b0 + q;
+        const T *gc = G + (int64_t)fc[q] * ldg;
+        double col = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t au = a + u;
+            const double v = (au < k && b < k && au >= b) ? fabs((double)gc[fr[4 * tx + u]]) : 0.0;
+            col += v;
+            if (au > b) row[u] += v;
+        }
+        for (int o = 16; o > 0; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
+        if (tx == 0 && b < k) colpart[(int64_t)blockIdx.x * k + b] = col;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) rs[ty][4 * tx + u] = row[u];
+    __syncthreads();
+    if (tid < kGatherRows && a0 + tid < k) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += rs[w][tid];
+        rowpart[(int64_t)blockIdx.y * k + a0 + tid] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+    gram_norm_reduce_kernel(const double *__restrict__ colpart, const double *__restrict__ rowpart, int64_t k,
+                            int64_t nrt, int64_t nct, double *__restrict__ out) {
+    __shared__ double sh[32];
+    double best = 0.0;
+    for (int64_t j = threadIdx.x; j < k; j += blockDim.x) {
+        double t = 0.0;
+        for (int64_t I = 0; I < nrt; ++I) t += colpart[I * k + j];
+        for (int64_t J = 0; J < nct; ++J) t += rowpart[J * k + j];
+        best = fmax(best, t);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        best = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (threadIdx.x == 0) *out = best;
+    }
+}
+
+size_t gram_norm_scratch_bytes(int64_t k) {
+    return (size_t)(cdiv(k, kGatherRows) + cdiv(k, kGatherCols)) * (size_t)std::max<int64_t>(k, 1) * 8;
+}
+
+template <typename T>
+cudaError_t launch_gram_norm1(cudaStream_t s, const T *G, int64_t ldg, const int32_t *F, int64_t k,
+                              double *scratch, double *out) {
+    if (k <= 0) return cudaMemsetAsync(out, 0, sizeof(double), s);
+    const int64_t nrt = cdiv(k, kGatherRows), nct = cdiv(k, kGatherCols);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, gram_norm_scratch_bytes(k), s);
+    if (e != cudaSuccess) return e;
+    double *colpart = scratch, *rowpart = scratch + nrt * k;
+    gram_norm_part_kernel<T><<<dim3((unsigned)nrt, (unsigned)nct), 256, 0, s>>>(G, ldg, F, k, colpart, rowpart);
+    gram_norm_reduce_kernel<<<1, 1024, 0, s>>>(colpart, rowpart, k, nrt, nct, out);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gram_norm1<float>(cudaStream_t, const float *, int64_t, const int32_t *, int64_t,
+                                             double *, double *);
+template cudaError_t launch_gram_norm1<double>(cudaStream_t, const double *, int64_t, const int32_t *, int64_t,
+                                              double *, double *);
+
 template cudaError_t launch_gather<float>(cudaStream_t, const float *, int64_t, const int32_t *,
                                           const int32_t *, int64_t, float *, int64_t);
 template cudaError_t launch_gather<double>(cudaStream_t, const double *, int64_t,

@@ -198,11 +198,13 @@ struct Sync {
 
 template <typename T>
 int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,
-                 const tsnnls_opts &o, tsnnls_info *info, const SolveExtras *ex) {
+                 const tsnnls_opts &o, tsnnls_info *info, const SolveExtras *ex, bool force_refine) {
     (void)ctx;
     const int64_t m = A.m, n = A.n, nnz = A.nnz;
     const bool host_in = A.on_device == 0;
-    const bool mixed = o.precision == TSNNLS_MIXED;
+    // refinement with FP64 residuals: always on the FP32 factor; on the FP64
+    // factor only when redoing a MIXED solve whose FP32 refinement stagnated
+    const bool mixed = o.precision == TSNNLS_MIXED || force_refine;
     const int64_t ldg = round_up(n, 32);
     const int32_t max_iter = o.max_iter > 0 ? o.max_iter : (int32_t)std::min<int64_t>(10 * n + 100, INT32_MAX);
     cudaStream_t s = lane.stream;
@@ -211,6 +213,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
     int refine_total = 0;
     double last_rel = 0.0;
     int64_t trace_rows = 0;
+    double cond = 0.0;  // opts.cond_est
     const int64_t launch0 = launches_so_far();
 
     Carve cv;
@@ -454,6 +457,59 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             prof_end(lane, 17.0 * n, 0.0);
             ++trace_rows;
         }
+        if (status == TSNNLS_OK && o.cond_est && k > 0) {
+            // kappa_1 of the last pivot's (A^T A)_FF: its 1-norm times an
+            // estimate of ||(A^T A)_FF^-1||_1 from solves with the factor still
+            // in S (Hager's method with Higham's refinements, as in dpocon;
+            // Section 3 consults dpocon for the final recompute)
+            double *dv = nullptr, *part = nullptr;
+            T *xi = nullptr;
+            double h[8] = {};
+            auto solve = [&]() { return launch_chol_solve<T>(s, S, k, lds, rhs, trsv_scratch, lane.st_dev); };
+            auto fetch = [&]() -> cudaError_t {
+                cudaError_t e = cudaMemcpyAsync(h, dv, sizeof(h), cudaMemcpyDeviceToHost, s);
+                return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+            };
+            cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&dv), sizeof(h), s);
+            if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&xi), sizeof(T) * k, s);
+            if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&part), gram_norm_scratch_bytes(k), s);
+            if (e == cudaSuccess) e = launch_gram_norm1<T>(s, G, ldg, F, k, part, dv + 4);
+            // x = (1/k) 1
+            if (e == cudaSuccess) e = launch_est_fill<T>(s, rhs, k, 0, 0);
+            if (e == cudaSuccess) e = solve();
+            if (e == cudaSuccess) e = launch_est_norm_sign<T>(s, rhs, k, xi, dv);
+            if (e == cudaSuccess) e = fetch();
+            double est = h[0];
+            int32_t mode = 0;
+            int64_t jprev = 0;
+            for (int it = 0; e == cudaSuccess && it < 5 && k > 1; ++it) {
+                // z = G^-1 sign(y); stop once ||z||_inf <= z^T x, else x = e_j, j = argmax |z_j|
+                e = cudaMemcpyAsync(rhs, xi, sizeof(T) * k, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess) e = solve();
+                if (e == cudaSuccess) e = launch_est_argmax<T>(s, rhs, k, mode, jprev, dv);
+                if (e == cudaSuccess) e = fetch();
+                if (e != cudaSuccess || (it > 0 && h[1] <= h[3])) break;
+                const int64_t j = (int64_t)h[2];
+                e = launch_est_fill<T>(s, rhs, k, 1, j);
+                if (e == cudaSuccess) e = solve();
+                if (e == cudaSuccess) e = launch_est_norm_sign<T>(s, rhs, k, xi, dv);
+                if (e == cudaSuccess) e = fetch();
+                if (e != cudaSuccess || h[0] <= est) break;
+                est = h[0];
+                mode = 1;
+                jprev = j;
+            }
+            // the alternating probe guards against a poor first direction
+            if (e == cudaSuccess) e = launch_est_fill<T>(s, rhs, k, 2, 0);
+            if (e == cudaSuccess) e = solve();
+            if (e == cudaSuccess) e = launch_est_norm_sign<T>(s, rhs, k, xi, dv);
+            if (e == cudaSuccess) e = fetch();
+            if (e == cudaSuccess) cond = h[4] * std::max(est, 2.0 * h[0] / (3.0 * (double)k));
+            if (dv) cudaFreeAsync(dv, s);
+            if (xi) cudaFreeAsync(xi, s);
+            if (part) cudaFreeAsync(part, s);
+            TRY_CUDA(e);
+        }
         if (status == TSNNLS_OK) {
             TRY_CUDA(cudaEventRecord(lane.ev1, s));
             const cudaMemcpyKind kind = host_in ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -468,6 +524,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         if (info) {
             info->iters = lane.st_host->iters;
             info->nF = lane.st_host->k;
+            info->cond_est = cond;
         }
     }
 cleanup:
@@ -518,8 +575,27 @@ int solve_on_lane(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b
     if (choose_path(A, o, ctx.budget) == TSNNLS_PATH_LSQR)
         return solve_lsqr(ctx, lane, A, b, x_out, o, info, extras);
     if (o.precision == TSNNLS_FP64)
-        return solve_factor<double>(ctx, lane, A, b, x_out, o, info, extras);
-    return solve_factor<float>(ctx, lane, A, b, x_out, o, info, extras);
+        return solve_factor<double>(ctx, lane, A, b, x_out, o, info, extras, false);
+    int st = solve_factor<float>(ctx, lane, A, b, x_out, o, info, extras, false);
+    if ((st == TSNNLS_ENOCONV || st == TSNNLS_ENOTPD) && o.no_fallback == 0) {
+        // kappa(A_F)^2 too large for the FP32 factor (it loses positive
+        // definiteness, or no longer preconditions the refinement): the FP64
+        // factor with the same FP64 refinement
+        tsnnls_opts o64 = o;
+        o64.precision = TSNNLS_FP64;
+        std::memset(lane.st_host, 0, sizeof(DevStatus));
+        const tsnnls_info first = info ? *info : tsnnls_info{};
+        st = solve_factor<double>(ctx, lane, A, b, x_out, o64, info, extras, true);
+        if (st == TSNNLS_ENOMEM) st = first.status;  // no room for the FP64 copy: report the cause
+        if (info) {
+            info->status = st;
+            info->fallback_used = 1;
+            info->refine_steps += first.refine_steps;
+            info->kernel_launches += first.kernel_launches;
+            info->time_ms += first.time_ms;
+        }
+    }
+    return st;
 }
 
 }  // namespace tsnnls

@@ -344,6 +344,121 @@ cudaError_t launch_settled(cudaStream_t s, int64_t n, const uint8_t *inF, const 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Vector steps of the 1-norm estimate of G^-1 (Hager's method as refined by
+// Higham, the estimator behind LAPACK's dpocon): fill a probe vector, take
+// ||y||_1 and sign(y), find max_i |z_i| and z^T x.  One CTA each; fixed-order
+// reductions.  out: [0] ||y||_1, [1] max |z_i|, [2] its first index, [3] z^T x.
+
+template <typename T>
+__global__ void est_fill_kernel(T *__restrict__ v, int64_t k, int32_t mode, int64_t j) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        double x;
+        if (mode == 0) x = 1.0 / (double)k;                                  // uniform
+        else if (mode == 1) x = (i == j) ? 1.0 : 0.0;                          // unit vector
+        else x = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(k > 1 ? k - 1 : 1));  // alternating
+        v[i] = (T)x;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kExThreads)
+    est_norm_sign_kernel(const T *__restrict__ y, int64_t k, T *__restrict__ xi, double *out) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < k; i += kExThreads) {
+        const double v = (double)y[i];
+        a += fabs(v);
+        xi[i] = v >= 0.0 ? T(1) : T(-1);
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        a = sh[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (threadIdx.x == 0) out[0] = a;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kExThreads)
+    est_argmax_kernel(const T *__restrict__ z, int64_t k, int32_t mode, int64_t jprev, double *out) {
+    __shared__ double shv[32], shd[32];
+    __shared__ int64_t shi[32];
+    double best = -1.0, dot = 0.0;
+    int64_t arg = 0;
+    for (int64_t i = threadIdx.x; i < k; i += kExThreads) {
+        const double v = (double)z[i];
+        if (fabs(v) > best) {
+            best = fabs(v);
+            arg = i;
+        }
+        if (mode == 0) dot += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int64_t oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && oa < arg)) {
+            best = ob;
+            arg = oa;
+        }
+        dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        shv[warp] = best;
+        shi[warp] = arg;
+        shd[warp] = dot;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        best = shv[lane];
+        arg = shi[lane];
+        dot = shd[lane];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int64_t oa = __shfl_xor_sync(0xffffffffu, arg, o);
+            if (ob > best || (ob == best && oa < arg)) {
+                best = ob;
+                arg = oa;
+            }
+            dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        }
+        if (lane == 0) {
+            out[1] = best;
+            out[2] = (double)arg;
+            out[3] = mode == 0 ? dot / (double)k : (double)z[jprev];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_est_fill(cudaStream_t s, T *v, int64_t k, int32_t mode, int64_t j) {
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(k, 256), 152 * 4));
+    est_fill_kernel<T><<<g, 256, 0, s>>>(v, k, mode, j);
+    note_launches(1);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_est_norm_sign(cudaStream_t s, const T *y, int64_t k, T *xi, double *out) {
+    est_norm_sign_kernel<T><<<1, kExThreads, 0, s>>>(y, k, xi, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_est_argmax(cudaStream_t s, const T *z, int64_t k, int32_t mode, int64_t jprev, double *out) {
+    est_argmax_kernel<T><<<1, kExThreads, 0, s>>>(z, k, mode, jprev, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t launch_est_fill<float>(cudaStream_t, float *, int64_t, int32_t, int64_t);
+template cudaError_t launch_est_fill<double>(cudaStream_t, double *, int64_t, int32_t, int64_t);
+template cudaError_t launch_est_norm_sign<float>(cudaStream_t, const float *, int64_t, float *, double *);
+template cudaError_t launch_est_norm_sign<double>(cudaStream_t, const double *, int64_t, double *, double *);
+template cudaError_t launch_est_argmax<float>(cudaStream_t, const float *, int64_t, int32_t, int64_t, double *);
+template cudaError_t launch_est_argmax<double>(cudaStream_t, const double *, int64_t, int32_t, int64_t, double *);
+
 // Eq. 5 from s = A^T (b - A x): y_G = -s_G, y_F = 0.
 __global__ void y_from_s_kernel(int64_t n, const double *__restrict__ sv,
                                 const uint8_t *__restrict__ inF, double *__restrict__ y) {

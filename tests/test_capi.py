@@ -49,3 +49,32 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.tsnnls_submit(None, None, None, None, None, None) == ts.EINVAL
     assert lib.tsnnls_poll(None, 1, None) == ts.EINVAL
     assert lib.tsnnls_ctx_create(None, 0, 0) == ts.EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler
+    gives the header's structs."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = []
+    structs = (("tsnnls_opts", ts.Opts), ("tsnnls_info", ts.Info), ("tsnnls_csr", ts.CSR),
+               ("tsnnls_queue_stats", ts.QueueStats), ("tsnnls_phase_stat", ts.PhaseStat))
+    for cname, py in structs:
+        checks.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            checks.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tsnnls.h"\nint main(void) {\n'
+                   + "\n".join(checks) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for cname, py in structs:
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)

@@ -227,6 +227,64 @@ def test_settle_stop_matches_full_refinement(ts, ctx, oracle_mod):
     assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x1)
 
 
+def test_fallback_to_fp64_when_the_fp32_factor_fails(ts, ctx):
+    """kappa(A) = 1e5 puts kappa(A^T A) = 1e10 beyond an FP32 factor: the
+    mixed solve either loses positive definiteness or its refinement
+    stagnates, and is redone with the FP64 factor and the same FP64
+    refinement, whose error stays near kappa eps (the normal equations alone
+    give up to kappa^2 eps, Section 2)."""
+    kappa = 1e5
+    prob, xs, _ = workloads.conditioned_dense(300, 200, kappa, seed=51)
+    p = workloads.dense_to_csr(prob.a, prob.b)
+    A = ts.HostCSR.from_problem(p)
+    with pytest.raises(ts.TsnnlsError) as err:
+        ctx.solve_ex(A, p.b, no_fallback=1)
+    assert err.value.status in (ts.ENOCONV, ts.ENOTPD)
+    x, _, _, _, info = ctx.solve_ex(A, p.b)
+    assert info.fallback_used == 1 and info.precision_used == ts.FP64
+    eps = np.finfo(float).eps
+    assert np.linalg.norm(x - xs) <= 1e3 * kappa * eps * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("kappa", [1e1, 1e3, 1e5])
+def test_accuracy_vs_condition(ts, ctx, kappa):
+    """Fig. 1's experiment on the known-solution generator: the plain FP64
+    normal equations stay within the paper's c kappa^2 eps (c = 1 here), the
+    refined mixed path (FP64 fallback at kappa = 1e5) near kappa eps."""
+    eps = np.finfo(float).eps
+    prob, xs, _ = workloads.conditioned_dense(240, 160, kappa, seed=53)
+    p = workloads.dense_to_csr(prob.a, prob.b)
+    A = ts.HostCSR.from_problem(p)
+    paths = (("mixed", {}), ("fp64", {"precision": "fp64"}))
+    if kappa <= 1e1:  # restarted LSQR needs O(kappa) iterations: past its limits on these dense cases
+        paths += (("lsqr", {"path": "lsqr"}),)
+    err = {}
+    for name, kw in paths:
+        x, _ = ctx.solve(A, p.b, **kw)
+        err[name] = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+    assert err["fp64"] <= kappa ** 2 * eps + 1e-14
+    assert err["mixed"] <= 1e3 * kappa * eps
+    if "lsqr" in err:
+        assert err["lsqr"] <= 1e3 * kappa * eps
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4])
+def test_condition_estimate(ts, ctx, kappa):
+    """The 1-norm condition estimate of (A^T A)_FF at the last pivot is a
+    lower bound of the exact kappa_1 (to rounding) within the usual factor
+    of the estimator."""
+    prob, _, _ = workloads.conditioned_dense(300, 200, kappa, seed=52)
+    p = workloads.dense_to_csr(prob.a, prob.b)
+    A = ts.HostCSR.from_problem(p)
+    _, _, inF, _, info = ctx.solve_ex(A, p.b, cond_est=1)
+    af = prob.a[:, inF]
+    g = af.T @ af
+    exact = np.linalg.norm(g, 1) * np.linalg.norm(np.linalg.inv(g), 1)
+    assert exact / 10 <= info.cond_est <= 1.05 * exact, (info.cond_est, exact)
+    _, _, _, _, info0 = ctx.solve_ex(A, p.b)
+    assert info0.cond_est == 0.0
+
+
 # ---------------------------------------------------------------------------
 # degenerate and special cases
 
