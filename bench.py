@@ -214,8 +214,8 @@ NCU_TRAFFIC = {
     "factor_diag": 107_008,
     "factor_panel": None,  # only the 4-CTA head launch was captured for the current kernel
     "factor_update": 66_578_944 + 6_349_056,
-    "trsv": (72_824_320 + 819_968 + 72_833_024 + 732_160) // 2,
-    "gather": 96_258_560 + 39_352_320,
+    "trsv": (72_816_640 + 697_344 + 72_828_160 + 670_720) // 2,
+    "gather": 96_223_744 + 33_048_064,
     "gram": 10_600_704 + 70_255_104,
     "spmv": (5_289_984 + 5_129_984) // 2,
 }
