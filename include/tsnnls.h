@@ -97,6 +97,10 @@ typedef struct {
     int32_t cond_est;    /* 1: estimate kappa_1((A^T A)_FF) at the last pivot into info.cond_est
                             (a dpocon-style 1-norm estimate, Section 3; a few extra solves);
                             0 (default): skip */
+    int32_t no_reuse;    /* MIXED: 0 (default): a pivot that adds and removes only a few variables
+                            since the last factorisation is solved on that factor, bordered
+                            (info.factor_reuses); 1: refactor at every pivot, as the paper does */
+    int32_t reserved;
 } tsnnls_opts;
 
 typedef struct {
@@ -111,7 +115,7 @@ typedef struct {
     int64_t kernel_launches; /* kernels this call launched */
     double cond_est;         /* opts.cond_est: estimated kappa_1((A^T A)_FF) at the last pivot, else 0 */
     int32_t fallback_used;   /* 1 if a MIXED solve was redone in FP64 (opts.no_fallback) */
-    int32_t reserved;
+    int32_t factor_reuses;   /* pivots solved on an earlier pivot's factor, bordered (MIXED) */
 } tsnnls_info;
 
 typedef struct tsnnls_ctx tsnnls_ctx;
@@ -225,7 +229,8 @@ int tsnnls_batch_set_panel(int32_t precision, const int32_t *nb);
 #define TSNNLS_PHASE_FACTOR_DIAG 9     /* per kernel inside FACTOR: diagonal block factor + inverse */
 #define TSNNLS_PHASE_FACTOR_PANEL 10   /*   block column below it (X = B W^T) */
 #define TSNNLS_PHASE_FACTOR_UPDATE 11  /*   trailing update (tensor cores in MIXED) */
-#define TSNNLS_NUM_PHASES 12
+#define TSNNLS_PHASE_REUSE 12          /* setup of a bordered solve on an earlier factor (opts.no_reuse) */
+#define TSNNLS_NUM_PHASES 13
 
 typedef struct {
     double ms;          /* summed device time */

@@ -30,7 +30,7 @@ EXPORTS = (
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
-          "factor_diag", "factor_panel", "factor_update")
+          "factor_diag", "factor_panel", "factor_update", "reuse")
 
 
 class TsnnlsError(RuntimeError):
@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
                 ("p_max", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("full_refine", ctypes.c_int32),
-                ("no_fallback", ctypes.c_int32), ("cond_est", ctypes.c_int32)]
+                ("no_fallback", ctypes.c_int32), ("cond_est", ctypes.c_int32),
+                ("no_reuse", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -59,7 +60,7 @@ class Info(ctypes.Structure):
                 ("path_used", ctypes.c_int32), ("precision_used", ctypes.c_int32),
                 ("last_rel_step", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("cond_est", ctypes.c_double),
-                ("fallback_used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fallback_used", ctypes.c_int32), ("factor_reuses", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -26,6 +26,8 @@ struct DevStatus {
     int32_t timeout;    // 1 if a bounded device wait gave up
     int32_t maxiter_hit;
     int32_t unsettled;  // entries whose sign / zeroing decision the last check left open
+    int32_t border_a;   // variables in F but not in the factored base set (border.cu)
+    int32_t border_r;   // variables of the base set no longer in F
     double dnorm;       // ||dx_F||_inf of the last refinement step
     double xnorm;       // ||x_F||_inf after it
 };
@@ -109,6 +111,13 @@ size_t chol_solve_scratch_bytes(int64_t k, size_t elem);
 template <typename T>
 cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs,
                               void *scratch, DevStatus *st);
+// the two halves: rhs <- L^-1 rhs, rhs <- L^-T rhs
+template <typename T>
+cudaError_t launch_trsv_fwd(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
+                            DevStatus *st);
+template <typename T>
+cudaError_t launch_trsv_bwd(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
+                            DevStatus *st);
 
 // out = alpha * M x + beta * z over a CSR (or CSC viewed as CSR of M^T).
 cudaError_t launch_spmv(cudaStream_t s, int64_t rows, const int64_t *ptr, const int32_t *idx,
@@ -127,6 +136,36 @@ cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, const int32_t *F,
 template <typename T>
 cudaError_t launch_update_x(cudaStream_t s, const T *delta, const int32_t *F, int64_t k,
                             double *x, DevStatus *st);
+// ---- reuse of a factor across pivots (border.cu) ----
+constexpr int kBorderMax = 32;  // added and removed variables handled at most (each)
+struct BorderBuffers {
+    int32_t *Bl;      // base list (the F of the factored pivot), n entries
+    uint8_t *inB;     // base flags, n entries
+    int32_t *Ul;      // U = base list with removed entries -1, then the added ones
+    int32_t *Al;      // added variables (<= kBorderMax)
+    int32_t *Rpos;    // base positions of the removed ones (<= kBorderMax)
+    void *Pt;         // P^T = L^-1 G_BA, kb x a, leading dimension ldp
+    void *Z;          // H^-1 E_R, u x r, leading dimension ldz
+    double *GAA, *Lq, *Lc;  // kBorderMax^2 each: G_AA, factor of G_AA - P P^T, factor of Z_R
+    double *mu;
+    int32_t *bad;     // set by the setup when a small factor is not positive definite
+    int64_t ldp, ldz;
+};
+size_t border_bytes(int64_t n, size_t elem);
+BorderBuffers border_carve(void *base, int64_t n, size_t elem);
+// A, R and U for the new flags against the base (counts in st->border_a / border_r)
+cudaError_t launch_border_diff(cudaStream_t s, int64_t n, const uint8_t *inF, const BorderBuffers &b, int64_t kb,
+                               DevStatus *st);
+// P^T, the factor of G_AA - P P^T, Z and the factor of Z_R for a <= kBorderMax
+// added and r <= kBorderMax removed variables (L: the base factor, kb x kb)
+template <typename T>
+cudaError_t launch_border_setup(cudaStream_t s, const T *G, int64_t ldg, const T *L, int64_t kb, int64_t lds,
+                                int a, int r, const BorderBuffers &b, void *trsv_scratch, DevStatus *st);
+// z (u = kb + a entries, U order) <- solution of G_F'F' z_F' = z_F' with z_R = 0
+template <typename T>
+cudaError_t launch_border_solve(cudaStream_t s, const T *L, int64_t kb, int64_t lds, int a, int r,
+                                const BorderBuffers &b, T *z, void *trsv_scratch, DevStatus *st);
+
 // c = |A|^T (|A| 1): c_i bounds sum_f |(A^T A)_if| (t: m doubles of scratch).
 cudaError_t launch_gram_row_bound(cudaStream_t s, int64_t m, int64_t n, const int64_t *row_ptr,
                                   const double *val, const int64_t *col_ptr, const int32_t *row_idx,

@@ -154,6 +154,7 @@ size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     c.take<uint8_t>(n);
     c.take<int32_t>(n);
     c.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
+    c.take<char>(border_bytes(n, sizeof(T)));  // reuse of a factor across pivots
     if (sizeof(T) == 4) {
         c.take<float>((size_t)n * 128);  // K-major hi / lo panel copies for the tensor-core update
         c.take<float>((size_t)n * 128);
@@ -195,6 +196,12 @@ struct Sync {
             goto cleanup;                       \
         }                                       \
     } while (0)
+
+// a + 2 r triangular-solve passes of setup at most for reusing a factor: a
+// gather and refactorisation cost about 30 passes at any k >= 1024 (both
+// scale with the number of 128-wide block steps), and the bordered solves
+// add a little to every refinement step
+constexpr int kReuseBudget = 20;
 
 template <typename T>
 int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,
@@ -267,6 +274,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         uint8_t *inF = cv.take<uint8_t>(n);
         int32_t *F = cv.take<int32_t>(n);
         void *trsv_scratch = cv.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
+        const BorderBuffers bb = border_carve(cv.take<char>(border_bytes(n, sizeof(T))), n, sizeof(T));
         TcPanel tc;
         if (sizeof(T) == 4) {
             float *xhi = cv.take<float>((size_t)n * 128);
@@ -322,19 +330,33 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         // correction `prev`.  allow_settle: stop before rel_tol once the
         // settled test passes (*settled is then set).
         int64_t k = 0, lds = 32;
+        // The pivot's solver: a fresh factor of G_FF in S (list F, k), or the
+        // factor of an earlier base set B (kb, ldsb) reused with ba added and
+        // br removed variables (list U, kb + ba entries; border.cu).
+        bool base_valid = false, reuse = false;
+        int64_t kb = 0, ldsb = 32;
+        int ba = 0, br = 0;
+        int reuses = 0;
+        auto sol_list = [&]() -> const int32_t * { return reuse ? bb.Ul : F; };
+        auto sol_len = [&]() -> int64_t { return reuse ? kb + ba : k; };
+        auto pivot_solve = [&](T *v) -> cudaError_t {
+            return reuse ? launch_border_solve<T>(s, S, kb, ldsb, ba, br, bb, v, trsv_scratch, lane.st_dev)
+                         : launch_chol_solve<T>(s, S, k, lds, v, trsv_scratch, lane.st_dev);
+        };
         auto refine = [&](int steps, double prev, bool allow_settle, bool *settled) -> int {
             *settled = false;
             for (;;) {
-                const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
+                const int64_t kl = reuse ? kb : k;
+                const double tri = 0.5 * (double)kl * (double)(kl + 1) * sizeof(T);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                cudaError_t e = launch_gather_rhs<T>(s, sv, F, k, rhs);
-                prof_end(lane, (12.0 + sizeof(T)) * k, 0.0);
+                cudaError_t e = launch_gather_rhs<T>(s, sv, sol_list(), sol_len(), rhs);
+                prof_end(lane, (12.0 + sizeof(T)) * sol_len(), 0.0);
                 prof_begin(lane, TSNNLS_PHASE_TRSV);
-                if (e == cudaSuccess) e = launch_chol_solve<T>(s, S, k, lds, rhs, trsv_scratch, lane.st_dev);
-                prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * k, 2.0 * (double)k * (double)k);
+                if (e == cudaSuccess) e = pivot_solve(rhs);
+                prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * kl, 2.0 * (double)kl * (double)kl);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                if (e == cudaSuccess) e = launch_update_x<T>(s, rhs, F, k, x, lane.st_dev);
-                prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
+                if (e == cudaSuccess) e = launch_update_x<T>(s, rhs, sol_list(), sol_len(), x, lane.st_dev);
+                prof_end(lane, (20.0 + sizeof(T)) * sol_len(), 0.0);
                 if (e == cudaSuccess) e = sync.post();
                 if (e == cudaSuccess) e = residual();
                 if (e == cudaSuccess) e = sync.wait();
@@ -373,6 +395,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             prof_begin(lane, TSNNLS_PHASE_EXCHANGE);
             TRY_CUDA(launch_exchange(s, n, x, y, inF, F, o.zero_tol, o.p_max, max_iter,
                                      lane.st_host->iters > 0 ? 1 : 0, lane.st_dev));
+            if (base_valid) TRY_CUDA(launch_border_diff(s, n, inF, bb, kb, lane.st_dev));
             prof_end(lane, 17.0 * n + 17.0 * n + 4.0 * n, 0.0);
             TRY_CUDA(sync.read());
             const DevStatus st = *lane.st_host;
@@ -404,30 +427,60 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             }
             k = st.k;
             lds = round_up(std::max<int64_t>(k, 1), 32);
+            // Reuse the base factor when few variables moved since it was
+            // taken: a + 2 r triangular solves of setup against a factorisation
+            // (refinement path only; the plain FP64 path refactors every
+            // pivot as the paper does, and the condition estimate wants the
+            // factor of the last F itself).
+            reuse = false;
+            if (mixed && base_valid && k > 0 && o.cond_est == 0 && o.no_reuse == 0 && st.border_a <= kBorderMax &&
+                st.border_r <= kBorderMax && st.border_a + 2 * st.border_r <= kReuseBudget && kb >= 1024) {
+                ba = st.border_a;
+                br = st.border_r;
+                prof_begin(lane, TSNNLS_PHASE_REUSE);
+                TRY_CUDA(launch_border_setup<T>(s, G, ldg, S, kb, ldsb, ba, br, bb, trsv_scratch, lane.st_dev));
+                prof_end(lane, (double)(ba + 2 * br) * 0.5 * (double)kb * (double)kb * sizeof(T), 0.0);
+                int32_t bad = 0;
+                TRY_CUDA(cudaMemcpyAsync(&bad, bb.bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                TRY_CUDA(cudaStreamSynchronize(s));
+                reuse = bad == 0;
+                if (reuse) ++reuses;
+            }
             if (k > 0) {
                 const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
-                prof_begin(lane, TSNNLS_PHASE_GATHER);
-                TRY_CUDA(launch_gather<T>(s, G, ldg, F, nullptr, k, S, lds));
-                prof_end(lane, 2.0 * tri + 4.0 * k, 0.0);
-                if (lane.prof && lane.prof_kernels) {
-                    LaneTimer lt{lane};
-                    TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, &lt));
-                } else {
-                    prof_begin(lane, TSNNLS_PHASE_FACTOR);
-                    const FactorStreams fs{lane.side, lane.fork, lane.head, lane.join};
-                    TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, nullptr, &fs));
-                    prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
+                if (!reuse) {
+                    prof_begin(lane, TSNNLS_PHASE_GATHER);
+                    TRY_CUDA(launch_gather<T>(s, G, ldg, F, nullptr, k, S, lds));
+                    prof_end(lane, 2.0 * tri + 4.0 * k, 0.0);
+                    if (lane.prof && lane.prof_kernels) {
+                        LaneTimer lt{lane};
+                        TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, &lt));
+                    } else {
+                        prof_begin(lane, TSNNLS_PHASE_FACTOR);
+                        const FactorStreams fs{lane.side, lane.fork, lane.head, lane.join};
+                        TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, nullptr, &fs));
+                        prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
+                    }
+                    if (mixed) {  // this factor becomes the base for later pivots
+                        TRY_CUDA(cudaMemcpyAsync(bb.Bl, F, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, s));
+                        TRY_CUDA(cudaMemcpyAsync(bb.inB, inF, (size_t)n, cudaMemcpyDeviceToDevice, s));
+                        base_valid = true;
+                        kb = k;
+                        ldsb = lds;
+                    }
                 }
                 // first solve: x_F = (L L^T)^{-1} c_F  (x restarts from 0)
+                const int64_t kl = reuse ? kb : k;
+                const double tril = 0.5 * (double)kl * (double)(kl + 1) * sizeof(T);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                TRY_CUDA(launch_gather_rhs<T>(s, c, F, k, rhs));
-                prof_end(lane, (12.0 + sizeof(T)) * k, 0.0);
+                TRY_CUDA(launch_gather_rhs<T>(s, c, sol_list(), sol_len(), rhs));
+                prof_end(lane, (12.0 + sizeof(T)) * sol_len(), 0.0);
                 prof_begin(lane, TSNNLS_PHASE_TRSV);
-                TRY_CUDA(launch_chol_solve<T>(s, S, k, lds, rhs, trsv_scratch, lane.st_dev));
-                prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * k, 2.0 * (double)k * (double)k);
+                TRY_CUDA(pivot_solve(rhs));
+                prof_end(lane, 2.0 * tril + 4.0 * sizeof(T) * kl, 2.0 * (double)kl * (double)kl);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                TRY_CUDA(launch_update_x<T>(s, rhs, F, k, x, lane.st_dev));
-                prof_end(lane, (20.0 + sizeof(T)) * k, 0.0);
+                TRY_CUDA(launch_update_x<T>(s, rhs, sol_list(), sol_len(), x, lane.st_dev));
+                prof_end(lane, (20.0 + sizeof(T)) * sol_len(), 0.0);
                 TRY_CUDA(sync.post());
             }
             // the residual of the new x is needed whether the refinement goes
@@ -525,6 +578,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             info->iters = lane.st_host->iters;
             info->nF = lane.st_host->k;
             info->cond_est = cond;
+            info->factor_reuses = reuses;
         }
     }
 cleanup:

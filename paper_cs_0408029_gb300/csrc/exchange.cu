@@ -202,7 +202,7 @@ __global__ void gather_rhs_kernel(const double *__restrict__ v, const int32_t *_
                                   int64_t k, T *__restrict__ out) {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < k;
          a += (int64_t)gridDim.x * blockDim.x)
-        out[a] = (T)v[F[a]];
+        out[a] = F[a] >= 0 ? (T)v[F[a]] : T(0);  // -1: a variable held at zero
 }
 
 template <typename T>
@@ -228,8 +228,9 @@ __global__ void __launch_bounds__(kExThreads)
     __shared__ double shd[32], shx[32];
     double dm = 0.0, xm = 0.0;
     for (int64_t a = threadIdx.x; a < k; a += kExThreads) {
-        const double d = (double)delta[a];
         const int32_t j = F[a];
+        if (j < 0) continue;  // a variable held at zero
+        const double d = (double)delta[a];
         const double xn = x[j] + d;
         x[j] = xn;
         dm = fmax(dm, fabs(d));

@@ -1220,9 +1220,10 @@ __global__ void __launch_bounds__(256)
     trsv_put<T, NB>(sc, rhs, i, nr, wi);
 }
 
+// dir: bit 0 = forward (L z = rhs), bit 1 = backward (L^T w = rhs), in that order
 template <typename T>
-cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
-                              DevStatus *st) {
+static cudaError_t launch_trsv_dirs(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
+                                    DevStatus *st, int dirs) {
     constexpr int NB = FactorCfg<T>::NB;
     if (k <= 0) return cudaSuccess;
     const TrsvScratch<T, NB> sc = trsv_scratch<T, NB>(scratch, k);
@@ -1235,16 +1236,45 @@ cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(trsv_bwd_kernel<T, NB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sc.done, 0, bytes, s);
     if (e != cudaSuccess) return e;
-    trsv_fwd_kernel<T, NB><<<(unsigned)ctas, 256, smem, s>>>(L, k, lds, rhs, sc, st);
-    note_launches(1);
-    e = cudaMemsetAsync(sc.done, 0, bytes, s);
-    if (e != cudaSuccess) return e;
-    trsv_bwd_kernel<T, NB><<<(unsigned)ctas, 256, smem, s>>>(L, k, lds, rhs, sc, st);
-    note_launches(1);
+    if (dirs & 1) {
+        e = cudaMemsetAsync(sc.done, 0, bytes, s);
+        if (e != cudaSuccess) return e;
+        trsv_fwd_kernel<T, NB><<<(unsigned)ctas, 256, smem, s>>>(L, k, lds, rhs, sc, st);
+        note_launches(1);
+    }
+    if (dirs & 2) {
+        e = cudaMemsetAsync(sc.done, 0, bytes, s);
+        if (e != cudaSuccess) return e;
+        trsv_bwd_kernel<T, NB><<<(unsigned)ctas, 256, smem, s>>>(L, k, lds, rhs, sc, st);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_chol_solve(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
+                              DevStatus *st) {
+    return launch_trsv_dirs<T>(s, L, k, lds, rhs, scratch, st, 3);
+}
+template <typename T>
+cudaError_t launch_trsv_fwd(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
+                            DevStatus *st) {
+    return launch_trsv_dirs<T>(s, L, k, lds, rhs, scratch, st, 1);
+}
+template <typename T>
+cudaError_t launch_trsv_bwd(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
+                            DevStatus *st) {
+    return launch_trsv_dirs<T>(s, L, k, lds, rhs, scratch, st, 2);
+}
+template cudaError_t launch_trsv_fwd<float>(cudaStream_t, const float *, int64_t, int64_t, float *, void *,
+                                            DevStatus *);
+template cudaError_t launch_trsv_fwd<double>(cudaStream_t, const double *, int64_t, int64_t, double *, void *,
+                                             DevStatus *);
+template cudaError_t launch_trsv_bwd<float>(cudaStream_t, const float *, int64_t, int64_t, float *, void *,
+                                            DevStatus *);
+template cudaError_t launch_trsv_bwd<double>(cudaStream_t, const double *, int64_t, int64_t, double *, void *,
+                                             DevStatus *);
 
 template cudaError_t launch_chol_solve<float>(cudaStream_t, const float *, int64_t, int64_t,
                                               float *, void *, DevStatus *);

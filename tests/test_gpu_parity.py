@@ -227,6 +227,25 @@ def test_settle_stop_matches_full_refinement(ts, ctx, oracle_mod):
     assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x1)
 
 
+def test_factor_reuse_matches_refactoring(ts, ctx, oracle_mod):
+    """A pivot that moves only a few variables since the last factorisation is
+    solved on that factor, bordered by the added columns and with the removed
+    ones held at zero by a capacitance correction: the pivots, the split and x
+    must equal those of refactoring every pivot (as the paper does), and the
+    oracle's."""
+    p = workloads.random_sparse(5000, 2500, 0.004, seed=7, zero_frac=0.4, noise=0.05)
+    ref = oracle_mod.bpp_solve(p)
+    A = ts.HostCSR.from_problem(p)
+    x1, _, inF1, tr1, i1 = ctx.solve_ex(A, p.b)
+    x2, _, inF2, tr2, i2 = ctx.solve_ex(A, p.b, no_reuse=1)
+    assert i1.factor_reuses >= 1 and i2.factor_reuses == 0
+    for x, inF in ((x1, inF1), (x2, inF2)):
+        _check_solution(p, ref, x, inF)
+    assert np.array_equal(tr1, tr2) and np.array_equal(tr1, ref.trace)
+    assert np.array_equal(inF1, inF2)
+    assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x2)
+
+
 def test_fallback_to_fp64_when_the_fp32_factor_fails(ts, ctx):
     """kappa(A) = 1e5 puts kappa(A^T A) = 1e10 beyond an FP32 factor: the
     mixed solve either loses positive definiteness or its refinement
