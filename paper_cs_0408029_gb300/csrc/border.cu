@@ -186,7 +186,8 @@ constexpr int kMidThreads = 512;
 template <typename T>
 __global__ void __launch_bounds__(kMidThreads)
     border_mid_kernel(T *__restrict__ z, int64_t kb, int a, const T *__restrict__ Pt, int64_t ldp,
-                      const double *__restrict__ Lq) {
+                      const double *__restrict__ Lq, int64_t zld) {
+    z += (int64_t)blockIdx.y * zld;  // one vector per grid row
     __shared__ T red[kMidThreads / 32];
     __shared__ double tv[kBorderMax];
     __shared__ T za[kBorderMax];
@@ -285,7 +286,8 @@ size_t border_bytes(int64_t n, size_t elem) {
            + (size_t)round_up((int64_t)elem * n * kBorderMax, 256)   // P^T
            + (size_t)round_up((int64_t)elem * u * kBorderMax, 256)   // Z
            + 4 * (size_t)round_up(8 * kBorderMax * kBorderMax, 256)  // G_AA, Q, C, spare
-           + 256 + 256;                                              // mu, flag
+           + 256 + 256                                               // mu, flag
+           + trsv_multi_scratch_bytes(n, elem, kBorderMax);          // simultaneous solves
 }
 
 BorderBuffers border_carve(void *base, int64_t n, size_t elem) {
@@ -310,6 +312,7 @@ BorderBuffers border_carve(void *base, int64_t n, size_t elem) {
     take(8 * kBorderMax * kBorderMax);
     b.mu = reinterpret_cast<double *>(take(8 * kBorderMax));
     b.bad = reinterpret_cast<int32_t *>(take(4));
+    b.multi = take(trsv_multi_scratch_bytes(n, elem, kBorderMax));
     b.ldp = n;
     b.ldz = u;
     return b;
@@ -325,6 +328,7 @@ cudaError_t launch_border_diff(cudaStream_t s, int64_t n, const uint8_t *inF, co
 template <typename T>
 cudaError_t launch_border_setup(cudaStream_t s, const T *G, int64_t ldg, const T *L, int64_t kb, int64_t lds,
                                 int a, int r, const BorderBuffers &b, void *trsv_scratch, DevStatus *st) {
+    (void)trsv_scratch;  // the setup's solves run side by side in b.multi
     T *Pt = static_cast<T *>(b.Pt);
     T *Z = static_cast<T *>(b.Z);
     const int64_t u = kb + a;
@@ -335,8 +339,7 @@ cudaError_t launch_border_setup(cudaStream_t s, const T *G, int64_t ldg, const T
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(work, 256), 152 * 8));
         border_gather_kernel<T><<<g, 256, 0, s>>>(G, ldg, b.Bl, kb, b.Al, a, Pt, b.ldp, b.GAA);
         note_launches(1);
-        for (int al = 0; al < a && e == cudaSuccess; ++al)
-            e = launch_trsv_fwd<T>(s, L, kb, lds, Pt + (int64_t)al * b.ldp, trsv_scratch, st);
+        e = launch_trsv_multi<T>(s, L, kb, lds, Pt, b.ldp, a, b.multi, st, 1);
         if (e != cudaSuccess) return e;
         border_schur_kernel<T><<<a * a, 256, 0, s>>>(Pt, b.ldp, kb, a, b.GAA, b.Lq);
         border_chol_kernel<<<1, 32, 0, s>>>(b.Lq, a, b.bad);
@@ -346,15 +349,13 @@ cudaError_t launch_border_setup(cudaStream_t s, const T *G, int64_t ldg, const T
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(u * r, 256), 152 * 8));
         border_unit_kernel<T><<<g, 256, 0, s>>>(Z, u, b.ldz, r, b.Rpos);
         note_launches(1);
-        for (int q = 0; q < r && e == cudaSuccess; ++q) {
-            T *zc = Z + (int64_t)q * b.ldz;
-            e = launch_trsv_fwd<T>(s, L, kb, lds, zc, trsv_scratch, st);
-            if (e == cudaSuccess && a > 0) {
-                border_mid_kernel<T><<<1, kMidThreads, 0, s>>>(zc, kb, a, Pt, b.ldp, b.Lq);
-                note_launches(1);
-            }
-            if (e == cudaSuccess) e = launch_trsv_bwd<T>(s, L, kb, lds, zc, trsv_scratch, st);
+        // the r columns of Z side by side: forward, border step, backward
+        e = launch_trsv_multi<T>(s, L, kb, lds, Z, b.ldz, r, b.multi, st, 1);
+        if (e == cudaSuccess && a > 0) {
+            border_mid_kernel<T><<<dim3(1, (unsigned)r), kMidThreads, 0, s>>>(Z, kb, a, Pt, b.ldp, b.Lq, b.ldz);
+            note_launches(1);
         }
+        if (e == cudaSuccess) e = launch_trsv_multi<T>(s, L, kb, lds, Z, b.ldz, r, b.multi, st, 2);
         if (e != cudaSuccess) return e;
         border_cap_factor_kernel<T><<<1, 256, 0, s>>>(Z, b.ldz, r, b.Rpos, b.Lc, b.bad);
         note_launches(1);
@@ -368,7 +369,7 @@ cudaError_t launch_border_solve(cudaStream_t s, const T *L, int64_t kb, int64_t 
     const int64_t u = kb + a;
     cudaError_t e = launch_trsv_fwd<T>(s, L, kb, lds, z, trsv_scratch, st);
     if (e == cudaSuccess && a > 0) {
-        border_mid_kernel<T><<<1, kMidThreads, 0, s>>>(z, kb, a, static_cast<const T *>(b.Pt), b.ldp, b.Lq);
+        border_mid_kernel<T><<<1, kMidThreads, 0, s>>>(z, kb, a, static_cast<const T *>(b.Pt), b.ldp, b.Lq, 0);
         note_launches(1);
     }
     if (e == cudaSuccess) e = launch_trsv_bwd<T>(s, L, kb, lds, z, trsv_scratch, st);

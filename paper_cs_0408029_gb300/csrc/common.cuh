@@ -118,6 +118,13 @@ cudaError_t launch_trsv_fwd(cudaStream_t s, const T *L, int64_t k, int64_t lds, 
 template <typename T>
 cudaError_t launch_trsv_bwd(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
                             DevStatus *st);
+// q right-hand sides rhs + j rhs_ld at once (dirs: 1 forward, 2 backward, 3
+// both), each solved by its own chain of CTAs in one launch; scratch of
+// trsv_multi_scratch_bytes(k, sizeof(T), q) bytes, 256-byte aligned.
+size_t trsv_multi_scratch_bytes(int64_t k, size_t elem, int q);
+template <typename T>
+cudaError_t launch_trsv_multi(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, int64_t rhs_ld, int q,
+                              void *scratch, DevStatus *st, int dirs);
 
 // out = alpha * M x + beta * z over a CSR (or CSC viewed as CSR of M^T).
 cudaError_t launch_spmv(cudaStream_t s, int64_t rows, const int64_t *ptr, const int32_t *idx,
@@ -149,6 +156,7 @@ struct BorderBuffers {
     double *GAA, *Lq, *Lc;  // kBorderMax^2 each: G_AA, factor of G_AA - P P^T, factor of Z_R
     double *mu;
     int32_t *bad;     // set by the setup when a small factor is not positive definite
+    void *multi;      // scratch of kBorderMax simultaneous triangular solves
     int64_t ldp, ldz;
 };
 size_t border_bytes(int64_t n, size_t elem);

@@ -197,11 +197,12 @@ struct Sync {
         }                                       \
     } while (0)
 
-// a + 2 r triangular-solve passes of setup at most for reusing a factor: a
-// gather and refactorisation cost about 30 passes at any k >= 1024 (both
-// scale with the number of 128-wide block steps), and the bordered solves
-// add a little to every refinement step
-constexpr int kReuseBudget = 20;
+// Reusing a factor costs three triangular-solve passes of setup (the a
+// columns of P^T side by side, then the r columns of Z forward and back)
+// against about 30 passes' worth for a gather and refactorisation at any
+// k >= 1024 (both scale with the number of 128-wide block steps); the bordered
+// solves add a few small kernels to every refinement step.
+constexpr int64_t kReuseMinK = 1024;
 
 template <typename T>
 int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,
@@ -427,14 +428,13 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             }
             k = st.k;
             lds = round_up(std::max<int64_t>(k, 1), 32);
-            // Reuse the base factor when few variables moved since it was
-            // taken: a + 2 r triangular solves of setup against a factorisation
-            // (refinement path only; the plain FP64 path refactors every
-            // pivot as the paper does, and the condition estimate wants the
-            // factor of the last F itself).
+            // Reuse the base factor when at most kBorderMax variables were
+            // added and removed since it was taken (refinement path only; the
+            // plain FP64 path refactors every pivot as the paper does, and the
+            // condition estimate wants the factor of the last F itself).
             reuse = false;
             if (mixed && base_valid && k > 0 && o.cond_est == 0 && o.no_reuse == 0 && st.border_a <= kBorderMax &&
-                st.border_r <= kBorderMax && st.border_a + 2 * st.border_r <= kReuseBudget && kb >= 1024) {
+                st.border_r <= kBorderMax && kb >= kReuseMinK) {
                 ba = st.border_a;
                 br = st.border_r;
                 prof_begin(lane, TSNNLS_PHASE_REUSE);

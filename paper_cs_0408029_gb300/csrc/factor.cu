@@ -899,6 +899,20 @@ __host__ TrsvScratch<T, NB> trsv_scratch(void *base, int64_t k) {
     return s;
 }
 
+// The same scratch layout `bytes` further on (one region per right-hand side
+// of a multi-vector launch).
+template <typename T, int NB>
+__device__ __forceinline__ TrsvScratch<T, NB> trsv_shift(TrsvScratch<T, NB> s, int64_t bytes) {
+    auto mv = [&](auto *p) { return reinterpret_cast<decltype(p)>(reinterpret_cast<char *>(p) + bytes); };
+    s.done = mv(s.done);
+    s.hcnt = mv(s.hcnt);
+    s.ticket = mv(s.ticket);
+    s.abort_flag = mv(s.abort_flag);
+    if (s.words) s.words = mv(s.words);
+    s.part = mv(s.part);
+    return s;
+}
+
 // zs[0..NB) <- solved block j (nvalid entries, zeros beyond), once available.
 // Uniform across the CTA; false when the launch was aborted or a wait timed out.
 // tight: every thread polls its own word from the start (one round trip; used
@@ -983,7 +997,7 @@ __device__ __forceinline__ void trsv_put(const TrsvScratch<T, NB> &sc, T *rhs, i
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
     trsv_fwd_kernel(const T *__restrict__ L, int64_t k, int64_t lds, T *rhs, TrsvScratch<T, NB> sc,
-                    DevStatus *st) {
+                    DevStatus *st, int64_t rhs_ld, int64_t sc_stride) {
     constexpr int P = 256 / NB, CW = NB / P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T(*Wr)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);  // Wr[r][l] = W(r, l)
@@ -992,6 +1006,10 @@ __global__ void __launch_bounds__(256)
     __shared__ int64_t tk_sh;
     __shared__ int ok_sh;
     const int tid = threadIdx.x;
+    if (blockIdx.y > 0) {  // right-hand side blockIdx.y of a multi-vector launch: its own chain
+        rhs += (int64_t)blockIdx.y * rhs_ld;
+        sc = trsv_shift(sc, (int64_t)blockIdx.y * sc_stride);
+    }
     if (tid == 0) tk_sh = atomicAdd(sc.ticket, 1);
     __syncthreads();
     const int64_t tk = tk_sh;
@@ -1101,7 +1119,7 @@ __global__ void __launch_bounds__(256)
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
     trsv_bwd_kernel(const T *__restrict__ L, int64_t k, int64_t lds, T *rhs, TrsvScratch<T, NB> sc,
-                    DevStatus *st) {
+                    DevStatus *st, int64_t rhs_ld, int64_t sc_stride) {
     constexpr int CPW = NB / 8;   // columns per warp
     constexpr int RPL = NB / 32;  // rows per lane per column
     constexpr int P = 256 / NB, CW = NB / P;
@@ -1113,6 +1131,10 @@ __global__ void __launch_bounds__(256)
     __shared__ int64_t tk_sh;
     __shared__ int ok_sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (blockIdx.y > 0) {  // right-hand side blockIdx.y of a multi-vector launch: its own chain
+        rhs += (int64_t)blockIdx.y * rhs_ld;
+        sc = trsv_shift(sc, (int64_t)blockIdx.y * sc_stride);
+    }
     if (tid == 0) tk_sh = atomicAdd(sc.ticket, 1);
     __syncthreads();
     const int64_t tk = tk_sh;
@@ -1221,15 +1243,24 @@ __global__ void __launch_bounds__(256)
 }
 
 // dir: bit 0 = forward (L z = rhs), bit 1 = backward (L^T w = rhs), in that order
+size_t trsv_multi_scratch_bytes(int64_t k, size_t elem, int q) {
+    return (size_t)std::max(q, 1) * (size_t)round_up((int64_t)chol_solve_scratch_bytes(k, elem), 256);
+}
+
+// dir: bit 0 = forward (L z = rhs), bit 1 = backward (L^T w = rhs), in that
+// order; q right-hand sides rhs + j rhs_ld, each with its own chain of CTAs
+// (grid y) and scratch region.
 template <typename T>
 static cudaError_t launch_trsv_dirs(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, void *scratch,
-                                    DevStatus *st, int dirs) {
+                                    DevStatus *st, int dirs, int q = 1, int64_t rhs_ld = 0) {
     constexpr int NB = FactorCfg<T>::NB;
-    if (k <= 0) return cudaSuccess;
+    if (k <= 0 || q <= 0) return cudaSuccess;
     const TrsvScratch<T, NB> sc = trsv_scratch<T, NB>(scratch, k);
     const int64_t ctas = trsv_ctas(sc.nblk);
+    const int64_t stride = q > 1 ? round_up((int64_t)chol_solve_scratch_bytes(k, sizeof(T)), 256) : 0;
     // flags, ticket, abort and the published words start at zero for each pass
-    const size_t bytes = (size_t)trsv_zeroed_bytes(sc.nblk, NB, sizeof(T));
+    const size_t bytes = q > 1 ? (size_t)(stride * q) : (size_t)trsv_zeroed_bytes(sc.nblk, NB, sizeof(T));
+    const dim3 grid((unsigned)ctas, (unsigned)q);
     const size_t smem = sizeof(T) * NB * (NB + 4);
     cudaError_t e = cudaFuncSetAttribute(trsv_fwd_kernel<T, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1240,13 +1271,13 @@ static cudaError_t launch_trsv_dirs(cudaStream_t s, const T *L, int64_t k, int64
     if (dirs & 1) {
         e = cudaMemsetAsync(sc.done, 0, bytes, s);
         if (e != cudaSuccess) return e;
-        trsv_fwd_kernel<T, NB><<<(unsigned)ctas, 256, smem, s>>>(L, k, lds, rhs, sc, st);
+        trsv_fwd_kernel<T, NB><<<grid, 256, smem, s>>>(L, k, lds, rhs, sc, st, rhs_ld, stride);
         note_launches(1);
     }
     if (dirs & 2) {
         e = cudaMemsetAsync(sc.done, 0, bytes, s);
         if (e != cudaSuccess) return e;
-        trsv_bwd_kernel<T, NB><<<(unsigned)ctas, 256, smem, s>>>(L, k, lds, rhs, sc, st);
+        trsv_bwd_kernel<T, NB><<<grid, 256, smem, s>>>(L, k, lds, rhs, sc, st, rhs_ld, stride);
         note_launches(1);
     }
     return cudaGetLastError();
@@ -1267,6 +1298,15 @@ cudaError_t launch_trsv_bwd(cudaStream_t s, const T *L, int64_t k, int64_t lds, 
                             DevStatus *st) {
     return launch_trsv_dirs<T>(s, L, k, lds, rhs, scratch, st, 2);
 }
+template <typename T>
+cudaError_t launch_trsv_multi(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, int64_t rhs_ld, int q,
+                              void *scratch, DevStatus *st, int dirs) {
+    return launch_trsv_dirs<T>(s, L, k, lds, rhs, scratch, st, dirs, q, rhs_ld);
+}
+template cudaError_t launch_trsv_multi<float>(cudaStream_t, const float *, int64_t, int64_t, float *, int64_t, int,
+                                              void *, DevStatus *, int);
+template cudaError_t launch_trsv_multi<double>(cudaStream_t, const double *, int64_t, int64_t, double *, int64_t,
+                                               int, void *, DevStatus *, int);
 template cudaError_t launch_trsv_fwd<float>(cudaStream_t, const float *, int64_t, int64_t, float *, void *,
                                             DevStatus *);
 template cudaError_t launch_trsv_fwd<double>(cudaStream_t, const double *, int64_t, int64_t, double *, void *,
