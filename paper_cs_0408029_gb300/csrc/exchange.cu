@@ -221,13 +221,17 @@ template cudaError_t launch_gather_rhs<double>(cudaStream_t, const double *, con
                                                int64_t, double *);
 
 // x_F += delta (FP64), and ||delta||_inf, ||x_F||_inf into the status.
+// x_F += delta (list order), with max |delta| and max |x_F| into st->dnorm /
+// st->xnorm.  Several CTAs; the maxima of non-negative doubles combine through
+// integer atomicMax on their bit patterns (same order as the values, so the
+// result does not depend on the order of the CTAs).
 template <typename T>
-__global__ void __launch_bounds__(kExThreads)
+__global__ void __launch_bounds__(256)
     update_x_kernel(const T *__restrict__ delta, const int32_t *__restrict__ F, int64_t k,
                     double *__restrict__ x, DevStatus *st) {
-    __shared__ double shd[32], shx[32];
+    __shared__ double shd[8], shx[8];
     double dm = 0.0, xm = 0.0;
-    for (int64_t a = threadIdx.x; a < k; a += kExThreads) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < k; a += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = F[a];
         if (j < 0) continue;  // a variable held at zero
         const double d = (double)delta[a];
@@ -246,24 +250,24 @@ __global__ void __launch_bounds__(kExThreads)
         shx[warp] = xm;
     }
     __syncthreads();
-    if (warp == 0) {
-        dm = shd[lane];
-        xm = shx[lane];
-        for (int o = 16; o > 0; o >>= 1) {
-            dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-            xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) {
+            dm = fmax(dm, shd[w]);
+            xm = fmax(xm, shx[w]);
         }
-        if (lane == 0) {
-            st->dnorm = dm;
-            st->xnorm = xm;
-        }
+        atomicMax(reinterpret_cast<unsigned long long *>(&st->dnorm), (unsigned long long)__double_as_longlong(dm));
+        atomicMax(reinterpret_cast<unsigned long long *>(&st->xnorm), (unsigned long long)__double_as_longlong(xm));
     }
 }
 
 template <typename T>
 cudaError_t launch_update_x(cudaStream_t s, const T *delta, const int32_t *F, int64_t k,
                             double *x, DevStatus *st) {
-    update_x_kernel<T><<<1, kExThreads, 0, s>>>(delta, F, k, x, st);
+    static_assert(offsetof(DevStatus, xnorm) == offsetof(DevStatus, dnorm) + sizeof(double), "adjacent norms");
+    cudaError_t e = cudaMemsetAsync(&st->dnorm, 0, 2 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(k, 256), 152));
+    update_x_kernel<T><<<g, 256, 0, s>>>(delta, F, k, x, st);
     note_launches(1);
     return cudaGetLastError();
 }
