@@ -56,6 +56,16 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
     const double2 g = *reinterpret_cast<const double2 *>(p + 2);
     v[0] = f.x; v[1] = f.y; v[2] = g.x; v[3] = g.y;
 }
+__device__ __forceinline__ void ld2(const float *p, float (&v)[2]) {
+    const float2 a = *reinterpret_cast<const float2 *>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+}
+__device__ __forceinline__ void ld2(const double *p, double (&v)[2]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+}
 __device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -371,12 +381,13 @@ __global__ void __launch_bounds__(256)
 // (NB/16) register tile of X
 
 constexpr int kPanelRows = 32;
+constexpr int kHeadPanelRows = 16;  // the look-ahead's head rows, on the critical chain
 
-template <typename T, int NB>
+template <typename T, int NB, int PR = kPanelRows>
 __global__ void __launch_bounds__(256)
     chol_panel_kernel(T *__restrict__ S, int64_t k, int64_t lds, int64_t K, int64_t r_begin, int64_t r_end,
                       float *__restrict__ xhi, float *__restrict__ xlo) {
-    constexpr int PR = kPanelRows, RT = PR / 16, BP = PR + 4;  // rows, rows per thread, B pitch
+    constexpr int RT = PR / 16, BP = PR + 4;  // rows per thread, B pitch
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T(*Wl)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);  // Wl[l][c] = W(c, l)
     T(*B)[BP] = reinterpret_cast<T(*)[BP]>(smem_raw + sizeof(T) * NB * (NB + 4));  // B[l][row]
@@ -614,16 +625,27 @@ __global__ void __launch_bounds__(256)
         Xr[e / 32][e % 32] = vr[u];
         Xc[e / 32][e % 32] = vc[u];
     }
-    __syncthreads();
     const int rr = (tid % 16) * 2, cc = (tid / 16) * 2;
+    // this thread's entries of C, loaded before the products need the barrier
+    T cv[2][2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int gr = rb + rr + p, gc = cb + cc + q;
+            cv[p][q] = (gr < kb && gc < kb && gr >= gc) ? S[(Kn + gr) + (Kn + gc) * lds] : T(0);
+        }
+    __syncthreads();
     T a00 = T(0), a01 = T(0), a10 = T(0), a11 = T(0);
 #pragma unroll 8
     for (int t = 0; t < NB; ++t) {
-        const T x0 = Xr[t][rr], x1 = Xr[t][rr + 1], y0 = Xc[t][cc], y1 = Xc[t][cc + 1];
-        a00 += x0 * y0;
-        a01 += x0 * y1;
-        a10 += x1 * y0;
-        a11 += x1 * y1;
+        T x[2], y[2];
+        ld2(&Xr[t][rr], x);  // 2-vector shared loads (even offsets, 8-byte aligned rows)
+        ld2(&Xc[t][cc], y);
+        a00 += x[0] * y[0];
+        a01 += x[0] * y[1];
+        a10 += x[1] * y[0];
+        a11 += x[1] * y[1];
     }
     const T acc[2][2] = {{a00, a01}, {a10, a11}};
 #pragma unroll
@@ -631,7 +653,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int gr = rb + rr + p, gc = cb + cc + q;
-            if (gr < kb && gc < kb && gr >= gc) S[(Kn + gr) + (Kn + gc) * lds] -= acc[p][q];
+            if (gr < kb && gc < kb && gr >= gc) S[(Kn + gr) + (Kn + gc) * lds] = cv[p][q] - acc[p][q];
         }
 }
 
@@ -648,6 +670,9 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(chol_panel_kernel<T, NB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(chol_panel_kernel<T, NB, kHeadPanelRows>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel);
     if (e != cudaSuccess) return e;
     const bool ahead = fs != nullptr && kt == nullptr;
@@ -713,7 +738,11 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
         e = cudaEventRecord(fs->fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(fs->side, fs->fork, 0);
         if (e != cudaSuccess) return e;
-        panel(fs->side, K, Kn, head_end);
+        // the head rows in 16-row CTAs: twice the CTAs, half the work on the chain each
+        chol_panel_kernel<T, NB, kHeadPanelRows>
+            <<<(unsigned)cdiv(head_end - Kn, kHeadPanelRows), 256, smem_panel, fs->side>>>(
+                S, k, lds, K, Kn, head_end, use_tc ? tc->xhi : nullptr, use_tc ? tc->xlo : nullptr);
+        note_launches(1);
         e = cudaEventRecord(fs->head, fs->side);
         if (e != cudaSuccess) return e;
         chol_tile_update_kernel<T, NB><<<10, 256, 0, fs->side>>>(S, k, lds, K, Kn);
