@@ -119,7 +119,9 @@ __device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, T (*col)[32], int
             for (int u = 0; u < 4; ++u) {
                 const int l = 4 * g + u;
                 if (l > J) {
-                    if (lane >= l) s.a[l] -= lij * v[u];
+                    // rows above l (lane < l) update entries above the
+                    // diagonal, which are never read as L: no predicate
+                    s.a[l] -= lij * v[u];
                     s.w[l] += v[u] * wj;
                 }
             }
