@@ -82,6 +82,26 @@ __global__ void __launch_bounds__(kBThreads)
     }
 }
 
+// Counts only: st->border_a = |F' \ B|, st->border_r = |B \ F'| (integer
+// sums, so the order of the CTAs does not matter).
+__global__ void border_count_kernel(int64_t n, const uint8_t *__restrict__ inF, const uint8_t *__restrict__ inB,
+                                    DevStatus *st) {
+    int a = 0, r = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const bool f = inF[j] != 0, b = inB[j] != 0;
+        a += f && !b;
+        r += b && !f;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (a | r)) {
+        atomicAdd(&st->border_a, a);
+        atomicAdd(&st->border_r, r);
+    }
+}
+
 // Pt(p, al) = G(B[p], A[al]) for p < kb; GAA(al, be) = G(A[al], A[be]).
 // G holds the lower triangle of the cached A^T A (leading dimension ldg).
 template <typename T>
@@ -226,17 +246,16 @@ __global__ void __launch_bounds__(kMidThreads)
 }
 
 // mu = C^-1 z_R (one warp), then z <- z - Z mu over all u rows.
-__global__ void border_cap_mu_kernel(const float *__restrict__ zf, const double *__restrict__ zd, int64_t u,
-                                     int r, const int32_t *__restrict__ Rpos, const double *__restrict__ Lc,
-                                     double *__restrict__ mu) {
-    (void)u;
+template <typename T>
+__global__ void border_cap_mu_kernel(const T *__restrict__ z, int r, const int32_t *__restrict__ Rpos,
+                                     const double *__restrict__ Lc, double *__restrict__ mu) {
     __shared__ double Ls[kBorderMax * kBorderMax];
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int e = lane; e < kBorderMax * kBorderMax; e += 32) Ls[e] = Lc[e];
     __syncwarp();
     double g = 0.0;
-    if (lane < r) g = zf ? (double)zf[Rpos[lane]] : zd[Rpos[lane]];
+    if (lane < r) g = (double)z[Rpos[lane]];
     g = warp_small_solve(Ls, r, g);
     if (lane < r) mu[lane] = g;
 }
@@ -318,6 +337,17 @@ BorderBuffers border_carve(void *base, int64_t n, size_t elem) {
     return b;
 }
 
+cudaError_t launch_border_count(cudaStream_t s, int64_t n, const uint8_t *inF, const BorderBuffers &b,
+                                DevStatus *st) {
+    static_assert(offsetof(DevStatus, border_r) == offsetof(DevStatus, border_a) + sizeof(int32_t), "adjacent");
+    cudaError_t e = cudaMemsetAsync(&st->border_a, 0, 2 * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152));
+    border_count_kernel<<<g, 256, 0, s>>>(n, inF, b.inB, st);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_border_diff(cudaStream_t s, int64_t n, const uint8_t *inF, const BorderBuffers &b, int64_t kb,
                                DevStatus *st) {
     border_diff_kernel<<<1, kBThreads, 0, s>>>(n, inF, b.inB, b.Bl, kb, b.Ul, b.Al, b.Rpos, st);
@@ -327,8 +357,7 @@ cudaError_t launch_border_diff(cudaStream_t s, int64_t n, const uint8_t *inF, co
 
 template <typename T>
 cudaError_t launch_border_setup(cudaStream_t s, const T *G, int64_t ldg, const T *L, int64_t kb, int64_t lds,
-                                int a, int r, const BorderBuffers &b, void *trsv_scratch, DevStatus *st) {
-    (void)trsv_scratch;  // the setup's solves run side by side in b.multi
+                                int a, int r, const BorderBuffers &b, DevStatus *st) {
     T *Pt = static_cast<T *>(b.Pt);
     T *Z = static_cast<T *>(b.Z);
     const int64_t u = kb + a;
@@ -374,9 +403,7 @@ cudaError_t launch_border_solve(cudaStream_t s, const T *L, int64_t kb, int64_t 
     }
     if (e == cudaSuccess) e = launch_trsv_bwd<T>(s, L, kb, lds, z, trsv_scratch, st);
     if (e == cudaSuccess && r > 0) {
-        border_cap_mu_kernel<<<1, 32, 0, s>>>(sizeof(T) == 4 ? reinterpret_cast<const float *>(z) : nullptr,
-                                             sizeof(T) == 8 ? reinterpret_cast<const double *>(z) : nullptr, u, r,
-                                             b.Rpos, b.Lc, b.mu);
+        border_cap_mu_kernel<T><<<1, 32, 0, s>>>(z, r, b.Rpos, b.Lc, b.mu);
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(u, 256), 152 * 2));
         border_cap_apply_kernel<T><<<g, 256, 0, s>>>(z, u, r, static_cast<const T *>(b.Z), b.ldz, b.mu);
         note_launches(2);
@@ -385,9 +412,9 @@ cudaError_t launch_border_solve(cudaStream_t s, const T *L, int64_t kb, int64_t 
 }
 
 template cudaError_t launch_border_setup<float>(cudaStream_t, const float *, int64_t, const float *, int64_t,
-                                                int64_t, int, int, const BorderBuffers &, void *, DevStatus *);
+                                                int64_t, int, int, const BorderBuffers &, DevStatus *);
 template cudaError_t launch_border_setup<double>(cudaStream_t, const double *, int64_t, const double *, int64_t,
-                                                 int64_t, int, int, const BorderBuffers &, void *, DevStatus *);
+                                                 int64_t, int, int, const BorderBuffers &, DevStatus *);
 template cudaError_t launch_border_solve<float>(cudaStream_t, const float *, int64_t, int64_t, int, int,
                                                 const BorderBuffers &, float *, void *, DevStatus *);
 template cudaError_t launch_border_solve<double>(cudaStream_t, const double *, int64_t, int64_t, int, int,

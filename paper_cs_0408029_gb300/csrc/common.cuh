@@ -161,6 +161,9 @@ struct BorderBuffers {
 };
 size_t border_bytes(int64_t n, size_t elem);
 BorderBuffers border_carve(void *base, int64_t n, size_t elem);
+// st->border_a / border_r: how many variables F' adds to and removes from the base
+cudaError_t launch_border_count(cudaStream_t s, int64_t n, const uint8_t *inF, const BorderBuffers &b,
+                                DevStatus *st);
 // A, R and U for the new flags against the base (counts in st->border_a / border_r)
 cudaError_t launch_border_diff(cudaStream_t s, int64_t n, const uint8_t *inF, const BorderBuffers &b, int64_t kb,
                                DevStatus *st);
@@ -168,7 +171,7 @@ cudaError_t launch_border_diff(cudaStream_t s, int64_t n, const uint8_t *inF, co
 // added and r <= kBorderMax removed variables (L: the base factor, kb x kb)
 template <typename T>
 cudaError_t launch_border_setup(cudaStream_t s, const T *G, int64_t ldg, const T *L, int64_t kb, int64_t lds,
-                                int a, int r, const BorderBuffers &b, void *trsv_scratch, DevStatus *st);
+                                int a, int r, const BorderBuffers &b, DevStatus *st);
 // z (u = kb + a entries, U order) <- solution of G_F'F' z_F' = z_F' with z_R = 0
 template <typename T>
 cudaError_t launch_border_solve(cudaStream_t s, const T *L, int64_t kb, int64_t lds, int a, int r,

@@ -396,7 +396,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             prof_begin(lane, TSNNLS_PHASE_EXCHANGE);
             TRY_CUDA(launch_exchange(s, n, x, y, inF, F, o.zero_tol, o.p_max, max_iter,
                                      lane.st_host->iters > 0 ? 1 : 0, lane.st_dev));
-            if (base_valid) TRY_CUDA(launch_border_diff(s, n, inF, bb, kb, lane.st_dev));
+            if (base_valid) TRY_CUDA(launch_border_count(s, n, inF, bb, lane.st_dev));
             prof_end(lane, 17.0 * n + 17.0 * n + 4.0 * n, 0.0);
             TRY_CUDA(sync.read());
             const DevStatus st = *lane.st_host;
@@ -438,7 +438,8 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 ba = st.border_a;
                 br = st.border_r;
                 prof_begin(lane, TSNNLS_PHASE_REUSE);
-                TRY_CUDA(launch_border_setup<T>(s, G, ldg, S, kb, ldsb, ba, br, bb, trsv_scratch, lane.st_dev));
+                TRY_CUDA(launch_border_diff(s, n, inF, bb, kb, lane.st_dev));
+                TRY_CUDA(launch_border_setup<T>(s, G, ldg, S, kb, ldsb, ba, br, bb, lane.st_dev));
                 prof_end(lane, (double)(ba + 2 * br) * 0.5 * (double)kb * (double)kb * sizeof(T), 0.0);
                 int32_t bad = 0;
                 TRY_CUDA(cudaMemcpyAsync(&bad, bb.bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
