@@ -331,7 +331,7 @@ static int64_t lsqr_on_AF(int64_t m, const int64_t *row_ptr, const int32_t *col,
 }
 
 /* ------------------------------------------------------------------------ */
-/* The BPP driver (Section 2, algorithm box).                                */
+/* The BPP loop (Section 2, algorithm box).                                  */
 
 typedef struct {
     double zero_tol;   /* 1e-12 in the paper */

@@ -2,7 +2,7 @@
 
 Every .cu file under csrc/ is compiled for sm_103a in parallel with nvcc and
 linked into ``_build/libtsnnls.so``; the CUDA runtime is linked statically so
-the library has no dependency beyond the driver.
+the library has no dependency beyond the NVIDIA kernel-mode driver.
 """
 from __future__ import annotations
 
