@@ -429,12 +429,13 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             k = st.k;
             lds = round_up(std::max<int64_t>(k, 1), 32);
             // Reuse the base factor when at most kBorderMax variables were
-            // added and removed since it was taken (refinement path only; the
-            // plain FP64 path refactors every pivot as the paper does, and the
+            // added and removed since it was taken (the FP32 refinement path
+            // only; the plain FP64 path refactors every pivot as the paper
+            // does, so does the FP64 redo of a failed MIXED solve, and the
             // condition estimate wants the factor of the last F itself).
             reuse = false;
-            if (mixed && base_valid && k > 0 && o.cond_est == 0 && o.no_reuse == 0 && st.border_a <= kBorderMax &&
-                st.border_r <= kBorderMax && kb >= kReuseMinK) {
+            if (sizeof(T) == 4 && mixed && base_valid && k > 0 && o.cond_est == 0 && o.no_reuse == 0 &&
+                st.border_a <= kBorderMax && st.border_r <= kBorderMax && kb >= kReuseMinK) {
                 ba = st.border_a;
                 br = st.border_r;
                 prof_begin(lane, TSNNLS_PHASE_REUSE);
@@ -462,7 +463,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                         TRY_CUDA(launch_cholesky<T>(s, S, k, lds, lane.st_dev, &tc, nullptr, &fs));
                         prof_end(lane, 2.0 * tri, (double)k * (double)k * (double)k / 3.0);
                     }
-                    if (mixed) {  // this factor becomes the base for later pivots
+                    if (sizeof(T) == 4 && mixed) {  // this factor becomes the base for later pivots
                         TRY_CUDA(cudaMemcpyAsync(bb.Bl, F, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, s));
                         TRY_CUDA(cudaMemcpyAsync(bb.inB, inF, (size_t)n, cudaMemcpyDeviceToDevice, s));
                         base_valid = true;
