@@ -11,9 +11,11 @@
 //   z = H^-1 w - Z C^-1 (H^-1 w)_R
 // solves H z + E_R mu = w, z_R = 0: its F' = U \ R part solves
 // G_F'F' z_F' = w_F' (block elimination with a bordered factor, and the
-// capacitance form of deleting rows and columns).  All of it runs in the
-// factor's precision; the FP64 refinement of the solve takes the result to
-// full accuracy exactly as with a fresh factor.
+// capacitance form of deleting rows and columns).  The long vectors and
+// their triangular solves run in the factor's precision, the a x a and r x r
+// factors in FP64; the FP64 refinement of the solve takes the result to full
+// accuracy exactly as with a fresh factor.  The setup's triangular solves run
+// side by side (one launch for the a columns of P^T, two for the r of Z).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
