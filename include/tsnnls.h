@@ -317,6 +317,14 @@ int tsnnls_chol_solve(tsnnls_ctx *ctx, int32_t precision, const void *L, int64_t
 int tsnnls_chol_solve_noalloc(int32_t precision, const void *L, int64_t k, int64_t lds,
                               void *rhs, void *stream);
 
+/* Self-test of the failure path of the device-side waits (every wait in the
+ * library is bounded and ends in TSNNLS_ETIMEOUT instead of hanging): one
+ * kernel polls, at most `polls` times, a device flag that nothing sets.
+ * Returns TSNNLS_ETIMEOUT (the expected outcome; the device stays usable),
+ * TSNNLS_EINVAL for polls < 0, or a CUDA error status.  Current device, no
+ * context; allocates 2 small device buffers for the call. */
+int tsnnls_wait_probe(int64_t polls);
+
 /* Sparse products in FP64 on a device CSR matrix:
  *   trans == 0:  out = alpha * A x + beta * z   (x: n entries, out, z: m)
  *   trans == 1:  out = alpha * A^T x + beta * z (x: m entries, out, z: n)

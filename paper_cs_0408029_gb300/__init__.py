@@ -26,7 +26,7 @@ EXPORTS = (
     "tsnnls_solve_batch_dense", "tsnnls_gram", "tsnnls_gather", "tsnnls_cholesky",
     "tsnnls_chol_solve", "tsnnls_spmv", "tsnnls_profile_enable", "tsnnls_profile_read",
     "tsnnls_chol_solve_noalloc", "tsnnls_batch_autotune", "tsnnls_batch_set_panel",
-    "tsnnls_queue_stats_read",
+    "tsnnls_queue_stats_read", "tsnnls_wait_probe",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
         "tsnnls_profile_enable": ([p, i32], ctypes.c_int),
         "tsnnls_profile_read": ([p, p, i32], ctypes.c_int),
         "tsnnls_chol_solve_noalloc": ([i32, p, i64, i64, p, p], ctypes.c_int),
+        "tsnnls_wait_probe": ([i64], ctypes.c_int),
         "tsnnls_batch_autotune": ([p, i32, i32, p], ctypes.c_int),
         "tsnnls_batch_set_panel": ([i32, p], ctypes.c_int),
         "tsnnls_queue_stats_read": ([p, p], ctypes.c_int),
@@ -142,6 +143,11 @@ def default_opts(**kw) -> Opts:
             v = {"auto": PATH_AUTO, "factor": PATH_FACTOR, "lsqr": PATH_LSQR}[v]
         setattr(o, k, v)
     return o
+
+
+def wait_probe(polls: int) -> int:
+    """Status of one bounded device wait on a flag nothing sets (ETIMEOUT expected)."""
+    return load().tsnnls_wait_probe(int(polls))
 
 
 def chol_solve_noalloc(L, k, lds, rhs, precision=MIXED, stream=None):

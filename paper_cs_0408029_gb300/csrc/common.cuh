@@ -126,6 +126,10 @@ template <typename T>
 cudaError_t launch_trsv_multi(cudaStream_t s, const T *L, int64_t k, int64_t lds, T *rhs, int64_t rhs_ld, int q,
                               void *scratch, DevStatus *st, int dirs);
 
+// One bounded device wait on *flag >= 1 (limit polls), st->timeout = 1 when
+// it gives up (self-test of the waits' failure path).
+cudaError_t launch_wait_probe(cudaStream_t s, const int32_t *flag, int64_t limit, DevStatus *st);
+
 // out = alpha * M x + beta * z over a CSR (or CSC viewed as CSR of M^T).
 cudaError_t launch_spmv(cudaStream_t s, int64_t rows, const int64_t *ptr, const int32_t *idx,
                         const double *val, double alpha, const double *x, double beta,

@@ -837,6 +837,26 @@ __device__ __forceinline__ bool wait_at_least(const int32_t *p, int target, int3
     return *sh_ok != 0;
 }
 
+// Self-test of the bounded waits: thread 0 polls a flag that nothing sets for
+// at most `limit` polls, then records the timeout and returns.
+__global__ void wait_probe_kernel(const int32_t *flag, int64_t limit, DevStatus *st) {
+    if (threadIdx.x != 0) return;
+    int64_t spins = 0;
+    while (flag_load(flag) < 1) {
+        if (++spins > limit) {
+            st->timeout = 1;
+            return;
+        }
+        if (spins > 8) __nanosleep(32);
+    }
+}
+
+cudaError_t launch_wait_probe(cudaStream_t s, const int32_t *flag, int64_t limit, DevStatus *st) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(flag, limit, st);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 constexpr int kTrsvSeg = 4;      // tiles kept by the finisher, and the helpers' target length
 constexpr int kTrsvHelpers = 8;  // helpers per row at most
 

@@ -94,3 +94,21 @@ extern "C" int tsnnls_chol_solve_noalloc(int32_t precision, const void *L, int64
     if (e != cudaSuccess) return status_from_cuda(e);
     return timed_out ? TSNNLS_ETIMEOUT : TSNNLS_OK;
 }
+
+extern "C" int tsnnls_wait_probe(int64_t polls) {
+    if (polls < 0) return TSNNLS_EINVAL;
+    int32_t *flag = nullptr;
+    DevStatus *st = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&flag), sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&st), sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMemset(flag, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(DevStatus));
+    if (e == cudaSuccess) e = launch_wait_probe(nullptr, flag, polls, st);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int32_t timed_out = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&timed_out, &st->timeout, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (flag) cudaFree(flag);
+    if (st) cudaFree(st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    return timed_out ? TSNNLS_ETIMEOUT : TSNNLS_OK;
+}

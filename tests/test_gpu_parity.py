@@ -348,6 +348,16 @@ def test_empty_rows_and_degenerate(ts, ctx, oracle_mod):
     np.testing.assert_allclose(x, xs, rtol=0, atol=1e-10)
 
 
+def test_bounded_wait_reports_timeout(ts, ctx):
+    """A device wait on a flag that nothing sets gives up after its bound and
+    reports TSNNLS_ETIMEOUT; the device stays usable for the next solve."""
+    assert ts.wait_probe(1 << 16) == ts.ETIMEOUT
+    assert ts.wait_probe(-1) == ts.EINVAL
+    p = workloads.plain_single()
+    x, info = ctx.solve(ts.HostCSR.from_problem(p), p.b)
+    assert info.status == ts.OK and np.all(np.isfinite(x))
+
+
 def test_invalid_inputs(ts, ctx):
     p = workloads.random_sparse(40, 20, 0.2, seed=3)
     A = ts.HostCSR.from_problem(p)
