@@ -326,10 +326,6 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                      4.0 * nnz);
             return e;
         };
-        // Refinement of the current pivot's x_F on the factor in S (Section 3:
-        // FP32 solves, FP64 residuals), from `steps` solves done and the last
-        // correction `prev`.  allow_settle: stop before rel_tol once the
-        // settled test passes (*settled is then set).
         int64_t k = 0, lds = 32;
         // The pivot's solver: a fresh factor of G_FF in S (list F, k), or the
         // factor of an earlier base set B (kb, ldsb) reused with ba added and
@@ -344,6 +340,10 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             return reuse ? launch_border_solve<T>(s, S, kb, ldsb, ba, br, bb, v, trsv_scratch, lane.st_dev)
                          : launch_chol_solve<T>(s, S, k, lds, v, trsv_scratch, lane.st_dev);
         };
+        // Refinement of the current pivot's x_F on its solver (Section 3: FP32
+        // solves, FP64 residuals), from `steps` solves done and the last
+        // correction `prev`.  allow_settle: stop before rel_tol once the
+        // settled test passes (*settled is then set).
         auto refine = [&](int steps, double prev, bool allow_settle, bool *settled) -> int {
             *settled = false;
             for (;;) {
