@@ -15,10 +15,12 @@ Contents
 
 Parity status: every function here is pinned by a CPU test (brute-force
 enumeration, scipy's Lawson-Hanson NNLS, numpy's lstsq/cholesky, closed
-forms, constructed solutions).  The only unpinned quantity is the pivot
-*count*: the paper prints no worked example of the iteration, so the
-iteration counts of the oracle have no external reference (parity unpinned
-for iteration counts; the invariants of the exchange rule are tested).
+forms, constructed solutions); the exchange rule of the algorithm box,
+including the index the single-variable fallback moves, by a hand-worked
+example and by a numpy replay of every trace row.  The only unpinned
+quantity is the pivot *count* of the paper's own problems: the paper prints
+no worked iteration, so iteration counts have no external reference (parity
+unpinned for iteration counts).
 """
 from __future__ import annotations
 
@@ -171,7 +173,7 @@ def bpp_solve(prob, *, zero_tol=1e-12, p_max=3, max_iter=None, inner=INNER_CHOLE
     x = np.empty(n)
     y = np.empty(n)
     inF = np.empty(n, dtype=np.uint8)
-    trace = np.zeros((trace_cap, 5), dtype=np.int64)
+    trace = np.zeros((trace_cap, 6), dtype=np.int64)
     st = _load().oracle_bpp_solve(m, n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(b),
                                   ctypes.byref(opts), _ptr(x), _ptr(y), _ptr(inF),
                                   ctypes.byref(info), _ptr(trace), trace_cap)

@@ -369,9 +369,10 @@ static void compute_y(int64_t m, int64_t n, const int64_t *row_ptr, const int32_
 /*
  * Solve Eq. 1 by BPP.  x_out, y_out (length n) receive the final x and
  * y = A^T (A x - b) restricted to G (0 on F); inF_out (length n) the final
- * set F as 0/1.  trace, if non-NULL, receives up to trace_cap rows of five
+ * set F as 0/1.  trace, if non-NULL, receives up to trace_cap rows of six
  * int64 per pivot: {n_inf, N before the branch, p after the branch,
- * branch (0 = count dropped, 1 = backup full exchange, 2 = single), |F| after}.
+ * branch (0 = count dropped, 1 = backup full exchange, 2 = single), |F| after,
+ * the index the single exchange moved (-1 for a full exchange)}.
  */
 int oracle_bpp_solve(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
                      const double *val, const double *b, const oracle_opts *opts,
@@ -485,12 +486,13 @@ int oracle_bpp_solve(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t
         zero_small(y, n, opts->zero_tol);
 
         if (trace && iters < trace_cap) {
-            int64_t *t = trace + 5 * iters;
+            int64_t *t = trace + 6 * iters;
             t[0] = ninf;
             t[1] = Nprev;
             t[2] = p;
             t[3] = branch;
             t[4] = k;
+            t[5] = branch == 2 ? largest : -1;
         }
         ++iters;
     }

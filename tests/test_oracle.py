@@ -260,7 +260,8 @@ def test_invariances(oracle_mod):
 
 def _check_trace(trace, p_max=3):
     p_prev, n_best = p_max, None
-    for n_inf, n_before, p_after, branch, _ in trace:
+    for n_inf, n_before, p_after, branch, _, moved in trace:
+        assert (moved >= 0) == (branch == 2)
         if n_best is None:
             assert n_before == np.iinfo(np.int64).max  # N = infinity at the start
         else:
@@ -299,6 +300,99 @@ def test_single_exchange_fallback_reaches_solution(oracle_mod):
     r = oracle_mod.bpp_solve(p, p_max=0)
     _check_trace(r.trace, p_max=0)
     np.testing.assert_allclose(r.x, ref.x, rtol=1e-10, atol=1e-13)
+
+
+def _worked_fallback_problem():
+    """A 4 x 3 problem worked by hand for the single-variable rule.
+
+    Columns a0 = (1,0,0,0), a1 = (-1,1,1,0), a2 = (-1,1,-1,0) give
+    A^T A = [[1,-1,-1],[-1,3,1],[-1,1,3]]; b = (2,1,0,5) gives
+    c = A^T b = (2,-1,-1).  With p = 0 backup exchanges allowed:
+
+    pivot 1: y = -c = (-2,1,1); infeasible {0}, count 1 < N = inf, so N = 1
+             and the full exchange gives F = {0}; x_0 = c_0 / 1 = 2,
+             y_1 = y_2 = -1*2 - (-1) = -1.
+    pivot 2: infeasible {1, 2}, count 2 >= N = 1 and p = 0, so only the
+             largest infeasible index moves: F = {0, 2}.  Then
+             [[1,-1],[-1,3]] x_F = (2,-1) gives x_0 = 5/2, x_2 = 1/2, and
+             y_1 = -5/2 + 1/2 + 1 = -1.
+    pivot 3: infeasible {1}, count 1 >= N: the single exchange moves 1,
+             F = {0,1,2}, x = (A^T A)^{-1} c = (3, 1/2, 1/2) > 0: done.
+
+    Every value is a small dyadic rational, so no rounding enters.  Moving
+    the smallest infeasible index instead would move 1 at pivot 2 (and
+    reach the same x), which only the moved-index column tells apart."""
+    a = np.array([[1.0, -1.0, -1.0], [0.0, 1.0, 1.0], [0.0, 1.0, -1.0], [0.0, 0.0, 0.0]])
+    b = np.array([2.0, 1.0, 0.0, 5.0])
+    return a, b
+
+
+def test_single_exchange_moves_largest_index_worked_example(oracle_mod):
+    a, b = _worked_fallback_problem()
+    big = np.iinfo(np.int64).max
+    r = oracle_mod.bpp_solve(_dense_prob(a, b), p_max=0, final_step=oracle_mod.FINAL_NONE)
+    expect = np.array([[1, big, 0, 0, 1, -1],
+                       [2, 1, 0, 2, 2, 2],
+                       [1, 1, 0, 2, 3, 1]])
+    assert np.array_equal(r.trace, expect)
+    np.testing.assert_allclose(r.x, [3.0, 0.5, 0.5], rtol=1e-14)  # square roots round
+    # with the backup counter at its default the second pivot is a full exchange
+    r3 = oracle_mod.bpp_solve(_dense_prob(a, b), p_max=3, final_step=oracle_mod.FINAL_NONE)
+    assert [tuple(t[3:]) for t in r3.trace] == [(0, 1, -1), (1, 3, -1)]
+    np.testing.assert_allclose(r3.x, [3.0, 0.5, 0.5], rtol=1e-14)
+
+
+def _replay_exchange_rule(a, b, trace, p_max, zero_tol=1e-12):
+    """Replay the algorithm box of Section 2 from the trace's own decisions,
+    recomputing every pivot's x_F (numpy least squares on A_F) and
+    y_G = A_G^T (A_F x_F - b) (Eq. 5) without the oracle, and check each row:
+    the infeasible count, N and p, the branch, |F| and, for a single
+    exchange, that the moved index is the largest infeasible one."""
+    n = a.shape[1]
+    inF = np.zeros(n, dtype=bool)
+    x = np.zeros(n)
+    y = -(a.T @ b)
+    n_best, p = None, p_max
+    for i, (n_inf, n_before, p_after, branch, k, moved) in enumerate(trace):
+        infeas = np.nonzero(np.where(inF, x < 0, y < 0))[0]
+        assert n_inf == infeas.size, i
+        assert n_before == (np.iinfo(np.int64).max if n_best is None else n_best), i
+        if n_best is None or infeas.size < n_best:
+            n_best, p, want = infeas.size, p_max, 0
+        elif p > 0:
+            p, want = p - 1, 1
+        else:
+            want = 2
+        assert branch == want and p_after == p, i
+        if want == 2:
+            assert moved == infeas.max(), i
+            inF[infeas.max()] ^= True
+        else:
+            assert moved == -1, i
+            inF[infeas] ^= True
+        assert k == inF.sum(), i
+        x = np.zeros(n)
+        if inF.any():
+            x[inF] = np.linalg.lstsq(a[:, inF], b, rcond=None)[0]
+        y = a.T @ (a @ x - b)
+        y[inF] = 0.0
+        x[np.abs(x) < zero_tol] = 0.0
+        y[np.abs(y) < zero_tol] = 0.0
+    assert not np.where(inF, x < 0, y < 0).any()  # the last pivot is feasible
+
+
+@pytest.mark.parametrize("m,n,kappa,seed", [(60, 40, 1e3, 2), (30, 20, 3e2, 2),
+                                            (200, 150, 1e3, 3), (400, 300, 3e3, 4)])
+@pytest.mark.parametrize("p_max", [0, 3])
+def test_trace_replays_exchange_rule(oracle_mod, m, n, kappa, seed, p_max):
+    """The oracle's trace follows the exchange rule step by step, against x
+    and y recomputed in numpy from each pivot's F; with p_max = 0 these
+    conditioned problems take the single-variable fallback many times."""
+    prob, _, _ = workloads.conditioned_dense(m, n, kappa, seed=seed, active_frac=1.0)
+    r = oracle_mod.bpp_solve(_dense_prob(prob.a, prob.b), p_max=p_max)
+    _replay_exchange_rule(prob.a, prob.b, r.trace, p_max)
+    if p_max == 0:
+        assert (r.trace[:, 3] == 2).sum() >= 2
 
 
 def test_invalid_inputs_rejected(oracle_mod):
