@@ -116,6 +116,15 @@ typedef struct {
     double cond_est;         /* opts.cond_est: estimated kappa_1((A^T A)_FF) at the last pivot, else 0 */
     int32_t fallback_used;   /* 1 if a MIXED solve was redone in FP64 (opts.no_fallback) */
     int32_t factor_reuses;   /* pivots solved on an earlier pivot's factor, bordered (MIXED) */
+    double kkt_viol;         /* largest violation of Eq. 3 at the returned x, computed on the
+                                device in FP64 with y = A^T (A x - b):
+                                max(-min x, -min y, max_i |x_i y_i| / max(1, |x_i|)) / ||A^T b||_2
+                                (the solve's target is <= 1e-10); 0 unless status is OK */
+    double rel_resid_change; /* ||A dx||_2 / ||b - A x||_2 for the last refinement correction dx
+                                (the FP64 refinement that stands in for Section 3's final
+                                recompute): how much the last step still changed the residual;
+                                0 when the last pivot took no refinement step (the plain FP64
+                                path) or status is not OK */
 } tsnnls_info;
 
 typedef struct tsnnls_ctx tsnnls_ctx;
@@ -147,12 +156,13 @@ int tsnnls_solve(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *
 /* tsnnls_solve with extra outputs, for inspection and tests.  y_out (n
  * doubles) receives y = A^T (A x - b) on G and 0 on F (Eq. 3, Eq. 5);
  * inF_out (n bytes) the final F as 0/1 -- both in the same memory space as
- * x_out and written only on TSNNLS_OK.  trace (host, 5 * trace_cap int64)
+ * x_out and written only on TSNNLS_OK.  trace (host, 6 * trace_cap int64)
  * receives one row per pivot: {infeasible count, N before the branch
  * (INT64_MAX = infinity), p after the branch, branch (0 = count dropped and
  * full exchange, 1 = backup full exchange, 2 = single exchange of the
- * largest infeasible index), |F| after the exchange}.  Any of the three may
- * be NULL. */
+ * largest infeasible index), |F| after the exchange, the index that a single
+ * exchange moved (-1 after a full exchange)}.  Any of the three may be
+ * NULL. */
 int tsnnls_solve_ex(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double *x_out,
                     double *y_out, uint8_t *inF_out, int64_t *trace, int64_t trace_cap,
                     const tsnnls_opts *opts, tsnnls_info *info);
@@ -297,9 +307,11 @@ int tsnnls_chol_solve(tsnnls_ctx *ctx, int32_t precision, const void *L, int64_t
  * which may synchronise the whole device and can fail at run time.  This
  * call needs no context and allocates nothing: the caller passes the factor
  * L and the right-hand side (device memory, as for tsnnls_chol_solve), and
- * the solve's scratch (block flags, a ticket counter, a status word) lives
- * in one fixed array in the library's static device memory, about 4 KB that
- * every GPU which loads the library keeps until the process exits.
+ * the solve's scratch (block flags, a ticket counter, the published solution
+ * words, one partial vector per helper CTA and a status word) lives in one
+ * fixed array in the library's static device memory: about 5.3 MB (sized
+ * for k = TSNNLS_NOALLOC_MAX_K) that every GPU which loads the library keeps
+ * until the process exits.
  *
  *   precision  TSNNLS_MIXED (float L, rhs) or TSNNLS_FP64 (double)
  *   k, lds     order of L and its leading dimension; k may be at most
@@ -309,7 +321,8 @@ int tsnnls_chol_solve(tsnnls_ctx *ctx, int32_t precision, const void *L, int64_t
  *
  * Runs on the current CUDA device.  The first call on each device looks up
  * the device address of the static array (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array: calls
+ * first call before any stream capture.  The address is kept until the
+ * process exits, so do not call this after a cudaDeviceReset.  All calls share the array: calls
  * that overlap on the GPU (other host threads, other streams) race on it and
  * must be serialised by the caller.  Returns TSNNLS_ETIMEOUT if a bounded
  * wait inside the solve gave up. */
@@ -320,9 +333,13 @@ int tsnnls_chol_solve_noalloc(int32_t precision, const void *L, int64_t k, int64
 /* Self-test of the failure path of the device-side waits (every wait in the
  * library is bounded and ends in TSNNLS_ETIMEOUT instead of hanging): one
  * kernel polls, at most `polls` times, a device flag that nothing sets.
- * Returns TSNNLS_ETIMEOUT (the expected outcome; the device stays usable),
- * TSNNLS_EINVAL for polls < 0, or a CUDA error status.  Current device, no
- * context; allocates 2 small device buffers for the call. */
+ * polls may be at most TSNNLS_WAIT_PROBE_MAX_POLLS, the bound of every wait
+ * inside the solver (seconds of polling at most).  Returns TSNNLS_ETIMEOUT (the
+ * expected outcome; the device stays usable), TSNNLS_EINVAL for polls < 0 or
+ * above the maximum, or a CUDA error status.  Current device, no context;
+ * runs on a private non-blocking stream, but allocates and frees two small
+ * device buffers (cudaMalloc / cudaFree may synchronise the device). */
+#define TSNNLS_WAIT_PROBE_MAX_POLLS 4194304
 int tsnnls_wait_probe(int64_t polls);
 
 /* Sparse products in FP64 on a device CSR matrix:

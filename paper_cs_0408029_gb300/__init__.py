@@ -18,6 +18,7 @@ from . import build as _build_mod
 OK, EINVAL, ENOMEM, EADMIT, ENOTPD, EMAXITER, ENOCONV, ETIMEOUT, PENDING, ECUDA, ENODEV = range(11)
 MIXED, FP64 = 0, 1
 PATH_AUTO, PATH_FACTOR, PATH_LSQR = 0, 1, 2
+WAIT_PROBE_MAX_POLLS = 1 << 22  # TSNNLS_WAIT_PROBE_MAX_POLLS
 
 # every entry point declared in include/tsnnls.h
 EXPORTS = (
@@ -60,7 +61,8 @@ class Info(ctypes.Structure):
                 ("path_used", ctypes.c_int32), ("precision_used", ctypes.c_int32),
                 ("last_rel_step", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("cond_est", ctypes.c_double),
-                ("fallback_used", ctypes.c_int32), ("factor_reuses", ctypes.c_int32)]
+                ("fallback_used", ctypes.c_int32), ("factor_reuses", ctypes.c_int32),
+                ("kkt_viol", ctypes.c_double), ("rel_resid_change", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -266,7 +268,7 @@ class Context:
         return x, info
 
     def solve_ex(self, A: HostCSR, b, trace_cap=1000, opts=None, **kw):
-        """Host solve returning (x, y, inF(bool), trace[iters, 5], Info)."""
+        """Host solve returning (x, y, inF(bool), trace[iters, 6], Info)."""
         o = opts if opts is not None else default_opts(**kw)
         info = Info()
         s = A.struct()
@@ -274,7 +276,7 @@ class Context:
         x = np.empty(A.n)
         y = np.empty(A.n)
         f = np.empty(A.n, dtype=np.uint8)
-        tr = np.zeros((trace_cap, 5), dtype=np.int64)
+        tr = np.zeros((trace_cap, 6), dtype=np.int64)
         st = self._lib.tsnnls_solve_ex(self._h, ctypes.byref(s), _np_ptr(b), _np_ptr(x), _np_ptr(y),
                                        _np_ptr(f), _np_ptr(tr), trace_cap, ctypes.byref(o),
                                        ctypes.byref(info))

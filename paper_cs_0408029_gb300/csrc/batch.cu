@@ -862,13 +862,13 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
         if (e != cudaSuccess) break;
         cudaMemsetAsync(d_queue, 0, sizeof(int32_t), s);
         const int gitems = (int)items.size();
-        const int ggrid = std::max(1, std::min(gitems, 152 * 8));
+        const int ggrid = std::max(1, std::min(gitems, num_sms() * 8));
         if (mixed) batch_gram_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
         else batch_gram64_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
         note_launches(1);
-        batch_atb_kernel<<<std::min(count, 152 * 8), 256, 0, s>>>(d_probs, count);
+        batch_atb_kernel<<<std::min(count, num_sms() * 8), 256, 0, s>>>(d_probs, count);
         note_launches(1);
-        const int pgrid = std::min(count, 152);
+        const int pgrid = std::min(count, num_sms());
         if (mixed)
             batch_bpp_kernel<float><<<pgrid, kBT, smem, s>>>(d_probs, count, d_queue, prm, d_out);
         else

@@ -344,7 +344,7 @@ cudaError_t launch_border_count(cudaStream_t s, int64_t n, const uint8_t *inF, c
     static_assert(offsetof(DevStatus, border_r) == offsetof(DevStatus, border_a) + sizeof(int32_t), "adjacent");
     cudaError_t e = cudaMemsetAsync(&st->border_a, 0, 2 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), num_sms()));
     border_count_kernel<<<g, 256, 0, s>>>(n, inF, b.inB, st);
     note_launches(1);
     return cudaGetLastError();
@@ -367,7 +367,7 @@ cudaError_t launch_border_setup(cudaStream_t s, const T *G, int64_t ldg, const T
     if (e != cudaSuccess) return e;
     if (a > 0) {
         const int64_t work = (kb + a) * a;
-        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(work, 256), 152 * 8));
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(work, 256), num_sms() * 8));
         border_gather_kernel<T><<<g, 256, 0, s>>>(G, ldg, b.Bl, kb, b.Al, a, Pt, b.ldp, b.GAA);
         note_launches(1);
         e = launch_trsv_multi<T>(s, L, kb, lds, Pt, b.ldp, a, b.multi, st, 1);
@@ -377,7 +377,7 @@ cudaError_t launch_border_setup(cudaStream_t s, const T *G, int64_t ldg, const T
         note_launches(2);
     }
     if (r > 0) {
-        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(u * r, 256), 152 * 8));
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(u * r, 256), num_sms() * 8));
         border_unit_kernel<T><<<g, 256, 0, s>>>(Z, u, b.ldz, r, b.Rpos);
         note_launches(1);
         // the r columns of Z side by side: forward, border step, backward
@@ -406,7 +406,7 @@ cudaError_t launch_border_solve(cudaStream_t s, const T *L, int64_t kb, int64_t 
     if (e == cudaSuccess) e = launch_trsv_bwd<T>(s, L, kb, lds, z, trsv_scratch, st);
     if (e == cudaSuccess && r > 0) {
         border_cap_mu_kernel<T><<<1, 32, 0, s>>>(z, r, b.Rpos, b.Lc, b.mu);
-        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(u, 256), 152 * 2));
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(u, 256), num_sms() * 2));
         border_cap_apply_kernel<T><<<g, 256, 0, s>>>(z, u, r, static_cast<const T *>(b.Z), b.ldz, b.mu);
         note_launches(2);
     }

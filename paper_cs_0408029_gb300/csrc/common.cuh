@@ -28,14 +28,22 @@ struct DevStatus {
     int32_t unsettled;  // entries whose sign / zeroing decision the last check left open
     int32_t border_a;   // variables in F but not in the factored base set (border.cu)
     int32_t border_r;   // variables of the base set no longer in F
+    int32_t moved;      // index the single exchange moved (branch 2), else -1
+    int32_t pad_;
     double dnorm;       // ||dx_F||_inf of the last refinement step
     double xnorm;       // ||x_F||_inf after it
+    double kkt_viol;      // quality.cu: violation of Eq. 3 / ||A^T b||_2 at the final x
+    double resid_change;  // quality.cu: ||A dx||_2 / ||b - A x||_2 of the last correction
 };
 
 constexpr int kSpinLimit = 1 << 22;  // bounded polls (with backoff) before a wait gives up
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+// Streaming multiprocessors of the current device (queried once per device;
+// launch sizes are multiples of it).
+int num_sms();
 
 // Launch accounting: every launcher below calls note_launches() once per
 // kernel it starts; the engine reads the per-thread count around a solve.
@@ -207,6 +215,24 @@ cudaError_t launch_gram_norm1(cudaStream_t s, const T *G, int64_t ldg, const int
                               double *scratch, double *out);
 cudaError_t launch_y_from_s(cudaStream_t s, int64_t n, const double *sv, const uint8_t *inF,
                             double *y);
+
+// Quality of a finished solve (quality.cu): st->kkt_viol and st->resid_change
+// from the final x, s = A^T (b - A x), c = A^T b, r = b - A x and the last
+// correction (delta over list[0..len), list entries -1 skipped; NULL: none).
+// scratch: quality_scratch_bytes(m, n) bytes, 256-byte aligned.
+size_t quality_scratch_bytes(int64_t m, int64_t n);
+template <typename T>
+cudaError_t launch_quality(cudaStream_t s, int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                           const double *val, double avg_row, const double *x, const double *sv,
+                           const double *c, const double *r, const T *delta, const int32_t *list,
+                           int64_t len, void *scratch, DevStatus *st);
+// The same with the correction given as D z on the columns of F (LSQR path).
+template <typename V>
+cudaError_t launch_quality_scaled(cudaStream_t s, int64_t m, int64_t n, const int64_t *row_ptr,
+                                  const int32_t *col, const double *val, double avg_row, const double *x,
+                                  const double *sv, const double *c, const double *r, const V *D,
+                                  const V *z, const uint8_t *inF, bool have_delta, void *scratch,
+                                  DevStatus *st);
 
 }  // namespace tsnnls
 

@@ -35,6 +35,18 @@ thread_local int64_t g_launches = 0;
 }
 
 void note_launches(int n) { g_launches += n; }
+
+int num_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 int64_t launches_so_far() { return g_launches; }
 
 static cudaEvent_t pool_event(Lane &l) {
@@ -155,6 +167,7 @@ size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     c.take<int32_t>(n);
     c.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
     c.take<char>(border_bytes(n, sizeof(T)));  // reuse of a factor across pivots
+    c.take<char>(quality_scratch_bytes(m, n));
     if (sizeof(T) == 4) {
         c.take<float>((size_t)n * 128);  // K-major hi / lo panel copies for the tensor-core update
         c.take<float>((size_t)n * 128);
@@ -276,6 +289,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         int32_t *F = cv.take<int32_t>(n);
         void *trsv_scratch = cv.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
         const BorderBuffers bb = border_carve(cv.take<char>(border_bytes(n, sizeof(T))), n, sizeof(T));
+        void *qscratch = cv.take<char>(quality_scratch_bytes(m, n));
         TcPanel tc;
         if (sizeof(T) == 4) {
             float *xhi = cv.take<float>((size_t)n * 128);
@@ -419,12 +433,13 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 break;
             }
             if (ex && ex->trace && trace_rows < ex->trace_cap) {
-                int64_t *t = ex->trace + 5 * trace_rows;
+                int64_t *t = ex->trace + kTraceCols * trace_rows;
                 t[0] = st.n_inf;
                 t[1] = -1;  // filled below from the previous row
                 t[2] = st.p;
                 t[3] = st.branch;
                 t[4] = st.k;
+                t[5] = st.moved;
             }
             k = st.k;
             lds = round_up(std::max<int64_t>(k, 1), 32);
@@ -512,6 +527,18 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             prof_end(lane, 17.0 * n, 0.0);
             ++trace_rows;
         }
+        if (status == TSNNLS_OK) {
+            // KKT violation and last residual change at the returned x (before
+            // the condition estimate reuses rhs); the mixed path's last
+            // correction is still in rhs, over the last pivot's list
+            if (trace_rows == 0) TRY_CUDA(residual());  // no pivot ran: r, s of x = 0
+            prof_begin(lane, TSNNLS_PHASE_VECTOR);
+            const bool have_delta = mixed && k > 0;
+            TRY_CUDA(launch_quality<T>(s, m, n, row_ptr, col, val, avg_row, x, sv, c, r,
+                                       have_delta ? rhs : nullptr, sol_list(), have_delta ? sol_len() : 0,
+                                       qscratch, lane.st_dev));
+            prof_end(lane, 8.0 * (2.0 * m + 4.0 * n) + (have_delta ? csr_bytes + 16.0 * m : 0.0), 0.0);
+        }
         if (status == TSNNLS_OK && o.cond_est && k > 0) {
             // kappa_1 of the last pivot's (A^T A)_FF: its 1-norm times an
             // estimate of ||(A^T A)_FF^-1||_1 from solves with the factor still
@@ -568,6 +595,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         if (status == TSNNLS_OK) {
             TRY_CUDA(cudaEventRecord(lane.ev1, s));
             const cudaMemcpyKind kind = host_in ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+            TRY_CUDA(cudaMemcpyAsync(lane.st_host, lane.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
             TRY_CUDA(cudaMemcpyAsync(x_out, x, sizeof(double) * n, kind, s));
             if (ex && ex->y_out) TRY_CUDA(cudaMemcpyAsync(ex->y_out, y, sizeof(double) * n, kind, s));
             if (ex && ex->inF_out)
@@ -581,6 +609,10 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             info->nF = lane.st_host->k;
             info->cond_est = cond;
             info->factor_reuses = reuses;
+            if (status == TSNNLS_OK) {
+                info->kkt_viol = lane.st_host->kkt_viol;
+                info->rel_resid_change = lane.st_host->resid_change;
+            }
         }
     }
 cleanup:
@@ -591,8 +623,8 @@ cleanup:
         // column 1: N before the branch = smallest count over the earlier pivots
         int64_t best = INT64_MAX;
         for (int64_t i = 0; i < std::min(trace_rows, ex->trace_cap); ++i) {
-            ex->trace[5 * i + 1] = best;
-            best = std::min(best, ex->trace[5 * i]);
+            ex->trace[kTraceCols * i + 1] = best;
+            best = std::min(best, ex->trace[kTraceCols * i]);
         }
     }
     if (info) {

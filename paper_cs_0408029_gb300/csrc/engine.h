@@ -67,11 +67,14 @@ struct Request {
     bool done = false;
 };
 
+// Columns of a pivot-trace row (tsnnls_solve_ex).
+constexpr int kTraceCols = 6;
+
 // Extra outputs of a solve (for tests and tools); any pointer may be NULL.
 struct SolveExtras {
     double *y_out = nullptr;       // n entries, same memory space as x_out
     uint8_t *inF_out = nullptr;    // n entries, same memory space as x_out
-    int64_t *trace = nullptr;      // host, 5 per pivot
+    int64_t *trace = nullptr;      // host, kTraceCols per pivot
     int64_t trace_cap = 0;
 };
 

@@ -30,6 +30,7 @@ __global__ void init_state_kernel(int64_t n, const double *__restrict__ c, doubl
         st->N = INT64_MAX;
         st->p = p_max;
         st->branch = -1;
+        st->moved = -1;
         st->done = 0;
         st->iters = 0;
         st->chol_info = 0;
@@ -42,7 +43,7 @@ __global__ void init_state_kernel(int64_t n, const double *__restrict__ c, doubl
 
 cudaError_t launch_init_state(cudaStream_t s, int64_t n, const double *c, double *x, double *y,
                               uint8_t *inF, int32_t p_max, DevStatus *st) {
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 8));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), num_sms() * 8));
     init_state_kernel<<<g, 256, 0, s>>>(n, c, x, y, inF, p_max, st);
     note_launches(1);
     return cudaGetLastError();
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kExThreads)
             d = 2;
         }
         st->branch = d;
+        st->moved = d == 2 ? (int32_t)big : -1;
         decision = d;
     }
     __syncthreads();
@@ -209,7 +211,7 @@ template <typename T>
 cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, const int32_t *F, int64_t k,
                               T *out) {
     if (k <= 0) return cudaSuccess;
-    const int g = (int)std::min<int64_t>(cdiv(k, 256), 152 * 8);
+    const int g = (int)std::min<int64_t>(cdiv(k, 256), num_sms() * 8);
     gather_rhs_kernel<T><<<g, 256, 0, s>>>(v, F, k, out);
     note_launches(1);
     return cudaGetLastError();
@@ -266,7 +268,7 @@ cudaError_t launch_update_x(cudaStream_t s, const T *delta, const int32_t *F, in
     static_assert(offsetof(DevStatus, xnorm) == offsetof(DevStatus, dnorm) + sizeof(double), "adjacent norms");
     cudaError_t e = cudaMemsetAsync(&st->dnorm, 0, 2 * sizeof(double), s);
     if (e != cudaSuccess) return e;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(k, 256), 152));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(k, 256), num_sms()));
     update_x_kernel<T><<<g, 256, 0, s>>>(delta, F, k, x, st);
     note_launches(1);
     return cudaGetLastError();
@@ -308,8 +310,8 @@ __global__ void abs_col_dot_kernel(int64_t n, const int64_t *__restrict__ col_pt
 cudaError_t launch_gram_row_bound(cudaStream_t s, int64_t m, int64_t n, const int64_t *row_ptr,
                                   const double *val, const int64_t *col_ptr, const int32_t *row_idx,
                                   const double *cval, double *t, double *c) {
-    const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 256), 152 * 8));
-    const int gn = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 8));
+    const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 256), num_sms() * 8));
+    const int gn = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), num_sms() * 8));
     abs_row_sum_kernel<<<gm, 256, 0, s>>>(m, row_ptr, val, t);
     abs_col_dot_kernel<<<gn, 256, 0, s>>>(n, col_ptr, row_idx, cval, t, c);
     note_launches(2);
@@ -343,7 +345,7 @@ cudaError_t launch_settled(cudaStream_t s, int64_t n, const uint8_t *inF, const 
                            const double *sv, const double *c, double E, double zero_tol, DevStatus *st) {
     cudaError_t e = cudaMemsetAsync(&st->unsettled, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 2));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), num_sms() * 2));
     settled_kernel<<<g, 256, 0, s>>>(n, inF, x, sv, c, E, zero_tol, st);
     note_launches(1);
     return cudaGetLastError();
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(kExThreads)
 
 template <typename T>
 cudaError_t launch_est_fill(cudaStream_t s, T *v, int64_t k, int32_t mode, int64_t j) {
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(k, 256), 152 * 4));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(k, 256), num_sms() * 4));
     est_fill_kernel<T><<<g, 256, 0, s>>>(v, k, mode, j);
     note_launches(1);
     return cudaGetLastError();
@@ -474,7 +476,7 @@ __global__ void y_from_s_kernel(int64_t n, const double *__restrict__ sv,
 
 cudaError_t launch_y_from_s(cudaStream_t s, int64_t n, const double *sv, const uint8_t *inF,
                             double *y) {
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 8));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), num_sms() * 8));
     y_from_s_kernel<<<g, 256, 0, s>>>(n, sv, inF, y);
     note_launches(1);
     return cudaGetLastError();

@@ -707,7 +707,9 @@ cudaError_t launch_cholesky(cudaStream_t s, T *S, int64_t k, int64_t lds, DevSta
             if (kt) kt->begin(TSNNLS_PHASE_FACTOR_DIAG);
             chol_diag_kernel<T, NB><<<1, 256, smem_diag, s>>>(S, k, lds, K, st);
             note_launches(1);
-            if (kt) kt->end(2.0 * sizeof(T) * kbd * kbd, 2.0 * kbd * kbd * kbd / 3.0);
+            // the method's own work: the block's Cholesky, kb^3 / 3 (the inverse
+            // built alongside, another kb^3 / 3, is this design's extra work)
+            if (kt) kt->end(2.0 * sizeof(T) * kbd * kbd, kbd * kbd * kbd / 3.0);
             if (below == 0) break;
             if (kt) kt->begin(TSNNLS_PHASE_FACTOR_PANEL);
             panel(s, K, K + kb, k);
@@ -816,6 +818,11 @@ __device__ __forceinline__ void word_store(uint64_t *p, uint64_t v) {
 }
 
 // Thread 0 polls until *p >= target (bounded), the CTA learns the outcome.
+// Ordering: the producer writes its data, then publishes with a release
+// store (flag_store / count_add); thread 0 reads the flag with an acquire
+// load, so the producer's writes happen before everything thread 0 does
+// next, and the CTA barrier below extends that to every thread of the CTA,
+// whose reads of the published data come after the barrier.
 __device__ __forceinline__ bool wait_at_least(const int32_t *p, int target, int32_t *abort_flag,
                                               DevStatus *st, int *sh_ok) {
     if (threadIdx.x == 0) {

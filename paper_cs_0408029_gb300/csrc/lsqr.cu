@@ -36,7 +36,7 @@ struct LsqrScalars {
 };
 
 constexpr int kLT = 256;
-constexpr int kMaxPartials = 152 * 8;
+constexpr int kMaxPartials = 4096;  // cap of the per-CTA partial sums (>= 8 CTAs per SM)
 
 // Sum of `count` partials in a fixed order, broadcast to the CTA.
 __device__ __forceinline__ double sum_partials(const double *__restrict__ part, int count,
@@ -445,6 +445,7 @@ size_t lsqr_layout(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     size_t b = 0;
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
     if (host_in) b += up(8 * (m + 1)) + up(4 * nnz) + up(8 * nnz) + up(8 * m);
+    b += up(quality_scratch_bytes(m, n));
     b += up(8 * (n + 1)) + up(4 * nnz) + up(8 * nnz) + up(4 * (n + 1)) + up(8 * (n + 1));  // CSC
     b += 2 * up(sizeof(V) * nnz) + up(sizeof(V) * n);  // value copies, D
     b += 5 * up(8 * n) + up(8 * m);                     // c, x, y, s, xprev; r
@@ -474,6 +475,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
     cudaStream_t s = lane.stream;
     int status = TSNNLS_OK;
     int outer_total = 0, inner_total = 0;
+    int last_steps = 0;  // outer corrections of the last pivot (its z is the last one)
     double last_rel = 0.0;
     int64_t trace_rows = 0;
     const int64_t launch0 = launches_so_far();
@@ -516,6 +518,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         bd = b;
     }
     {
+        void *qscratch = take(quality_scratch_bytes(m, n));
         int64_t *col_ptr = (int64_t *)take(8 * (n + 1));
         int32_t *row_idx = (int32_t *)take(4 * nnz);
         double *cval = (double *)take(8 * nnz);
@@ -545,7 +548,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         const double csc_bytes = 12.0 * nnz + 8.0 * (n + 1);
         LsqrLaunch<V> L{s, m, n, row_ptr, col_ptr, col, row_idx, val_v, cval_v, D, inF,
                         u, v, w, z, dv, part_u, part_v, sc, tpr_for(avg_row), tpr_for_cols(avg_col)};
-        const int gconv = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nnz, 256), 152 * 8));
+        const int gconv = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nnz, 256), num_sms() * 8));
 
         TRY_CUDA_L(cudaEventRecord(lane.ev0, s));
         prof_begin(lane, TSNNLS_PHASE_SETUP);
@@ -560,7 +563,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         TRY_CUDA_L(launch_csr_to_csc(s, m, n, nnz, row_ptr, col, val, col_ptr, row_idx, cval, cnt, next));
         convert_kernel<V><<<gconv, 256, 0, s>>>(nnz, val, val_v);
         convert_kernel<V><<<gconv, 256, 0, s>>>(nnz, cval, cval_v);
-        lsqr_prep_kernel<V><<<(int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 8)), 256, 0, s>>>(
+        lsqr_prep_kernel<V><<<(int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), num_sms() * 8)), 256, 0, s>>>(
             n, col_ptr, cval, D);
         note_launches(3);
         prof_end(lane, 2.0 * csr_bytes + 2.0 * csc_bytes + 2.0 * sizeof(V) * nnz, 0.0);
@@ -589,14 +592,15 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 break;
             }
             if (ex && ex->trace && trace_rows < ex->trace_cap) {
-                int64_t *t = ex->trace + 5 * trace_rows;
+                int64_t *t = ex->trace + kTraceCols * trace_rows;
                 t[0] = st.n_inf;
                 t[1] = -1;
                 t[2] = st.p;
                 t[3] = st.branch;
                 t[4] = st.k;
+                t[5] = st.moved;
             }
-            keep_x_on_F_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 8)), 256, 0, s>>>(
+            keep_x_on_F_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), num_sms() * 8)), 256, 0, s>>>(
                 n, inF, x, xprev);
             note_launches(1);
             const int64_t k = st.k;
@@ -654,10 +658,21 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col));
             prof_end(lane, csc_bytes + 8.0 * (m + n), 2.0 * nnz);
             TRY_CUDA_L(launch_y_from_s(s, n, sv, inF, y));
+            last_steps = steps;
             ++trace_rows;
         }
         if (status == TSNNLS_OK) {
+            if (trace_rows == 0) {  // no pivot ran: r and s of x = 0
+                TRY_CUDA_L(launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row));
+                TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col));
+            }
+            // KKT violation and the residual change of the last correction D z
+            prof_begin(lane, TSNNLS_PHASE_VECTOR);
+            TRY_CUDA_L(launch_quality_scaled<V>(s, m, n, row_ptr, col, val, avg_row, x, sv, c, r, D, z, inF,
+                                                last_steps > 0, qscratch, lane.st_dev));
+            prof_end(lane, 8.0 * (2.0 * m + 4.0 * n) + (last_steps > 0 ? csr_bytes + 16.0 * m : 0.0), 0.0);
             TRY_CUDA_L(cudaEventRecord(lane.ev1, s));
+            TRY_CUDA_L(cudaMemcpyAsync(lane.st_host, lane.st_dev, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
             const cudaMemcpyKind kind = host_in ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
             TRY_CUDA_L(cudaMemcpyAsync(x_out, x, 8 * n, kind, s));
             if (ex && ex->y_out) TRY_CUDA_L(cudaMemcpyAsync(ex->y_out, y, 8 * n, kind, s));
@@ -669,6 +684,10 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         if (info) {
             info->iters = lane.st_host->iters;
             info->nF = lane.st_host->k;
+            if (status == TSNNLS_OK) {
+                info->kkt_viol = lane.st_host->kkt_viol;
+                info->rel_resid_change = lane.st_host->resid_change;
+            }
         }
     }
 cleanup:
@@ -678,8 +697,8 @@ cleanup:
     if (ex && ex->trace) {
         int64_t best = INT64_MAX;
         for (int64_t i = 0; i < std::min(trace_rows, ex->trace_cap); ++i) {
-            ex->trace[5 * i + 1] = best;
-            best = std::min(best, ex->trace[5 * i]);
+            ex->trace[kTraceCols * i + 1] = best;
+            best = std::min(best, ex->trace[kTraceCols * i]);
         }
     }
     if (info) {

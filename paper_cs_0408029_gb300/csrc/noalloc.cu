@@ -42,7 +42,10 @@ void *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  In host code
 // the symbol names a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The
+// address is kept for the life of the process: a cudaDeviceReset after the
+// first call would leave it stale, so the entry point is not for use after
+// a device reset.
 int scratch_for_current_device(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -95,20 +98,28 @@ extern "C" int tsnnls_chol_solve_noalloc(int32_t precision, const void *L, int64
     return timed_out ? TSNNLS_ETIMEOUT : TSNNLS_OK;
 }
 
+static_assert(kSpinLimit == TSNNLS_WAIT_PROBE_MAX_POLLS, "the probe's limit is the waits' bound");
+
 extern "C" int tsnnls_wait_probe(int64_t polls) {
-    if (polls < 0) return TSNNLS_EINVAL;
+    // the same bound as every wait inside the solver: a larger count could
+    // keep a shared GPU polling for a practically unlimited time
+    if (polls < 0 || polls > kSpinLimit) return TSNNLS_EINVAL;
     int32_t *flag = nullptr;
     DevStatus *st = nullptr;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&flag), sizeof(int32_t));
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&flag), sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&st), sizeof(DevStatus));
-    if (e == cudaSuccess) e = cudaMemset(flag, 0, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(DevStatus));
-    if (e == cudaSuccess) e = launch_wait_probe(nullptr, flag, polls, st);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess) e = launch_wait_probe(s, flag, polls, st);
     int32_t timed_out = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&timed_out, &st->timeout, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&timed_out, &st->timeout, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (flag) cudaFree(flag);
     if (st) cudaFree(st);
+    if (s) cudaStreamDestroy(s);
     if (e != cudaSuccess) return status_from_cuda(e);
     return timed_out ? TSNNLS_ETIMEOUT : TSNNLS_OK;
 }

@@ -135,17 +135,17 @@ cudaError_t launch_csr_to_csc(cudaStream_t s, int64_t m, int64_t n, int64_t nnz,
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int32_t) * (size_t)(n + 1), s);
     if (e != cudaSuccess) return e;
     if (nnz > 0) {
-        int g = (int)std::min<int64_t>(cdiv(nnz, 256), 152 * 16);
+        int g = (int)std::min<int64_t>(cdiv(nnz, 256), num_sms() * 16);
         csc_count_kernel<<<g, 256, 0, s>>>(nnz, col, work);
         note_launches(1);
     }
     csc_scan_kernel<<<1, 1024, 0, s>>>(n, work, col_ptr, scan_work);
     note_launches(1);
     if (nnz > 0) {
-        int g = (int)std::min<int64_t>(cdiv(m, 128), 152 * 16);
+        int g = (int)std::min<int64_t>(cdiv(m, 128), num_sms() * 16);
         csc_fill_kernel<<<g, 128, 0, s>>>(m, row_ptr, col, val, scan_work, row_idx, cval);
         note_launches(1);
-        int gs = (int)std::min<int64_t>(n, 152 * 8);
+        int gs = (int)std::min<int64_t>(n, num_sms() * 8);
         csc_sort_kernel<<<gs, 256, 0, s>>>(n, col_ptr, row_idx, cval);
         note_launches(1);
     }
@@ -317,7 +317,7 @@ cudaError_t launch_spmv(cudaStream_t s, int64_t rows, const int64_t *ptr, const 
                         const double *z, double *out, double avg_nnz) {
     if (rows == 0) return cudaSuccess;
     auto grid_for = [&](int tpr) {
-        return (int)std::min<int64_t>(cdiv(rows * tpr, 256), 152 * 32);
+        return (int)std::min<int64_t>(cdiv(rows * tpr, 256), num_sms() * 32);
     };
     if (avg_nnz <= 3) {
         spmv_kernel<2><<<grid_for(2), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, beta, z, out);
@@ -368,7 +368,7 @@ __global__ void validate_kernel(int64_t m, int64_t n, int64_t nnz,
 cudaError_t launch_validate(cudaStream_t s, int64_t m, int64_t n, int64_t nnz,
                             const int64_t *row_ptr, const int32_t *col, const double *val,
                             const double *b, int32_t *bad) {
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 256), 152 * 8));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 256), num_sms() * 8));
     validate_kernel<<<g, 256, 0, s>>>(m, n, nnz, row_ptr, col, val, b, bad);
     note_launches(1);
     return cudaGetLastError();

@@ -40,12 +40,17 @@ def _worker(rank, ws, port, out_q, mode):
             slowest = r.max_over_ranks(1.0 + rank)  # rank 1 is the slow one
             out_q.put((rank, slowest, r.value(5, slowest)))
         else:
-            # the reference arm with a stub for the oracle sample: rank 0
-            # alone prints its line, the other ranks return without work
-            bench.cpu_baseline = lambda prob, ks: {"value": 2.0, "sample": "stub"}
+            # the reference arm with a stub for the oracle's timed solves:
+            # rank 0 alone prints its line, the other ranks return without work
+            import types
+
+            import numpy as np
+
+            stub = types.SimpleNamespace(iters=3, x=np.zeros(8000))
+            bench.oracle_full_solves = lambda prob, count, budget_s, warmup=0: ([0.5, 0.5], stub)
 
             class Args:
-                steps, warmup = 2, 0
+                steps, warmup, ref_budget_s = 2, 0, 60.0
 
             buf = io.StringIO()
             with redirect_stdout(buf):
@@ -85,3 +90,4 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert len(lines0) == 1 and res[1][1].strip() == ""
     d = json.loads(lines0[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] == pytest.approx(2.0)
+    assert d["steps"] == 2 and d["ms_per_step"] == pytest.approx(500.0)

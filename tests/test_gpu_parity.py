@@ -170,6 +170,86 @@ def test_random_sparse_tiles_and_tails(ts, ctx, oracle_mod, m, n, density, seed)
         assert np.array_equal(trace, ref.trace), precision
 
 
+def _worked_fallback_problem():
+    """The 4 x 3 example worked by hand in tests/test_oracle.py: with no
+    backup exchanges the second and third pivots are single exchanges that
+    move index 2 (the larger of the tied infeasible {1, 2}) and then 1."""
+    a = np.array([[1.0, -1.0, -1.0], [0.0, 1.0, 1.0], [0.0, 1.0, -1.0], [0.0, 0.0, 0.0]])
+    b = np.array([2.0, 1.0, 0.0, 5.0])
+    return workloads.dense_to_csr(a, b)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_single_exchange_worked_example(ts, ctx, oracle_mod, precision):
+    """Section 2, algorithm box: once the backup counter is spent, only the
+    infeasible variable with the largest index changes sides."""
+    p = _worked_fallback_problem()
+    big = np.iinfo(np.int64).max
+    expect = np.array([[1, big, 0, 0, 1, -1], [2, 1, 0, 2, 2, 2], [1, 1, 0, 2, 3, 1]])
+    ref = oracle_mod.bpp_solve(p, p_max=0)
+    assert np.array_equal(ref.trace, expect)
+    x, y, inF, trace, info = ctx.solve_ex(ts.HostCSR.from_problem(p), p.b, precision=precision,
+                                          p_max=0)
+    assert np.array_equal(trace, expect)
+    np.testing.assert_allclose(x, [3.0, 0.5, 0.5], rtol=1e-13)
+    assert inF.all()
+
+
+def _fallback_cases():
+    prob, _, _ = workloads.conditioned_dense(400, 300, 3e3, seed=4, active_frac=1.0)
+    return [("plain_single_600x400", workloads.plain_single()),
+            ("conditioned_400x300", workloads.dense_to_csr(prob.a, prob.b))]
+
+
+@pytest.mark.parametrize("case", [0, 1])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_single_exchange_trace_matches_oracle(ts, ctx, oracle_mod, case, precision):
+    """p_max = 0 makes every pivot whose infeasible count does not drop a
+    single exchange.  On the 600 x 400 config (3 such pivots) and on a
+    conditioned 400 x 300 problem whose final F spans two 128-column blocks
+    and a ragged tail (15 of 31 pivots), the GPU's pivot trace, including the
+    index each single exchange moved, equals the oracle's."""
+    name, p = _fallback_cases()[case]
+    ref = oracle_mod.bpp_solve(p, p_max=0)
+    singles = ref.trace[:, 3] == 2
+    assert singles.sum() >= 3
+    x, y, inF, trace, info = ctx.solve_ex(ts.HostCSR.from_problem(p), p.b, precision=precision,
+                                          p_max=0)
+    _check_solution(p, ref, x, inF)
+    assert np.array_equal(trace, ref.trace), name
+    assert np.array_equal(trace[singles, 5], ref.trace[singles, 5])
+
+
+@pytest.mark.parametrize("kw", [{}, {"precision": "fp64"}, {"path": "lsqr"}])
+def test_info_quality_fields(ts, ctx, kw):
+    """info.kkt_viol is the violation of Eq. 3 at the returned x over
+    ||A^T b||, computed on the device; it must agree with the CPU
+    certificate (scipy products) to rounding.  info.rel_resid_change is the
+    residual change of the last refinement correction: small once the
+    refinement has converged, 0 on the plain FP64 path, which takes none."""
+    p = workloads.plain_single()
+    x, info = ctx.solve(ts.HostCSR.from_problem(p), p.b, **kw)
+    want = kkt.violation(p, x) / kkt.atb_norm(p)
+    assert want <= KKT_FACTOR
+    assert info.kkt_viol <= KKT_FACTOR
+    assert abs(info.kkt_viol - want) <= 1e-14
+    if kw.get("precision") == "fp64":
+        assert info.rel_resid_change == 0.0
+    else:
+        assert 0.0 < info.rel_resid_change <= 1e-8
+
+
+def test_info_quality_fields_zero_pivots(ts, ctx):
+    """A^T b <= 0: x = 0 after no pivot; the certificate is then that of x = 0."""
+    rng = np.random.default_rng(40)
+    a = np.abs(rng.standard_normal((20, 6)))
+    b = -np.abs(rng.standard_normal(20))
+    p = workloads.dense_to_csr(a, b)
+    x, info = ctx.solve(ts.HostCSR.from_problem(p), p.b)
+    assert info.iters == 0 and info.rel_resid_change == 0.0
+    assert abs(info.kkt_viol - kkt.violation(p, x) / kkt.atb_norm(p)) <= 1e-15
+
+
 def test_device_input_matches_host_input(ts, ctx, torch_cuda):
     torch = torch_cuda
     p = workloads.random_sparse(800, 500, 0.02, seed=9)
@@ -353,6 +433,7 @@ def test_bounded_wait_reports_timeout(ts, ctx):
     reports TSNNLS_ETIMEOUT; the device stays usable for the next solve."""
     assert ts.wait_probe(1 << 16) == ts.ETIMEOUT
     assert ts.wait_probe(-1) == ts.EINVAL
+    assert ts.wait_probe(ts.WAIT_PROBE_MAX_POLLS + 1) == ts.EINVAL  # no unbounded waits
     p = workloads.plain_single()
     x, info = ctx.solve(ts.HostCSR.from_problem(p), p.b)
     assert info.status == ts.OK and np.all(np.isfinite(x))

@@ -6,8 +6,10 @@ device-wide synchronisation) use this entry point: it runs the same
 triangular solves as tsnnls_chol_solve with the scratch in a static device
 array.  The test calls it through the C ABI twice in a row and checks each
 result against tsnnls_chol_solve on the same factor, within the tolerance
-the other factor tests use.  The file name sorts last so that a run stopping
-at the first failure has already run every other test.
+the other factor tests use, and against the CPU oracle's textbook Cholesky
+solve of the same matrix, within the tolerances of the factor parity tests.
+The file name sorts last so that a run stopping at the first failure has
+already run every other test.
 """
 import numpy as np
 import pytest
@@ -28,8 +30,8 @@ def env():
     ctx.close()
 
 
-@pytest.mark.parametrize("k,precision,rtol", [(700, 0, 1e-5), (257, 1, 1e-12)])
-def test_noalloc_matches_context_solve_twice(env, k, precision, rtol):
+@pytest.mark.parametrize("k,precision,rtol,rtol_oracle", [(700, 0, 1e-5, 1e-2), (257, 1, 1e-12, 1e-9)])
+def test_noalloc_matches_context_solve_twice(env, oracle_mod, k, precision, rtol, rtol_oracle):
     ts, ctx, torch = env
     dt = torch.float32 if precision == ts.MIXED else torch.float64
     rng = np.random.default_rng(k)
@@ -38,6 +40,7 @@ def test_noalloc_matches_context_solve_twice(env, k, precision, rtol):
     S = torch.as_tensor(s.T.copy(), dtype=dt, device="cuda")
     st, info = ctx.cholesky(S, k, k, precision=precision)
     assert st == ts.OK and info == 0
+    L_ref = oracle_mod.cholesky(s)
     for call in range(2):
         rhs = rng.standard_normal(k)
         want = torch.as_tensor(rhs, dtype=dt, device="cuda")
@@ -47,6 +50,8 @@ def test_noalloc_matches_context_solve_twice(env, k, precision, rtol):
         w = want.cpu().numpy().astype(np.float64)
         g = got.cpu().numpy().astype(np.float64)
         assert np.linalg.norm(g - w) <= rtol * np.linalg.norm(w), call
+        x_ref = oracle_mod.cholesky_solve(L_ref, rhs)
+        assert np.linalg.norm(g - x_ref) <= rtol_oracle * np.linalg.norm(x_ref), call
 
 
 def test_noalloc_rejects_oversized_k(env):
