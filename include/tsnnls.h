@@ -177,12 +177,43 @@ int tsnnls_submit(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double 
                   const tsnnls_opts *opts, tsnnls_ticket *ticket);
 
 /* TSNNLS_PENDING while the ticket runs; otherwise its final status (and the
- * ticket is released; polling it again gives TSNNLS_EINVAL). */
+ * ticket is released; polling it again gives TSNNLS_EINVAL).  Also takes the
+ * tickets of tsnnls_submit_batch (below). */
 int tsnnls_poll(tsnnls_ctx *ctx, tsnnls_ticket ticket, tsnnls_info *info);
 
 /* Wait up to timeout_us microseconds (< 0: no limit).  Returns
  * TSNNLS_PENDING if the time ran out, else as tsnnls_poll. */
 int tsnnls_wait(tsnnls_ctx *ctx, tsnnls_ticket ticket, int64_t timeout_us, tsnnls_info *info);
+
+/* Asynchronous batch of independent solves under one ticket (Section 1 sets
+ * the method inside a larger application that has many such problems).
+ * Problem i is A[i] (an array of `count` CSR descriptors, each with its own
+ * on_device), right-hand side b[i] and output x_out[i] (host arrays of
+ * `count` pointers, each in the memory space its A[i].on_device names).
+ * Every member is checked first (as for tsnnls_submit); if any is invalid
+ * (TSNNLS_EINVAL) or can never fit the context's budget (TSNNLS_EADMIT),
+ * nothing is queued.  Otherwise the call returns at once with *ticket; each
+ * member is then admitted by its own device footprint and runs beside the
+ * other members and the context's other requests (continuous batching).
+ * The arrays of descriptors and pointers are copied; the matrices, b[i] and
+ * x_out[i] must stay valid and unmodified until the ticket completes.
+ * tsnnls_poll / tsnnls_wait on the ticket return TSNNLS_PENDING until every
+ * member has finished, then the first failing member's status (in
+ * submission order) or TSNNLS_OK, and release the ticket; their info sums
+ * the members' pivots, refinement steps, |F|, device times, launches,
+ * fallbacks and reuses, and takes the largest last_rel_step, cond_est,
+ * kkt_viol and rel_resid_change.  x_out[i] is written only if member i
+ * succeeded. */
+int tsnnls_submit_batch(tsnnls_ctx *ctx, int32_t count, const tsnnls_csr *A, const double *const *b,
+                        double *const *x_out, const tsnnls_opts *opts, tsnnls_ticket *ticket);
+
+/* Status and info of member i (0-based, submission order) of a batch ticket
+ * that has not been released yet: TSNNLS_PENDING while the member runs,
+ * else its own final status (info filled).  Does not release anything, so
+ * members' results can be collected as they finish, before tsnnls_poll /
+ * tsnnls_wait releases the ticket.  TSNNLS_EINVAL for an unknown ticket or i
+ * out of range. */
+int tsnnls_batch_member_info(tsnnls_ctx *ctx, tsnnls_ticket ticket, int32_t i, tsnnls_info *info);
 
 /* Counters of the asynchronous queue since the context was created. */
 typedef struct {

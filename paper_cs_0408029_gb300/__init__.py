@@ -27,7 +27,8 @@ EXPORTS = (
     "tsnnls_solve_batch_dense", "tsnnls_gram", "tsnnls_gather", "tsnnls_cholesky",
     "tsnnls_chol_solve", "tsnnls_spmv", "tsnnls_profile_enable", "tsnnls_profile_read",
     "tsnnls_chol_solve_noalloc", "tsnnls_batch_autotune", "tsnnls_batch_set_panel",
-    "tsnnls_queue_stats_read", "tsnnls_wait_probe",
+    "tsnnls_queue_stats_read", "tsnnls_wait_probe", "tsnnls_submit_batch",
+    "tsnnls_batch_member_info",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
@@ -114,6 +115,9 @@ def load(build_if_missing: bool = True):
         "tsnnls_batch_autotune": ([p, i32, i32, p], ctypes.c_int),
         "tsnnls_batch_set_panel": ([i32, p], ctypes.c_int),
         "tsnnls_queue_stats_read": ([p, p], ctypes.c_int),
+        "tsnnls_submit_batch": ([p, i32, p, p, p, ctypes.POINTER(Opts), ctypes.POINTER(i64)],
+                                ctypes.c_int),
+        "tsnnls_batch_member_info": ([p, i64, i32, ctypes.POINTER(Info)], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -293,6 +297,27 @@ class Context:
                                        ctypes.byref(t)), "submit")
         self._inflight[t.value] = (A, b, x_out)
         return t.value
+
+    def submit_batch(self, As, bs, xs, opts=None, **kw):
+        """One ticket for len(As) independent solves (HostCSR with numpy b / x,
+        or DeviceCSR with CUDA tensors, per member)."""
+        o = opts if opts is not None else default_opts(**kw)
+        cnt = len(As)
+        arr = (CSR * cnt)(*[a.struct() for a in As])
+        bp = np.array([b.ctypes.data if isinstance(b, np.ndarray) else b.data_ptr() for b in bs],
+                      dtype=np.uint64)
+        xp = np.array([x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr() for x in xs],
+                      dtype=np.uint64)
+        t = ctypes.c_int64()
+        _check(self._lib.tsnnls_submit_batch(self._h, cnt, ctypes.cast(arr, ctypes.c_void_p), _np_ptr(bp),
+                                             _np_ptr(xp), ctypes.byref(o), ctypes.byref(t)), "submit_batch")
+        self._inflight[t.value] = (As, bs, xs, arr)
+        return t.value
+
+    def batch_member_info(self, ticket, i):
+        info = Info()
+        st = self._lib.tsnnls_batch_member_info(self._h, ticket, int(i), ctypes.byref(info))
+        return st, info
 
     def poll(self, ticket):
         info = Info()

@@ -239,6 +239,56 @@ int tsnnls_submit(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double 
     return TSNNLS_OK;
 }
 
+int tsnnls_submit_batch(tsnnls_ctx *ctx, int32_t count, const tsnnls_csr *A, const double *const *b,
+                        double *const *x_out, const tsnnls_opts *opts, tsnnls_ticket *ticket) {
+    if (!ctx || !ticket || count <= 0 || !A || !b || !x_out) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    const tsnnls_opts o = resolve_opts(opts);
+    // all members are checked before any is queued: a batch is accepted whole or not at all
+    std::vector<std::shared_ptr<Request>> reqs((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        int st = check_csr_args(&A[i], b[i], x_out[i]);
+        if (st != TSNNLS_OK) return st;
+        auto req = std::make_shared<Request>();
+        req->A = A[i];
+        req->b = b[i];
+        req->x_out = x_out[i];
+        req->opts = o;
+        req->footprint = solve_footprint(A[i], o, c.budget);
+        if (req->footprint > c.budget) return TSNNLS_EADMIT;
+        reqs[(size_t)i] = std::move(req);
+    }
+    std::lock_guard<std::mutex> g(c.q_mu);
+    int st = ensure_workers(ctx);
+    if (st != TSNNLS_OK) return st;
+    std::vector<tsnnls_ticket> members;
+    members.reserve((size_t)count);
+    for (auto &req : reqs) {
+        const tsnnls_ticket t = c.next_ticket++;
+        c.requests[t] = req;
+        c.waiting.push_back(t);
+        members.push_back(t);
+    }
+    const tsnnls_ticket bt = c.next_ticket++;
+    c.batches[bt] = std::move(members);
+    c.submitted += count;
+    *ticket = bt;
+    c.q_cv.notify_all();
+    return TSNNLS_OK;
+}
+
+int tsnnls_batch_member_info(tsnnls_ctx *ctx, tsnnls_ticket t, int32_t i, tsnnls_info *info) {
+    if (!ctx) return TSNNLS_EINVAL;
+    Context &c = ctx->c;
+    std::lock_guard<std::mutex> g(c.q_mu);
+    auto it = c.batches.find(t);
+    if (it == c.batches.end() || i < 0 || (size_t)i >= it->second.size()) return TSNNLS_EINVAL;
+    const auto &req = c.requests[it->second[(size_t)i]];
+    if (!req->done) return TSNNLS_PENDING;
+    if (info) *info = req->info;
+    return req->status;
+}
+
 int tsnnls_queue_stats_read(tsnnls_ctx *ctx, tsnnls_queue_stats *out) {
     if (!ctx || !out) return TSNNLS_EINVAL;
     Context &c = ctx->c;
@@ -252,10 +302,63 @@ int tsnnls_queue_stats_read(tsnnls_ctx *ctx, tsnnls_queue_stats *out) {
     return TSNNLS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Caller holds q_mu.  True once every member of batch `members` has finished.
+bool batch_done(Context &c, const std::vector<tsnnls_ticket> &members) {
+    for (tsnnls_ticket m : members)
+        if (!c.requests[m]->done) return false;
+    return true;
+}
+
+// Caller holds q_mu; every member has finished.  The batch's status is the
+// first failing member's (in submission order), else OK; info sums the
+// members' counts and device times and takes the worst quality figures.
+int batch_release(Context &c, tsnnls_ticket t, tsnnls_info *info) {
+    auto it = c.batches.find(t);
+    int st = TSNNLS_OK;
+    tsnnls_info agg;
+    std::memset(&agg, 0, sizeof(agg));
+    for (tsnnls_ticket m : it->second) {
+        const auto &r = c.requests[m];
+        if (st == TSNNLS_OK && r->status != TSNNLS_OK) st = r->status;
+        const tsnnls_info &v = r->info;
+        agg.iters += v.iters;
+        agg.refine_steps += v.refine_steps;
+        agg.nF += v.nF;
+        agg.path_used = agg.path_used ? agg.path_used : v.path_used;
+        agg.precision_used = std::max(agg.precision_used, v.precision_used);
+        agg.last_rel_step = std::max(agg.last_rel_step, v.last_rel_step);
+        agg.time_ms += v.time_ms;
+        agg.kernel_launches += v.kernel_launches;
+        agg.cond_est = std::max(agg.cond_est, v.cond_est);
+        agg.fallback_used += v.fallback_used;
+        agg.factor_reuses += v.factor_reuses;
+        agg.kkt_viol = std::max(agg.kkt_viol, v.kkt_viol);
+        agg.rel_resid_change = std::max(agg.rel_resid_change, v.rel_resid_change);
+        c.requests.erase(m);
+    }
+    c.batches.erase(it);
+    agg.status = st;
+    if (info) *info = agg;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
 int tsnnls_poll(tsnnls_ctx *ctx, tsnnls_ticket t, tsnnls_info *info) {
     if (!ctx) return TSNNLS_EINVAL;
     Context &c = ctx->c;
     std::lock_guard<std::mutex> g(c.q_mu);
+    auto bit = c.batches.find(t);
+    if (bit != c.batches.end()) {
+        if (!batch_done(c, bit->second)) return TSNNLS_PENDING;
+        return batch_release(c, t, info);
+    }
     auto it = c.requests.find(t);
     if (it == c.requests.end()) return TSNNLS_EINVAL;
     if (!it->second->done) return TSNNLS_PENDING;
@@ -269,6 +372,17 @@ int tsnnls_wait(tsnnls_ctx *ctx, tsnnls_ticket t, int64_t timeout_us, tsnnls_inf
     if (!ctx) return TSNNLS_EINVAL;
     Context &c = ctx->c;
     std::unique_lock<std::mutex> lk(c.q_mu);
+    auto bit = c.batches.find(t);
+    if (bit != c.batches.end()) {
+        const std::vector<tsnnls_ticket> members = bit->second;
+        auto all_done = [&] { return batch_done(c, members); };
+        if (timeout_us < 0) {
+            c.done_cv.wait(lk, all_done);
+        } else if (!c.done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), all_done)) {
+            return TSNNLS_PENDING;
+        }
+        return batch_release(c, t, info);
+    }
     auto it = c.requests.find(t);
     if (it == c.requests.end()) return TSNNLS_EINVAL;
     auto req = it->second;

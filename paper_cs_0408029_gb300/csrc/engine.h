@@ -90,6 +90,9 @@ struct Context {
     std::condition_variable q_cv, done_cv;
     std::deque<tsnnls_ticket> waiting;
     std::map<tsnnls_ticket, std::shared_ptr<Request>> requests;
+    // tsnnls_submit_batch: batch ticket -> the member tickets (each an
+    // ordinary queued request that only the batch ticket refers to)
+    std::map<tsnnls_ticket, std::vector<tsnnls_ticket>> batches;
     tsnnls_ticket next_ticket = 1;
     std::vector<std::thread> workers;
     std::vector<Lane> lanes;

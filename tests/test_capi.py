@@ -47,6 +47,8 @@ def test_null_arguments_rejected_without_device(lib):
     # argument checks happen before any CUDA call
     assert lib.tsnnls_solve(None, None, None, None, None, None) == ts.EINVAL
     assert lib.tsnnls_submit(None, None, None, None, None, None) == ts.EINVAL
+    assert lib.tsnnls_submit_batch(None, 0, None, None, None, None, None) == ts.EINVAL
+    assert lib.tsnnls_batch_member_info(None, 1, 0, None) == ts.EINVAL
     assert lib.tsnnls_poll(None, 1, None) == ts.EINVAL
     assert lib.tsnnls_ctx_create(None, 0, 0) == ts.EINVAL
 
