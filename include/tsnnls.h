@@ -65,6 +65,9 @@ extern "C" {
 #define TSNNLS_PATH_AUTO 0    /* factor when A^T A fits the budget, LSQR otherwise */
 #define TSNNLS_PATH_FACTOR 1  /* normal equations on the cached A^T A (Sections 2-3) */
 #define TSNNLS_PATH_LSQR 2    /* LSQR on A_F for each pivot (Section 3's LSQR, no A^T A) */
+#define TSNNLS_PATH_SPARSE 3  /* normal equations with A^T A kept sparse and a supernodal sparse Cholesky
+                                 of its F x F block per pivot (Section 3: the paper's TAUCS factor);
+                                 for Grams with a small-separator pattern.  AUTO never picks it */
 
 /* A sparse matrix in CSR form.  row_ptr has m+1 entries, row_ptr[0] == 0 and
  * row_ptr[m] == nnz; col_idx and val have nnz entries.  on_device selects
@@ -108,7 +111,7 @@ typedef struct {
     int32_t iters;           /* pivots performed (exchange + solve) */
     int32_t refine_steps;    /* total refinement steps over all pivots */
     int32_t nF;              /* |F| at the solution */
-    int32_t path_used;       /* TSNNLS_PATH_FACTOR or TSNNLS_PATH_LSQR */
+    int32_t path_used;       /* TSNNLS_PATH_FACTOR, TSNNLS_PATH_LSQR or TSNNLS_PATH_SPARSE */
     int32_t precision_used;  /* TSNNLS_MIXED or TSNNLS_FP64 */
     double last_rel_step;    /* ||dx_F||_inf / ||x_F||_inf of the last refinement step */
     double time_ms;          /* device time of the solve, CUDA events */
@@ -372,6 +375,28 @@ int tsnnls_chol_solve_noalloc(int32_t precision, const void *L, int64_t k, int64
  * device buffers (cudaMalloc / cudaFree may synchronise the device). */
 #define TSNNLS_WAIT_PROBE_MAX_POLLS 4194304
 int tsnnls_wait_probe(int64_t polls);
+
+/* Symbolic analysis of the sparse normal-equations factor of
+ * TSNNLS_PATH_SPARSE, on the host only (no GPU, no context): the pattern of
+ * A^T A from the pattern of A (host CSR: row_ptr m + 1 entries, col_idx
+ * row_ptr[m] entries), a nested-dissection order, the elimination tree of
+ * the reordered matrix in postorder, the row structure of L and its
+ * supernodes of at most max_width columns (Section 3: the structure TAUCS
+ * computes before its numeric factorisation).  perm_out (n entries, may be
+ * NULL) receives the order (position -> original column); parent_out (n, may
+ * be NULL) the elimination tree in positions (-1 at a root); stats (may be
+ * NULL) the sizes below.  TSNNLS_EINVAL for a malformed pattern. */
+typedef struct {
+    int64_t n;             /* columns */
+    int64_t nnz_gram;      /* entries of the lower triangle of A^T A's pattern, diagonal included */
+    int64_t nnz_l;         /* entries of L's structure (lower triangle, diagonal included) */
+    int64_t supernodes;
+    int64_t max_height;    /* rows of the tallest supernode */
+    double factor_flops;   /* sum over the columns of L of (entries in the column)^2 */
+    double analysis_ms;    /* host wall time */
+} tsnnls_sparse_stats;
+int tsnnls_sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t max_width,
+                          int32_t *perm_out, int32_t *parent_out, tsnnls_sparse_stats *stats);
 
 /* Sparse products in FP64 on a device CSR matrix:
  *   trans == 0:  out = alpha * A x + beta * z   (x: n entries, out, z: m)

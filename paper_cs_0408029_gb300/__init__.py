@@ -17,7 +17,7 @@ from . import build as _build_mod
 
 OK, EINVAL, ENOMEM, EADMIT, ENOTPD, EMAXITER, ENOCONV, ETIMEOUT, PENDING, ECUDA, ENODEV = range(11)
 MIXED, FP64 = 0, 1
-PATH_AUTO, PATH_FACTOR, PATH_LSQR = 0, 1, 2
+PATH_AUTO, PATH_FACTOR, PATH_LSQR, PATH_SPARSE = 0, 1, 2, 3
 WAIT_PROBE_MAX_POLLS = 1 << 22  # TSNNLS_WAIT_PROBE_MAX_POLLS
 
 # every entry point declared in include/tsnnls.h
@@ -28,7 +28,7 @@ EXPORTS = (
     "tsnnls_chol_solve", "tsnnls_spmv", "tsnnls_profile_enable", "tsnnls_profile_read",
     "tsnnls_chol_solve_noalloc", "tsnnls_batch_autotune", "tsnnls_batch_set_panel",
     "tsnnls_queue_stats_read", "tsnnls_wait_probe", "tsnnls_submit_batch",
-    "tsnnls_batch_member_info",
+    "tsnnls_batch_member_info", "tsnnls_sparse_analyze",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
@@ -67,6 +67,12 @@ class Info(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SparseStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz_gram", ctypes.c_int64), ("nnz_l", ctypes.c_int64),
+                ("supernodes", ctypes.c_int64), ("max_height", ctypes.c_int64),
+                ("factor_flops", ctypes.c_double), ("analysis_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -118,6 +124,7 @@ def load(build_if_missing: bool = True):
         "tsnnls_submit_batch": ([p, i32, p, p, p, ctypes.POINTER(Opts), ctypes.POINTER(i64)],
                                 ctypes.c_int),
         "tsnnls_batch_member_info": ([p, i64, i32, ctypes.POINTER(Info)], ctypes.c_int),
+        "tsnnls_sparse_analyze": ([i64, i64, p, p, i32, p, p, ctypes.POINTER(SparseStats)], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -146,9 +153,21 @@ def default_opts(**kw) -> Opts:
         if k == "precision" and isinstance(v, str):
             v = {"mixed": MIXED, "fp64": FP64}[v]
         if k == "path" and isinstance(v, str):
-            v = {"auto": PATH_AUTO, "factor": PATH_FACTOR, "lsqr": PATH_LSQR}[v]
+            v = {"auto": PATH_AUTO, "factor": PATH_FACTOR, "lsqr": PATH_LSQR, "sparse": PATH_SPARSE}[v]
         setattr(o, k, v)
     return o
+
+
+def sparse_analyze(m, n, row_ptr, col_idx, max_width=64):
+    """Host-only symbolic analysis of the sparse path: (perm, parent, stats dict)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    perm = np.empty(n, dtype=np.int32)
+    parent = np.empty(n, dtype=np.int32)
+    st = SparseStats()
+    _check(load().tsnnls_sparse_analyze(int(m), int(n), _np_ptr(rp), _np_ptr(ci), int(max_width), _np_ptr(perm),
+                                        _np_ptr(parent), ctypes.byref(st)), "sparse_analyze")
+    return perm, parent, {f: getattr(st, f) for f, _ in st._fields_}
 
 
 def wait_probe(polls: int) -> int:

@@ -1,8 +1,9 @@
 """Build libtsnnls.so (the CUDA library behind include/tsnnls.h) in-tree.
 
-Every .cu file under csrc/ is compiled for sm_103a in parallel with nvcc and
-linked into ``_build/libtsnnls.so``; the CUDA runtime is linked statically so
-the library has no dependency beyond the NVIDIA kernel-mode driver.
+Every .cu file under csrc/ is compiled for sm_103a with nvcc and every .cpp
+file (host-only code) with the host C++ compiler, all in parallel, and linked
+into ``_build/libtsnnls.so``; the CUDA runtime is linked statically so the
+library has no dependency beyond the NVIDIA kernel-mode driver.
 """
 from __future__ import annotations
 
@@ -30,7 +31,11 @@ def _nvcc() -> str:
 
 
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+
+
+def _cxx() -> str:
+    return shutil.which("g++") or shutil.which("c++") or "g++"
 
 
 def _headers():
@@ -53,9 +58,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(OUT_DIR, os.path.splitext(os.path.basename(src))[0] + ".o")
         objs.append(obj)
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+        if src.endswith(".cpp"):
+            cmd = [_cxx(), "-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + os.path.join(ROOT, "include"),
+                   "-I" + CSRC, "-c", src, "-o", obj]
+        else:
+            cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -71,7 +71,9 @@ void worker_loop(tsnnls_ctx *ctx, int lane_id) {
         c.max_in_use = std::max(c.max_in_use, c.in_use);
         lk.unlock();
         tsnnls_info info;
-        int st = solve_on_lane(c, lane, req->A, req->b, req->x_out, req->opts, &info, nullptr);
+        SolveExtras ex;
+        ex.sym = req->sym;
+        int st = solve_on_lane(c, lane, req->A, req->b, req->x_out, req->opts, &info, &ex);
         lk.lock();
         c.in_use -= req->footprint;
         c.active -= 1;
@@ -202,11 +204,13 @@ int tsnnls_solve_ex(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, doubl
     Context &c = ctx->c;
     std::lock_guard<std::mutex> g(c.solve_mu);
     cudaSetDevice(c.device);
-    if (solve_footprint(*A, o, c.budget) > c.budget) {
+    std::shared_ptr<const SparseSym> sym;
+    if (solve_footprint(*A, o, c.budget, &sym) > c.budget) {
         if (info) info->status = TSNNLS_EADMIT;
         return TSNNLS_EADMIT;
     }
     SolveExtras ex;
+    ex.sym = sym;
     ex.y_out = y_out;
     ex.inF_out = inF_out;
     ex.trace = trace;
@@ -225,7 +229,7 @@ int tsnnls_submit(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, double 
     req->b = b;
     req->x_out = x_out;
     req->opts = resolve_opts(opts);
-    req->footprint = solve_footprint(*A, req->opts, c.budget);
+    req->footprint = solve_footprint(*A, req->opts, c.budget, &req->sym);
     if (req->footprint > c.budget) return TSNNLS_EADMIT;
     std::lock_guard<std::mutex> g(c.q_mu);
     st = ensure_workers(ctx);
@@ -254,7 +258,7 @@ int tsnnls_submit_batch(tsnnls_ctx *ctx, int32_t count, const tsnnls_csr *A, con
         req->b = b[i];
         req->x_out = x_out[i];
         req->opts = o;
-        req->footprint = solve_footprint(A[i], o, c.budget);
+        req->footprint = solve_footprint(A[i], o, c.budget, &req->sym);
         if (req->footprint > c.budget) return TSNNLS_EADMIT;
         reqs[(size_t)i] = std::move(req);
     }
@@ -287,6 +291,27 @@ int tsnnls_batch_member_info(tsnnls_ctx *ctx, tsnnls_ticket t, int32_t i, tsnnls
     if (!req->done) return TSNNLS_PENDING;
     if (info) *info = req->info;
     return req->status;
+}
+
+int tsnnls_sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t max_width,
+                          int32_t *perm_out, int32_t *parent_out, tsnnls_sparse_stats *stats) {
+    if (m <= 0 || n <= 0 || n > INT32_MAX || !row_ptr || max_width < 1) return TSNNLS_EINVAL;
+    tsnnls_csr A{m, n, row_ptr[m], row_ptr, col_idx, nullptr, 0};
+    if (A.nnz > 0 && !col_idx) return TSNNLS_EINVAL;
+    auto S = analyze_gram_pattern(A, max_width);
+    if (!S) return TSNNLS_EINVAL;
+    if (perm_out) std::memcpy(perm_out, S->perm.data(), sizeof(int32_t) * (size_t)n);
+    if (parent_out) std::memcpy(parent_out, S->parent.data(), sizeof(int32_t) * (size_t)n);
+    if (stats) {
+        stats->n = n;
+        stats->nnz_gram = (int64_t)S->grow.size();
+        stats->nnz_l = S->nnz_L;
+        stats->supernodes = S->ns;
+        stats->max_height = S->max_height;
+        stats->factor_flops = S->flops;
+        stats->analysis_ms = S->analysis_ms;
+    }
+    return TSNNLS_OK;
 }
 
 int tsnnls_queue_stats_read(tsnnls_ctx *ctx, tsnnls_queue_stats *out) {

@@ -15,10 +15,13 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "engine.h"
+#include "sparse_chol.h"
 
 namespace tsnnls {
 
@@ -143,10 +146,13 @@ struct Carve {
     }
 };
 
+// sparse_bytes > 0: the sparse path, whose factor state (sparse_bytes) replaces
+// the dense G and S, the reuse buffers and the tensor-core panels.
 template <typename T>
-size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
+size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in, size_t sparse_bytes = 0) {
     Carve c;
-    const int64_t ldg = round_up(n, 32);
+    const bool sparse = sparse_bytes > 0;
+    const int64_t ldg = sparse ? 0 : round_up(n, 32);
     if (host_in) {
         c.take<int64_t>(m + 1);
         c.take<int32_t>(nnz);
@@ -165,9 +171,13 @@ size_t layout_bytes(int64_t m, int64_t n, int64_t nnz, bool host_in) {
     c.take<T>(n);                                   // rhs
     c.take<uint8_t>(n);
     c.take<int32_t>(n);
+    c.take<char>(quality_scratch_bytes(m, n));
+    if (sparse) {
+        c.take<char>(sparse_bytes);
+        return c.off + 256;
+    }
     c.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
     c.take<char>(border_bytes(n, sizeof(T)));  // reuse of a factor across pivots
-    c.take<char>(quality_scratch_bytes(m, n));
     if (sizeof(T) == 4) {
         c.take<float>((size_t)n * 128);  // K-major hi / lo panel copies for the tensor-core update
         c.take<float>((size_t)n * 128);
@@ -226,7 +236,21 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
     // refinement with FP64 residuals: always on the FP32 factor; on the FP64
     // factor only when redoing a MIXED solve whose FP32 refinement stagnated
     const bool mixed = o.precision == TSNNLS_MIXED || force_refine;
-    const int64_t ldg = round_up(n, 32);
+    // the sparse path (supernodal factor of the permuted G_FF, sparse_chol.cu)
+    // replaces the dense G, the gather and the dense factor; the rest of the
+    // pivot loop is the same
+    const bool sparse = o.path == TSNNLS_PATH_SPARSE;
+    std::shared_ptr<const SparseSym> sym;
+    double analysis_ms = 0.0;
+    if (sparse) {
+        sym = ex ? ex->sym : nullptr;
+        if (!sym) sym = analyze_gram_pattern(A, kSpNB);
+        if (!sym) return TSNNLS_EINVAL;
+        analysis_ms = sym->analysis_ms;
+    }
+    const size_t sparse_bytes = sparse ? SparseChol<T>::device_bytes(*sym, std::max(1, num_sms())) : 0;
+    SparseChol<T> sc;
+    const int64_t ldg = sparse ? 0 : round_up(n, 32);
     const int32_t max_iter = o.max_iter > 0 ? o.max_iter : (int32_t)std::min<int64_t>(10 * n + 100, INT32_MAX);
     cudaStream_t s = lane.stream;
     Sync sync{lane};
@@ -238,7 +262,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
     const int64_t launch0 = launches_so_far();
 
     Carve cv;
-    const size_t bytes = layout_bytes<T>(m, n, nnz, host_in);
+    const size_t bytes = layout_bytes<T>(m, n, nnz, host_in, sparse_bytes);
     void *block = nullptr;
     {
         cudaError_t e = cudaMallocAsync(&block, bytes, s);
@@ -287,11 +311,13 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         T *rhs = cv.take<T>(n);
         uint8_t *inF = cv.take<uint8_t>(n);
         int32_t *F = cv.take<int32_t>(n);
-        void *trsv_scratch = cv.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
-        const BorderBuffers bb = border_carve(cv.take<char>(border_bytes(n, sizeof(T))), n, sizeof(T));
         void *qscratch = cv.take<char>(quality_scratch_bytes(m, n));
+        void *sparse_mem = sparse ? cv.take<char>(sparse_bytes) : nullptr;
+        void *trsv_scratch = sparse ? nullptr : cv.take<char>(chol_solve_scratch_bytes(n, sizeof(T)));
+        const BorderBuffers bb =
+            sparse ? BorderBuffers{} : border_carve(cv.take<char>(border_bytes(n, sizeof(T))), n, sizeof(T));
         TcPanel tc;
-        if (sizeof(T) == 4) {
+        if (sizeof(T) == 4 && !sparse) {
             float *xhi = cv.take<float>((size_t)n * 128);
             float *xlo = cv.take<float>((size_t)n * 128);
             tc_panel_init(tc, xhi, xlo, n);
@@ -324,8 +350,15 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             prof_end(lane, csr_bytes + csc_bytes + 8.0 * (2.0 * m + n), 2.0 * nnz);
         }
         prof_begin(lane, TSNNLS_PHASE_GRAM);
-        TRY_CUDA(launch_gram<T>(s, m, n, row_ptr, col, val, col_ptr, row_idx, cval, bd, G, ldg, c));
-        prof_end(lane, csr_bytes + csc_bytes + 0.5 * (double)n * (n + 1) * sizeof(T) + 8.0 * (m + n), 0.0);
+        if (sparse) {
+            // c = A^T b, and A^T A on the analysed pattern (FP64)
+            TRY_CUDA(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, bd, 0.0, nullptr, c, avg_col));
+            TRY_CUDA(sc.setup(*sym, sparse_mem, s, col_ptr, row_idx, cval));
+            prof_end(lane, csc_bytes + 8.0 * (m + n) + 16.0 * (double)sym->grow.size(), 0.0);
+        } else {
+            TRY_CUDA(launch_gram<T>(s, m, n, row_ptr, col, val, col_ptr, row_idx, cval, bd, G, ldg, c));
+            prof_end(lane, csr_bytes + csc_bytes + 0.5 * (double)n * (n + 1) * sizeof(T) + 8.0 * (m + n), 0.0);
+        }
         // F = {}, G = all, x = 0, y = -A^T b, p = p_max, N = infinity
         prof_begin(lane, TSNNLS_PHASE_VECTOR);
         TRY_CUDA(launch_init_state(s, n, c, x, y, inF, o.p_max, lane.st_dev));
@@ -348,9 +381,12 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         int64_t kb = 0, ldsb = 32;
         int ba = 0, br = 0;
         int reuses = 0;
-        auto sol_list = [&]() -> const int32_t * { return reuse ? bb.Ul : F; };
-        auto sol_len = [&]() -> int64_t { return reuse ? kb + ba : k; };
+        // sparse: the solves run on all n entries in the factor's order, the
+        // list giving each position's variable (-1 outside F: held at zero)
+        auto sol_list = [&]() -> const int32_t * { return sparse ? sc.permF : (reuse ? bb.Ul : F); };
+        auto sol_len = [&]() -> int64_t { return sparse ? n : (reuse ? kb + ba : k); };
         auto pivot_solve = [&](T *v) -> cudaError_t {
+            if (sparse) return sc.solve(s, v, lane.st_dev);
             return reuse ? launch_border_solve<T>(s, S, kb, ldsb, ba, br, bb, v, trsv_scratch, lane.st_dev)
                          : launch_chol_solve<T>(s, S, k, lds, v, trsv_scratch, lane.st_dev);
         };
@@ -362,7 +398,8 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             *settled = false;
             for (;;) {
                 const int64_t kl = reuse ? kb : k;
-                const double tri = 0.5 * (double)kl * (double)(kl + 1) * sizeof(T);
+                const double tri = sparse ? (double)sym->nnz_L * sizeof(T)
+                                          : 0.5 * (double)kl * (double)(kl + 1) * sizeof(T);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
                 cudaError_t e = launch_gather_rhs<T>(s, sv, sol_list(), sol_len(), rhs);
                 prof_end(lane, (12.0 + sizeof(T)) * sol_len(), 0.0);
@@ -449,7 +486,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             // does, so does the FP64 redo of a failed MIXED solve, and the
             // condition estimate wants the factor of the last F itself).
             reuse = false;
-            if (sizeof(T) == 4 && mixed && base_valid && k > 0 && o.cond_est == 0 && o.no_reuse == 0 &&
+            if (!sparse && sizeof(T) == 4 && mixed && base_valid && k > 0 && o.cond_est == 0 && o.no_reuse == 0 &&
                 st.border_a <= kBorderMax && st.border_r <= kBorderMax && kb >= kReuseMinK) {
                 ba = st.border_a;
                 br = st.border_r;
@@ -463,9 +500,16 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 reuse = bad == 0;
                 if (reuse) ++reuses;
             }
+            if (k > 0 && sparse) {
+                prof_begin(lane, TSNNLS_PHASE_FACTOR);
+                TRY_CUDA(sc.factor(s, inF, lane.st_dev));
+                TRY_CUDA(sc.perm_list(s, inF));
+                prof_end(lane, 2.0 * (double)sym->nnz_L * sizeof(T), sym->flops);
+            }
             if (k > 0) {
-                const double tri = 0.5 * (double)k * (double)(k + 1) * sizeof(T);
-                if (!reuse) {
+                const double tri = sparse ? (double)sym->nnz_L * sizeof(T)
+                                          : 0.5 * (double)k * (double)(k + 1) * sizeof(T);
+                if (!reuse && !sparse) {
                     prof_begin(lane, TSNNLS_PHASE_GATHER);
                     TRY_CUDA(launch_gather<T>(s, G, ldg, F, nullptr, k, S, lds));
                     prof_end(lane, 2.0 * tri + 4.0 * k, 0.0);
@@ -488,7 +532,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 }
                 // first solve: x_F = (L L^T)^{-1} c_F  (x restarts from 0)
                 const int64_t kl = reuse ? kb : k;
-                const double tril = 0.5 * (double)kl * (double)(kl + 1) * sizeof(T);
+                const double tril = sparse ? tri : 0.5 * (double)kl * (double)(kl + 1) * sizeof(T);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
                 TRY_CUDA(launch_gather_rhs<T>(s, c, sol_list(), sol_len(), rhs));
                 prof_end(lane, (12.0 + sizeof(T)) * sol_len(), 0.0);
@@ -539,7 +583,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                                        qscratch, lane.st_dev));
             prof_end(lane, 8.0 * (2.0 * m + 4.0 * n) + (have_delta ? csr_bytes + 16.0 * m : 0.0), 0.0);
         }
-        if (status == TSNNLS_OK && o.cond_est && k > 0) {
+        if (status == TSNNLS_OK && o.cond_est && k > 0 && !sparse) {
             // kappa_1 of the last pivot's (A^T A)_FF: its 1-norm times an
             // estimate of ||(A^T A)_FF^-1||_1 from solves with the factor still
             // in S (Hager's method with Higham's refinements, as in dpocon;
@@ -602,7 +646,9 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 TRY_CUDA(cudaMemcpyAsync(ex->inF_out, inF, (size_t)n, kind, s));
             TRY_CUDA(cudaStreamSynchronize(s));
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, lane.ev0, lane.ev1) == cudaSuccess && info) info->time_ms = ms;
+            // the sparse path's host analysis counts toward the solve's time
+            if (cudaEventElapsedTime(&ms, lane.ev0, lane.ev1) == cudaSuccess && info)
+                info->time_ms = ms + analysis_ms;
         }
         if (info) {
             info->iters = lane.st_host->iters;
@@ -631,7 +677,7 @@ cleanup:
         info->status = status;
         info->refine_steps = refine_total;
         info->last_rel_step = last_rel;
-        info->path_used = TSNNLS_PATH_FACTOR;
+        info->path_used = sparse ? TSNNLS_PATH_SPARSE : TSNNLS_PATH_FACTOR;
         info->precision_used = o.precision;
         info->kernel_launches = launches_so_far() - launch0;
     }
@@ -646,14 +692,61 @@ static size_t factor_footprint(const tsnnls_csr &A, const tsnnls_opts &o) {
                                       : layout_bytes<float>(A.m, A.n, A.nnz, host_in);
 }
 
+std::shared_ptr<const SparseSym> analyze_gram_pattern(const tsnnls_csr &A, int max_width) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    const int64_t *row_ptr = A.row_ptr;
+    const int32_t *col = A.col_idx;
+    if (A.on_device) {
+        rp.resize(A.m + 1);
+        ci.resize(std::max<int64_t>(A.nnz, 1));
+        if (cudaMemcpy(rp.data(), A.row_ptr, sizeof(int64_t) * (A.m + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return nullptr;
+        if (A.nnz > 0 &&
+            cudaMemcpy(ci.data(), A.col_idx, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return nullptr;
+        row_ptr = rp.data();
+        col = ci.data();
+    }
+    // the pattern must be valid before the analysis walks it
+    if (row_ptr[0] != 0 || row_ptr[A.m] != A.nnz) return nullptr;
+    for (int64_t r = 0; r < A.m; ++r) {
+        if (row_ptr[r + 1] < row_ptr[r]) return nullptr;
+        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
+            if (col[e] < 0 || col[e] >= A.n) return nullptr;
+    }
+    auto sym = std::make_shared<SparseSym>();
+    if (sparse_analyze(A.m, A.n, row_ptr, col, max_width, *sym) != 0) return nullptr;
+    sym->analysis_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return sym;
+}
+
+static size_t sparse_footprint(const tsnnls_csr &A, const tsnnls_opts &o, const SparseSym &S) {
+    const bool host_in = A.on_device == 0;
+    const int ctas = std::max(1, num_sms());
+    return o.precision == TSNNLS_FP64
+               ? layout_bytes<double>(A.m, A.n, A.nnz, host_in, SparseChol<double>::device_bytes(S, ctas))
+               : layout_bytes<float>(A.m, A.n, A.nnz, host_in, SparseChol<float>::device_bytes(S, ctas));
+}
+
 int choose_path(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget) {
-    if (o.path == TSNNLS_PATH_FACTOR || o.path == TSNNLS_PATH_LSQR) return o.path;
+    if (o.path == TSNNLS_PATH_FACTOR || o.path == TSNNLS_PATH_LSQR || o.path == TSNNLS_PATH_SPARSE)
+        return o.path;
     return factor_footprint(A, o) <= budget ? TSNNLS_PATH_FACTOR : TSNNLS_PATH_LSQR;
 }
 
-size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget) {
-    return choose_path(A, o, budget) == TSNNLS_PATH_LSQR ? lsqr_footprint(A, o)
-                                                         : factor_footprint(A, o);
+size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget,
+                       std::shared_ptr<const SparseSym> *sym) {
+    const int path = choose_path(A, o, budget);
+    if (path == TSNNLS_PATH_SPARSE) {
+        auto S = analyze_gram_pattern(A, kSpNB);
+        if (!S) return 0;  // malformed pattern: the solve reports TSNNLS_EINVAL
+        if (sym) *sym = S;
+        return sparse_footprint(A, o, *S);
+    }
+    return path == TSNNLS_PATH_LSQR ? lsqr_footprint(A, o) : factor_footprint(A, o);
 }
 
 int solve_on_lane(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sparse_sym.h"
 #include "tsnnls.h"
 
 namespace tsnnls {
@@ -65,6 +66,7 @@ struct Request {
     int status = TSNNLS_PENDING;
     tsnnls_info info{};
     bool done = false;
+    std::shared_ptr<const SparseSym> sym;  // sparse path: the analysis made at submission
 };
 
 // Columns of a pivot-trace row (tsnnls_solve_ex).
@@ -76,6 +78,7 @@ struct SolveExtras {
     uint8_t *inF_out = nullptr;    // n entries, same memory space as x_out
     int64_t *trace = nullptr;      // host, kTraceCols per pivot
     int64_t trace_cap = 0;
+    std::shared_ptr<const SparseSym> sym;  // sparse path: an analysis already made, else NULL
 };
 
 struct Context {
@@ -108,7 +111,13 @@ void lane_destroy(Lane &l);
 
 // Device footprint (bytes) of one solve at this size on the path AUTO would
 // take under `budget` (the factor path when its cached A^T A fits, else LSQR).
-size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget);
+// sym (may be NULL) receives the sparse path's symbolic analysis when that
+// path is taken (it is needed to size the path's device state).
+size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget,
+                       std::shared_ptr<const SparseSym> *sym = nullptr);
+// Symbolic analysis of A^T A for the sparse path (the pattern is copied to
+// the host first when A is on the device); NULL on failure.
+std::shared_ptr<const SparseSym> analyze_gram_pattern(const tsnnls_csr &A, int max_width);
 int choose_path(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget);
 size_t lsqr_footprint(const tsnnls_csr &A, const tsnnls_opts &o);
 int solve_lsqr(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,

@@ -1,0 +1,61 @@
+// Supernodal sparse Cholesky on the GPU (sparse_chol.cu): device copy of the
+// symbolic structure and the per-pivot factor and solves.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "sparse_sym.h"
+
+namespace tsnnls {
+
+// Device view of a SparseSym (pointers into one allocation).
+struct SpDev {
+    int64_t n, ns;
+    const int32_t *sn_first;
+    const int64_t *rows_off;
+    const int32_t *rows;
+    const int64_t *L_off, *W_off, *d_off, *a_off;
+    const int32_t *dlist, *alist;
+    const int32_t *perm;
+    const int64_t *gptr;
+    const int32_t *grow_orig, *gcol_orig;
+    const int64_t *gpos;
+    double *gval;        // A^T A on its lower pattern (FP64)
+    int32_t *map;        // per CTA of the factor: row -> panel row, n entries each
+    int32_t *flags;      // per supernode: done
+    int32_t *ticket;     // ticket counter, then the abort flag
+    int32_t *abort;
+};
+
+// Widest supernode, for both precisions (the FP64 redo of a mixed solve
+// reuses the same analysis): the dense block size of the factor kernel.
+constexpr int kSpNB = 64;
+
+template <typename T>
+struct SparseChol {
+    SpDev D{};
+    T *Lmem = nullptr;      // panels
+    T *Wmem = nullptr;      // inverses of the diagonal blocks
+    int32_t *permF = nullptr;  // per position of the order: its variable if in F, else -1
+    T *vec = nullptr;       // n entries of scratch in the factor's type
+    int ctas = 1;
+
+    static int nb();  // widest supernode: the dense block size of the factor
+    // device bytes for S (one allocation, 256-byte aligned pieces)
+    static size_t device_bytes(const SparseSym &S, int ctas);
+    // copy the structure into mem and compute A^T A on its pattern from the
+    // CSC copy of A (rows ascending); waits for the copies
+    cudaError_t setup(const SparseSym &S, void *mem, cudaStream_t s, const int64_t *col_ptr,
+                      const int32_t *row_idx, const double *cval);
+    cudaError_t reset(cudaStream_t s);
+    // factor P (A^T A)_FF P^T (+ identity outside F); st->chol_info, st->timeout
+    cudaError_t factor(cudaStream_t s, const uint8_t *inF, DevStatus *st);
+    // permF for the current F
+    cudaError_t perm_list(cudaStream_t s, const uint8_t *inF);
+    // v (n entries in the factor's order) <- (L L^T)^{-1} v
+    cudaError_t solve(cudaStream_t s, T *v, DevStatus *st);
+};
+
+}  // namespace tsnnls

@@ -1,0 +1,393 @@
+// Symbolic analysis for the supernodal sparse Cholesky of the cached normal
+// equations (Section 3: TAUCS factors A^T A as a sparse matrix; here the
+// structure is analysed once per problem on the host and the numeric work
+// runs on the GPU, sparse_chol.cu).
+//
+//   1. the pattern of G = A^T A from the pattern of A (column j meets column
+//      c when some row holds both);
+//   2. a fill-reducing order by nested dissection: a subgraph is split by
+//      the middle level of a breadth-first level structure rooted at a
+//      pseudo-peripheral vertex, both halves are ordered first, the
+//      separator last; small subgraphs keep their order;
+//   3. the elimination tree of P G P^T (Liu's algorithm with path
+//      compression) and a postorder of it, composed into the order;
+//   4. the row structure of every column of L by merging each column's own
+//      pattern with its children's structures;
+//   5. fundamental supernodes (a column joins its only child when their
+//      structures nest), at most max_width columns wide;
+//   6. per supernode: its rows, the earlier supernodes whose columns update
+//      it, the later supernodes that hold its off-diagonal rows, the offsets
+//      of its panel of L and of its diagonal block's inverse, and where every
+//      entry of the lower triangle of P G P^T lands in the panels.
+// Plain C++; deterministic (no hashing, no threads).
+#include "sparse_sym.h"
+
+#include <algorithm>
+#include <cstring>
+#include <functional>
+
+namespace tsnnls {
+
+namespace {
+
+struct Graph {
+    int64_t n = 0;
+    std::vector<int64_t> ptr;  // n + 1
+    std::vector<int32_t> adj;  // neighbours, no self loops, ascending
+};
+
+// Pattern of A^T A without the diagonal, as adjacency lists.
+void gram_graph(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col, Graph &g) {
+    const int64_t nnz = row_ptr[m];
+    std::vector<int64_t> cptr(n + 1, 0);
+    std::vector<int32_t> crow(nnz > 0 ? nnz : 1);
+    for (int64_t e = 0; e < nnz; ++e) cptr[col[e] + 1] += 1;
+    for (int64_t j = 0; j < n; ++j) cptr[j + 1] += cptr[j];
+    {
+        std::vector<int64_t> next(cptr.begin(), cptr.end() - 1);
+        for (int64_t r = 0; r < m; ++r)
+            for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) crow[next[col[e]]++] = (int32_t)r;
+    }
+    g.n = n;
+    g.ptr.assign(n + 1, 0);
+    g.adj.clear();
+    std::vector<int32_t> mark(n, -1);
+    std::vector<int32_t> nb;
+    for (int64_t j = 0; j < n; ++j) {
+        nb.clear();
+        mark[j] = (int32_t)j;
+        for (int64_t p = cptr[j]; p < cptr[j + 1]; ++p) {
+            const int32_t r = crow[p];
+            for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                const int32_t c = col[e];
+                if (mark[c] != (int32_t)j) {
+                    mark[c] = (int32_t)j;
+                    nb.push_back(c);
+                }
+            }
+        }
+        std::sort(nb.begin(), nb.end());
+        g.adj.insert(g.adj.end(), nb.begin(), nb.end());
+        g.ptr[j + 1] = (int64_t)g.adj.size();
+    }
+}
+
+// Nested dissection order (order[k] = vertex eliminated k-th).
+class Dissection {
+  public:
+    explicit Dissection(const Graph &g) : g_(g), sub_(g.n, -1), level_(g.n, -1) {}
+
+    std::vector<int32_t> run() {
+        std::vector<int32_t> all(g_.n);
+        for (int64_t v = 0; v < g_.n; ++v) all[v] = (int32_t)v;
+        order_.reserve(g_.n);
+        split(all);
+        return order_;
+    }
+
+  private:
+    static constexpr size_t kLeaf = 48;
+
+    // breadth-first levels inside the current subset (sub_ == id) from root;
+    // returns the vertices in visiting order, level_ set for them
+    std::vector<int32_t> bfs(int32_t root, int32_t id, int32_t *last_level) {
+        std::vector<int32_t> q;
+        q.push_back(root);
+        level_[root] = 0;
+        sub_[root] = id + 1;  // visited marker: id + 1
+        for (size_t h = 0; h < q.size(); ++h) {
+            const int32_t v = q[h];
+            for (int64_t p = g_.ptr[v]; p < g_.ptr[v + 1]; ++p) {
+                const int32_t u = g_.adj[p];
+                if (sub_[u] == id) {
+                    sub_[u] = id + 1;
+                    level_[u] = level_[v] + 1;
+                    q.push_back(u);
+                }
+            }
+        }
+        for (int32_t v : q) sub_[v] = id;  // back to "in the subset"
+        *last_level = level_[q.back()];
+        return q;
+    }
+
+    void split(std::vector<int32_t> &verts) {
+        if (verts.size() <= kLeaf) {
+            order_.insert(order_.end(), verts.begin(), verts.end());
+            return;
+        }
+        const int32_t id = next_id_;
+        next_id_ += 2;
+        for (int32_t v : verts) sub_[v] = id;
+        // connected components of the subset, each dissected on its own
+        int32_t last = 0;
+        std::vector<int32_t> comp = bfs(verts[0], id, &last);
+        if (comp.size() < verts.size()) {
+            std::vector<std::vector<int32_t>> comps;
+            for (int32_t v : comp) sub_[v] = -2;
+            comps.push_back(comp);
+            for (int32_t v : verts) {
+                if (sub_[v] != id) continue;
+                std::vector<int32_t> c = bfs(v, id, &last);
+                for (int32_t u : c) sub_[u] = -2;
+                comps.push_back(std::move(c));
+            }
+            for (auto &c : comps) split(c);
+            return;
+        }
+        // pseudo-peripheral root: repeat from the farthest vertex while the depth grows
+        int32_t root = comp.back(), depth = last;
+        for (int it = 0; it < 4; ++it) {
+            int32_t d2 = 0;
+            std::vector<int32_t> q = bfs(root, id, &d2);
+            if (d2 <= depth && it > 0) break;
+            depth = d2;
+            comp.swap(q);
+            root = comp.back();
+        }
+        int32_t maxl = 0;
+        comp = bfs(root, id, &maxl);
+        if (maxl < 2) {  // (nearly) complete subgraph: nothing to dissect
+            order_.insert(order_.end(), verts.begin(), verts.end());
+            for (int32_t v : verts) sub_[v] = -1;
+            return;
+        }
+        std::vector<int64_t> cnt(maxl + 1, 0);
+        for (int32_t v : comp) cnt[level_[v]] += 1;
+        // separator: the smallest level whose cumulative count lies within
+        // 35 %..65 % of the vertices (the median level if none)
+        const int64_t total = (int64_t)comp.size();
+        int64_t cum = 0;
+        int32_t best = -1, median = 1;
+        for (int32_t l = 0; l <= maxl; ++l) {
+            const int64_t before = cum;
+            cum += cnt[l];
+            if (before <= total / 2 && cum > total / 2) median = l;
+            if (l > 0 && l < maxl && 20 * before >= 7 * total && 20 * before <= 13 * total)
+                if (best < 0 || cnt[l] < cnt[best]) best = l;
+        }
+        if (best < 0) best = std::min(std::max(median, 1), maxl - 1);
+        std::vector<int32_t> a, b, s;
+        for (int32_t v : comp) {
+            sub_[v] = -1;
+            if (level_[v] < best) a.push_back(v);
+            else if (level_[v] > best) b.push_back(v);
+            else s.push_back(v);
+        }
+        split(a);
+        split(b);
+        order_.insert(order_.end(), s.begin(), s.end());
+    }
+
+    const Graph &g_;
+    std::vector<int32_t> sub_, level_;
+    std::vector<int32_t> order_;
+    int32_t next_id_ = 0;
+};
+
+}  // namespace
+
+int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col, int max_width,
+                   SparseSym &S) {
+    if (n <= 0 || m <= 0 || max_width < 1) return -1;
+    Graph g;
+    gram_graph(m, n, row_ptr, col, g);
+
+    // 2. nested dissection, then 3. elimination tree and postorder
+    std::vector<int32_t> perm = Dissection(g).run();  // new -> old
+    std::vector<int32_t> iperm(n);
+    auto etree_of = [&](const std::vector<int32_t> &pm, const std::vector<int32_t> &ipm,
+                        std::vector<int32_t> &parent) {
+        parent.assign(n, -1);
+        std::vector<int32_t> anc(n, -1);
+        for (int64_t i = 0; i < n; ++i) {  // row i of the lower triangle: columns k < i
+            const int32_t vi = pm[i];
+            for (int64_t p = g.ptr[vi]; p < g.ptr[vi + 1]; ++p) {
+                int32_t k = ipm[g.adj[p]];
+                if (k >= i) continue;
+                while (anc[k] != -1 && anc[k] != i) {
+                    const int32_t nx = anc[k];
+                    anc[k] = (int32_t)i;
+                    k = nx;
+                }
+                if (anc[k] == -1) {
+                    anc[k] = (int32_t)i;
+                    parent[k] = (int32_t)i;
+                }
+            }
+        }
+    };
+    for (int64_t k = 0; k < n; ++k) iperm[perm[k]] = (int32_t)k;
+    std::vector<int32_t> parent;
+    etree_of(perm, iperm, parent);
+    {
+        // postorder: children in ascending order, depth first
+        std::vector<int32_t> head(n, -1), nxt(n, -1), post;
+        post.reserve(n);
+        for (int64_t j = n - 1; j >= 0; --j)
+            if (parent[j] >= 0) {
+                nxt[j] = head[parent[j]];
+                head[parent[j]] = (int32_t)j;
+            }
+        std::vector<int32_t> stack;
+        for (int64_t r = 0; r < n; ++r) {
+            if (parent[r] != -1) continue;
+            stack.push_back((int32_t)r);
+            while (!stack.empty()) {
+                const int32_t v = stack.back();
+                if (head[v] >= 0) {
+                    const int32_t c = head[v];
+                    head[v] = nxt[c];
+                    stack.push_back(c);
+                } else {
+                    post.push_back(v);
+                    stack.pop_back();
+                }
+            }
+        }
+        std::vector<int32_t> p2(n);
+        for (int64_t k = 0; k < n; ++k) p2[k] = perm[post[k]];
+        perm.swap(p2);
+        for (int64_t k = 0; k < n; ++k) iperm[perm[k]] = (int32_t)k;
+        etree_of(perm, iperm, parent);
+    }
+
+    // lower pattern of P G P^T by column (new indices), diagonal first
+    S.n = n;
+    S.gptr.assign(n + 1, 0);
+    S.grow.clear();
+    S.gpair_orig_row.clear();
+    {
+        std::vector<int32_t> rows;
+        for (int64_t j = 0; j < n; ++j) {
+            rows.clear();
+            const int32_t vj = perm[j];
+            for (int64_t p = g.ptr[vj]; p < g.ptr[vj + 1]; ++p) {
+                const int32_t i = iperm[g.adj[p]];
+                if (i > j) rows.push_back(i);
+            }
+            std::sort(rows.begin(), rows.end());
+            S.grow.push_back((int32_t)j);
+            S.grow.insert(S.grow.end(), rows.begin(), rows.end());
+            S.gptr[j + 1] = (int64_t)S.grow.size();
+        }
+        S.gpair_orig_row.resize(S.grow.size());
+        for (size_t e = 0; e < S.grow.size(); ++e) S.gpair_orig_row[e] = perm[S.grow[e]];
+    }
+
+    // 4. column structures (rows below the diagonal), children merged
+    std::vector<std::vector<int32_t>> cs(n);
+    std::vector<int32_t> nchild(n, 0);
+    {
+        std::vector<int32_t> first_child(n, -1), sib(n, -1);
+        for (int64_t j = n - 1; j >= 0; --j)
+            if (parent[j] >= 0) {
+                sib[j] = first_child[parent[j]];
+                first_child[parent[j]] = (int32_t)j;
+                nchild[parent[j]] += 1;
+            }
+        std::vector<int32_t> mark(n, -1);
+        for (int64_t j = 0; j < n; ++j) {
+            std::vector<int32_t> &v = cs[j];
+            mark[j] = (int32_t)j;
+            for (int64_t p = S.gptr[j] + 1; p < S.gptr[j + 1]; ++p) {
+                const int32_t i = S.grow[p];
+                if (mark[i] != (int32_t)j) {
+                    mark[i] = (int32_t)j;
+                    v.push_back(i);
+                }
+            }
+            for (int32_t c = first_child[j]; c >= 0; c = sib[c])
+                for (int32_t i : cs[c])
+                    if (i > j && mark[i] != (int32_t)j) {
+                        mark[i] = (int32_t)j;
+                        v.push_back(i);
+                    }
+            std::sort(v.begin(), v.end());
+        }
+    }
+
+    // 5. fundamental supernodes, at most max_width wide
+    S.sn_first.clear();
+    S.col_sn.assign(n, 0);
+    for (int64_t j = 0; j < n; ++j) {
+        bool join = false;
+        if (j > 0 && !S.sn_first.empty()) {
+            const int64_t f = S.sn_first.back();
+            join = parent[j - 1] == j && nchild[j] == 1 && cs[j - 1].size() == cs[j].size() + 1 &&
+                   j - f < max_width;
+        }
+        if (!join) S.sn_first.push_back((int32_t)j);
+        S.col_sn[j] = (int32_t)S.sn_first.size() - 1;
+    }
+    const int64_t ns = (int64_t)S.sn_first.size();
+    S.ns = ns;
+    S.sn_first.push_back((int32_t)n);
+
+    // 6. rows, panel and inverse offsets, update and ancestor lists
+    S.rows_off.assign(ns + 1, 0);
+    S.rows.clear();
+    S.L_off.assign(ns + 1, 0);
+    S.W_off.assign(ns + 1, 0);
+    S.nnz_L = 0;
+    S.flops = 0.0;
+    S.max_height = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        const int32_t f = S.sn_first[s], l = S.sn_first[s + 1] - 1, w = l - f + 1;
+        for (int32_t c = f; c <= l; ++c) S.rows.push_back(c);
+        S.rows.insert(S.rows.end(), cs[l].begin(), cs[l].end());
+        S.rows_off[s + 1] = (int64_t)S.rows.size();
+        const int64_t h = S.rows_off[s + 1] - S.rows_off[s];
+        S.max_height = std::max<int64_t>(S.max_height, h);
+        S.L_off[s + 1] = S.L_off[s] + ((h + 3) / 4 * 4) * w;
+        S.W_off[s + 1] = S.W_off[s] + (int64_t)w * w;
+        S.nnz_L += h * w - (int64_t)w * (w - 1) / 2;
+        for (int32_t c = 0; c < w; ++c) {
+            const double cc = (double)(h - c);  // entries in column f + c, diagonal included
+            S.flops += cc * cc;
+        }
+    }
+    // D(s): supernodes d < s with a row in s's columns; A(d): supernodes
+    // above d holding its off-diagonal rows (both ascending)
+    S.d_off.assign(ns + 1, 0);
+    S.a_off.assign(ns + 1, 0);
+    S.alist.clear();
+    for (int64_t d = 0; d < ns; ++d) {
+        const int32_t w = S.sn_first[d + 1] - S.sn_first[d];
+        int32_t lastsn = -1;
+        for (int64_t p = S.rows_off[d] + w; p < S.rows_off[d + 1]; ++p) {
+            const int32_t t = S.col_sn[S.rows[p]];
+            if (t != lastsn) {
+                S.alist.push_back(t);
+                S.d_off[t + 1] += 1;
+                lastsn = t;
+            }
+        }
+        S.a_off[d + 1] = (int64_t)S.alist.size();
+    }
+    for (int64_t s = 0; s < ns; ++s) S.d_off[s + 1] += S.d_off[s];
+    S.dlist.assign(S.d_off[ns], 0);
+    {
+        std::vector<int64_t> fill(S.d_off.begin(), S.d_off.end() - 1);
+        for (int64_t d = 0; d < ns; ++d)
+            for (int64_t p = S.a_off[d]; p < S.a_off[d + 1]; ++p) S.dlist[fill[S.alist[p]]++] = (int32_t)d;
+    }
+    // where each lower entry of P G P^T lands: panel of its column's
+    // supernode, column j - f, local row = position of i among the rows
+    S.gpos.resize(S.grow.size());
+    for (int64_t j = 0; j < n; ++j) {
+        const int32_t s = S.col_sn[j], f = S.sn_first[s];
+        const int64_t h = S.rows_off[s + 1] - S.rows_off[s], ld = (h + 3) / 4 * 4;
+        const int32_t *rb = S.rows.data() + S.rows_off[s], *re = S.rows.data() + S.rows_off[s + 1];
+        for (int64_t p = S.gptr[j]; p < S.gptr[j + 1]; ++p) {
+            const int64_t loc = std::lower_bound(rb, re, S.grow[p]) - rb;
+            S.gpos[p] = S.L_off[s] + (j - f) * ld + loc;
+        }
+    }
+    S.perm.swap(perm);
+    S.iperm.swap(iperm);
+    S.parent.swap(parent);
+    return 0;
+}
+
+}  // namespace tsnnls

@@ -64,7 +64,8 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     checks = []
     structs = (("tsnnls_opts", ts.Opts), ("tsnnls_info", ts.Info), ("tsnnls_csr", ts.CSR),
-               ("tsnnls_queue_stats", ts.QueueStats), ("tsnnls_phase_stat", ts.PhaseStat))
+               ("tsnnls_queue_stats", ts.QueueStats), ("tsnnls_phase_stat", ts.PhaseStat),
+               ("tsnnls_sparse_stats", ts.SparseStats))
     for cname, py in structs:
         checks.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:

@@ -218,6 +218,42 @@ def lsqr_large(seed=SEED_BASE + 3, m=2_000_000, n=200_000, per_row=8,
     return CSRProblem(m, n, row_ptr, col_idx, val, b, x, f"lsqr_large_{m}x{n}")
 
 
+def grid_sparse(g, seed=SEED_BASE + 6, m_factor=2, per_row=4, zero_frac=0.4, noise=1e-2,
+                name=None) -> CSRProblem:
+    """A sparse problem whose A^T A keeps a small-separator pattern (the
+    sparse-Gram workload of the supernodal factor): n = g * g unknowns on a
+    g x g grid.  Rows 0 .. n-1 hold the unit diagonal (A[i, i] = 1); each of
+    the other m - n rows (m = m_factor * n) holds per_row distinct unknowns
+    drawn from the 3 x 3 grid neighbourhood of a uniformly chosen point, with
+    N(0,1) values.  Columns meet in A^T A only within grid distance 2.
+    x* has zero_frac exact zeros, the rest U(0.1, 1); b = A x* + N(0, noise^2)."""
+    rng = np.random.default_rng(seed)
+    n = g * g
+    m = int(m_factor * n)
+    extra = m - n
+    cx = rng.integers(0, g, size=extra)
+    cy = rng.integers(0, g, size=extra)
+    offs = np.array([(dx, dy) for dx in (-1, 0, 1) for dy in (-1, 0, 1)])
+    keys = rng.random((extra, 9))
+    nx = cx[:, None] + offs[None, :, 0]
+    ny = cy[:, None] + offs[None, :, 1]
+    inside = (nx >= 0) & (nx < g) & (ny >= 0) & (ny < g)
+    keys[~inside] = 2.0  # never chosen before an inside neighbour
+    pick = np.argsort(keys, axis=1)[:, :per_row]
+    ok = np.take_along_axis(inside, pick, axis=1)
+    cols = (np.take_along_axis(nx, pick, axis=1) * g + np.take_along_axis(ny, pick, axis=1))
+    rows = np.repeat(np.arange(n, m), per_row).reshape(extra, per_row)
+    vals = rng.standard_normal((extra, per_row))
+    rows, cols, vals = rows[ok], cols[ok], vals[ok]
+    rows = np.concatenate([np.arange(n), rows])
+    cols = np.concatenate([np.arange(n), cols])
+    vals = np.concatenate([np.ones(n), vals])
+    row_ptr, col_idx, val = _csr_from_rows(m, n, rows, cols, vals)
+    x, _ = _planted_x(rng, n, zero_frac)
+    b = _csr_matvec(row_ptr, col_idx, val, x) + rng.normal(0.0, noise, size=m)
+    return CSRProblem(m, n, row_ptr, col_idx, val, b, x, name or f"grid_sparse_{g}x{g}")
+
+
 def serving_request(index, seed=SEED_BASE + 4, n_lo=64, n_hi=8192) -> CSRProblem:
     """Request ``index`` of the serving mix: n = round(exp(U(ln 64, ln 8192))),
     m = 2n, density d ~ U(0.01, 0.05) at uniform positions, N(0,1) values,
