@@ -381,8 +381,9 @@ int tsnnls_wait_probe(int64_t polls);
  * A^T A from the pattern of A (host CSR: row_ptr m + 1 entries, col_idx
  * row_ptr[m] entries), a nested-dissection order, the elimination tree of
  * the reordered matrix in postorder, the row structure of L and its
- * supernodes of at most max_width columns (Section 3: the structure TAUCS
- * computes before its numeric factorisation).  perm_out (n entries, may be
+ * supernodes of at most max_width columns, small ones merged with their
+ * parents (Section 3: the structure TAUCS computes before its numeric
+ * factorisation).  perm_out (n entries, may be
  * NULL) receives the order (position -> original column); parent_out (n, may
  * be NULL) the elimination tree in positions (-1 at a root); stats (may be
  * NULL) the sizes below.  TSNNLS_EINVAL for a malformed pattern. */
@@ -392,8 +393,11 @@ typedef struct {
     int64_t nnz_l;         /* entries of L's structure (lower triangle, diagonal included) */
     int64_t supernodes;
     int64_t max_height;    /* rows of the tallest supernode */
-    double factor_flops;   /* sum over the columns of L of (entries in the column)^2 */
+    double factor_flops;   /* sum over the stored columns of L of (entries in the column)^2 */
     double analysis_ms;    /* host wall time */
+    int64_t nnz_l_stored;  /* entries the supernodal panels store: nnz_l plus the explicit zeros
+                              that relaxed amalgamation of small supernodes adds */
+    int64_t update_entries;  /* entries of the multifrontal update matrices (device memory) */
 } tsnnls_sparse_stats;
 int tsnnls_sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t max_width,
                           int32_t *perm_out, int32_t *parent_out, tsnnls_sparse_stats *stats);

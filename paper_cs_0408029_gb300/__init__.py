@@ -72,7 +72,8 @@ class Info(ctypes.Structure):
 class SparseStats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz_gram", ctypes.c_int64), ("nnz_l", ctypes.c_int64),
                 ("supernodes", ctypes.c_int64), ("max_height", ctypes.c_int64),
-                ("factor_flops", ctypes.c_double), ("analysis_ms", ctypes.c_double)]
+                ("factor_flops", ctypes.c_double), ("analysis_ms", ctypes.c_double),
+                ("nnz_l_stored", ctypes.c_int64), ("update_entries", ctypes.c_int64)]
 
 
 _lib = None

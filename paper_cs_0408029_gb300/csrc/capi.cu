@@ -305,7 +305,9 @@ int tsnnls_sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const in
     if (stats) {
         stats->n = n;
         stats->nnz_gram = (int64_t)S->grow.size();
-        stats->nnz_l = S->nnz_L;
+        stats->nnz_l = S->exact_nnz_L;
+        stats->nnz_l_stored = S->nnz_L;
+        stats->update_entries = S->U_off[S->ns];
         stats->supernodes = S->ns;
         stats->max_height = S->max_height;
         stats->factor_flops = S->flops;

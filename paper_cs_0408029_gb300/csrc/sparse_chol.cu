@@ -6,23 +6,23 @@
 // so one structure serves every F: a variable outside F keeps a unit column,
 // and its entry of every solve is 0.
 //
-// Factor: one persistent kernel, one CTA per SM.  CTAs take supernodes in
-// postorder by ticket; a supernode waits (bounded) until every earlier
-// supernode that updates it is done, which is always a CTA that took a
-// smaller ticket and so is running or finished.  It then
-//   - clears its panel (rows x width, column-major) and assembles the
-//     entries of G' in its columns;
-//   - subtracts, descendant by descendant in ascending order, L_d(R, :)
-//     L_d(C, :)^T for the descendant's rows R at or below its first column
-//     and C inside its columns (scattered through a row -> panel-row map);
+// Factor (multifrontal): one persistent kernel, one CTA per SM.  CTAs take
+// supernodes in postorder by ticket; a supernode waits (bounded) until its
+// children in the supernodal tree are done -- CTAs holding smaller tickets,
+// so running or finished.  It then
+//   - clears its panel (rows x width) and its update matrix (rows below
+//     squared), assembles the entries of G' in its columns, and adds its
+//     children's update matrices, child by child in ascending order, through
+//     the precomputed positions of their rows among its own;
 //   - factors and inverts its diagonal block in shared memory with the dense
-//     block code of the blocked factorisation (dense_block.cuh), and forms
+//     block code of the blocked factorisation (dense_block.cuh) and forms
 //     the rows below as X = B W^T, 32 rows at a time;
-//   - publishes a done flag (release).
-// Solves: the same ticketing, forward in postorder (a supernode gathers the
-// updates of its descendants, then applies W), backward in reverse
-// postorder (it gathers the solved entries of its rows below, then W^T).
-// Every sum runs in a fixed order, so results are reproducible.
+//   - subtracts X X^T from its update matrix and publishes a done flag.
+// Solves: forward in postorder (a supernode adds its children's update
+// vectors, applies W, and leaves the update vector of its rows below for its
+// parent), backward in reverse postorder (it gathers the solved entries of
+// its rows below from the supernodes above, then applies W^T).  Every sum
+// runs in a fixed order, so results are reproducible.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -125,28 +125,32 @@ struct SpSmem {
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256, 1)
-    sp_factor_kernel(SpDev D, const uint8_t *__restrict__ inF, T *__restrict__ L, T *__restrict__ Wa, DevStatus *st) {
+    sp_factor_kernel(SpDev D, const uint8_t *__restrict__ inF, T *__restrict__ L, T *__restrict__ Wa,
+                     T *__restrict__ Ua, DevStatus *st) {
     using SM = SpSmem<T, NB>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T(*A)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw);
     T(*W)[NB + 4] = reinterpret_cast<T(*)[NB + 4]>(smem_raw + sizeof(T) * NB * SM::P);
+    // the same memory viewed as 32 x 32 blocks, for supernodes of at most 32 columns
+    T(*A32)[36] = reinterpret_cast<T(*)[36]>(smem_raw);
+    T(*W32)[36] = reinterpret_cast<T(*)[36]>(smem_raw + sizeof(T) * NB * SM::P);
     T(*Bs)[36] = reinterpret_cast<T(*)[36]>(smem_raw + 2 * sizeof(T) * NB * SM::P);  // Bs[t][r]
     __shared__ int sh_s, ok_sh, bad_sh;
     __shared__ __align__(16) T col[2][32];
     const int tid = threadIdx.x;
-    int32_t *map = D.map + (int64_t)blockIdx.x * D.n;
     for (;;) {
         if (tid == 0) sh_s = atomicAdd(D.ticket, 1);
         __syncthreads();
         const int64_t s = sh_s;
         if (s >= D.ns) return;
-        if (!sp_wait_all(D, D.flags, D.dlist, D.d_off[s], D.d_off[s + 1], st, &ok_sh)) return;
+        if (!sp_wait_all(D, D.flags, D.clist, D.c_off[s], D.c_off[s + 1], st, &ok_sh)) return;
         const int32_t f = D.sn_first[s], w = D.sn_first[s + 1] - f;
-        const int32_t *rows = D.rows + D.rows_off[s];
         const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4;
+        const int64_t hu = h - w, ldu = (hu + 3) / 4 * 4;
         T *P = L + D.L_off[s];
-        for (int64_t i = tid; i < h; i += 256) map[rows[i]] = (int32_t)i;
+        T *U = Ua + D.U_off[s];
         for (int64_t e = tid; e < ld * w; e += 256) P[e] = T(0);
+        for (int64_t e = tid; e < ldu * hu; e += 256) U[e] = T(0);
         __syncthreads();
         // G' in this supernode's columns
         for (int64_t p = D.gptr[f] + tid; p < D.gptr[f + w]; p += 256) {
@@ -155,73 +159,59 @@ __global__ void __launch_bounds__(256, 1)
             L[D.gpos[p]] = v;
         }
         __syncthreads();
-        // updates from the descendants, one after another
-        for (int64_t di = D.d_off[s]; di < D.d_off[s + 1]; ++di) {
-            const int32_t d = D.dlist[di];
-            const int32_t wd = D.sn_first[d + 1] - D.sn_first[d];
-            const int64_t rb = D.rows_off[d], hd = D.rows_off[d + 1] - rb, ldd = (hd + 3) / 4 * 4;
-            const int32_t *rd = D.rows + rb;
-            const T *Ld = L + D.L_off[d];
-            const int64_t p0 = sp_lower_bound(rd, wd, hd, f), p1 = sp_lower_bound(rd, p0, hd, f + w);
-            const int64_t M = hd - p0, N = p1 - p0;
-            const int64_t mt = (M + 3) / 4, nt = (N + 3) / 4;
-            for (int64_t tile = tid; tile < mt * nt; tile += 256) {
-                const int64_t tr = tile % mt, tc = tile / mt;
-                const int64_t pa = p0 + 4 * tr, qa = p0 + 4 * tc;
-                if (pa + 3 < qa) continue;  // above the diagonal of the target
-                T acc[4][4] = {};
-                for (int k = 0; k < wd; ++k) {
-                    const T *lk = Ld + (int64_t)k * ldd;
-                    T x[4], y[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        x[u] = pa + u < hd ? lk[pa + u] : T(0);
-                        y[u] = qa + u < p1 ? lk[qa + u] : T(0);
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] += x[a] * y[b];
-                }
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int64_t q = qa + b;
-                    if (q >= p1) break;
-                    T *pc = P + (int64_t)(rd[q] - f) * ld;
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int64_t p = pa + a;
-                        if (p < hd && p >= q) {
-                            // rows of a descendant at or below this supernode's first
-                            // column are rows of this supernode (elimination tree)
-                            const int32_t loc = map[rd[p]];
-                            if (loc >= 0 && loc < h) pc[loc] -= acc[a][b];
-                        }
-                    }
-                }
+        // children's update matrices, one child after another (extend-add)
+        for (int64_t ci = D.c_off[s]; ci < D.c_off[s + 1]; ++ci) {
+            const int32_t c = D.clist[ci];
+            const int32_t wc = D.sn_first[c + 1] - D.sn_first[c];
+            const int64_t hc = D.rows_off[c + 1] - D.rows_off[c] - wc, lduc = (hc + 3) / 4 * 4;
+            const T *Uc = Ua + D.U_off[c];
+            const int32_t *rel = D.rel + D.u_off[c];
+            for (int64_t e = tid; e < hc * hc; e += 256) {
+                const int64_t i = e % hc, j = e / hc;
+                if (i < j) continue;
+                const int32_t li = rel[i], lj = rel[j];  // li >= lj: rows keep their order
+                const T v = Uc[j * lduc + i];
+                if (lj < w) P[(int64_t)lj * ld + li] += v;
+                else U[(int64_t)(lj - w) * ldu + (li - w)] += v;
             }
             __syncthreads();
         }
         // the diagonal block: factor and inverse in shared memory
         if (tid == 0) bad_sh = 0;
-        for (int e = tid; e < NB * NB; e += 256) {
-            const int c = e / NB, r = e % NB;
-            T v = T(0);
-            if (r < w && c < w) v = r >= c ? P[(int64_t)c * ld + r] : T(0);
-            else if (r == c) v = T(1);
-            A[c][r] = v;
-            W[c][r] = T(0);
+        if (w <= 32) {
+            for (int e = tid; e < 32 * 32; e += 256) {
+                const int c = e / 32, r = e % 32;
+                T v = T(0);
+                if (r < w && c < w) v = r >= c ? P[(int64_t)c * ld + r] : T(0);
+                else if (r == c) v = T(1);
+                A32[c][r] = v;
+                W32[c][r] = T(0);
+            }
+            __syncthreads();
+            diag_block_core<T, 32>(A32, W32, col, &bad_sh);
+        } else {
+            for (int e = tid; e < NB * NB; e += 256) {
+                const int c = e / NB, r = e % NB;
+                T v = T(0);
+                if (r < w && c < w) v = r >= c ? P[(int64_t)c * ld + r] : T(0);
+                else if (r == c) v = T(1);
+                A[c][r] = v;
+                W[c][r] = T(0);
+            }
+            __syncthreads();
+            diag_block_core<T, NB>(A, W, col, &bad_sh);
         }
-        __syncthreads();
-        diag_block_core<T, NB>(A, W, col, &bad_sh);
         if (tid == 0 && bad_sh && bad_sh <= w) atomicCAS(&st->chol_info, 0, (int32_t)(f + bad_sh));
+        auto Lsm = [&](int c, int r) -> T { return w <= 32 ? A32[c][r] : A[c][r]; };
+        auto Wsm = [&](int c, int r) -> T { return w <= 32 ? W32[c][r] : W[c][r]; };  // W(r, c)
         T *Ws = Wa + D.W_off[s];
         for (int e = tid; e < w * w; e += 256) {
             const int c = e / w, r = e % w;
-            if (r >= c) P[(int64_t)c * ld + r] = A[c][r];
-            Ws[e] = W[c][r];  // W(r, c), column-major, w x w
+            if (r >= c) P[(int64_t)c * ld + r] = Lsm(c, r);
+            Ws[e] = Wsm(c, r);  // W(r, c), column-major, w x w
         }
         // rows below: X = B W^T, 32 rows at a time through shared memory
+        // (Bs lies after both views of A and W)
         for (int64_t r0 = w; r0 < h; r0 += 32) {
             __syncthreads();
             for (int e = tid; e < w * 32; e += 256) {
@@ -232,8 +222,41 @@ __global__ void __launch_bounds__(256, 1)
             for (int e = tid; e < w * 32; e += 256) {
                 const int c = e / 32, rr = e % 32;
                 T acc = T(0);
-                for (int t = 0; t <= c; ++t) acc += Bs[t][rr] * W[t][c];  // W(c, t), zero for t > c
+                for (int t = 0; t <= c; ++t) acc += Bs[t][rr] * Wsm(t, c);  // W(c, t), zero for t > c
                 if (r0 + rr < h) P[(int64_t)c * ld + r0 + rr] = acc;
+            }
+        }
+        __syncthreads();
+        // update matrix: U -= X X^T on its lower triangle, X = rows below (hu x w)
+        const int64_t nt = (hu + 3) / 4;
+        const T *X = P + w;
+        for (int64_t tile = tid; tile < nt * nt; tile += 256) {
+            const int64_t tr = tile % nt, tc = tile / nt;
+            if (tr < tc) continue;
+            const int64_t i0 = 4 * tr, j0 = 4 * tc;
+            T acc[4][4] = {};
+            for (int k = 0; k < w; ++k) {
+                const T *xk = X + (int64_t)k * ld;
+                T xi[4], xj[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    xi[u] = i0 + u < hu ? xk[i0 + u] : T(0);
+                    xj[u] = j0 + u < hu ? xk[j0 + u] : T(0);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += xi[a] * xj[b];
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int64_t j = j0 + b;
+                if (j >= hu) break;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int64_t i = i0 + a;
+                    if (i < hu && i >= j) U[j * ldu + i] -= acc[a][b];
+                }
             }
         }
         __syncthreads();
@@ -248,8 +271,11 @@ constexpr int kSpT = 128;  // threads of a solve CTA
 
 template <typename T>
 __global__ void __launch_bounds__(kSpT)
-    sp_fwd_kernel(SpDev D, const T *__restrict__ L, const T *__restrict__ Wa, T *v, DevStatus *st) {
-    __shared__ T t_sh[128];
+    sp_fwd_kernel(SpDev D, const T *__restrict__ L, const T *__restrict__ Wa, T *__restrict__ ua, T *v,
+                  DevStatus *st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *a = reinterpret_cast<T *>(smem_raw);  // max_height entries
+    __shared__ T y_sh[64];
     __shared__ int sh_s, ok_sh;
     const int tid = threadIdx.x;
     for (;;) {
@@ -257,29 +283,36 @@ __global__ void __launch_bounds__(kSpT)
         __syncthreads();
         const int64_t s = sh_s;
         if (s >= D.ns) return;
-        if (!sp_wait_all(D, D.flags, D.dlist, D.d_off[s], D.d_off[s + 1], st, &ok_sh)) return;
+        if (!sp_wait_all(D, D.flags, D.clist, D.c_off[s], D.c_off[s + 1], st, &ok_sh)) return;
         const int32_t f = D.sn_first[s], w = D.sn_first[s + 1] - f;
-        if (tid < w) t_sh[tid] = __ldcg(v + f + tid);
+        const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4, hu = h - w;
+        for (int64_t i = tid; i < h; i += kSpT) a[i] = i < w ? v[f + i] : T(0);
         __syncthreads();
-        for (int64_t di = D.d_off[s]; di < D.d_off[s + 1]; ++di) {
-            const int32_t d = D.dlist[di];
-            const int32_t fd = D.sn_first[d], wd = D.sn_first[d + 1] - fd;
-            const int64_t rb = D.rows_off[d], hd = D.rows_off[d + 1] - rb, ldd = (hd + 3) / 4 * 4;
-            const int32_t *rd = D.rows + rb;
-            const T *Ld = L + D.L_off[d];
-            const int64_t p0 = sp_lower_bound(rd, wd, hd, f), p1 = sp_lower_bound(rd, p0, hd, f + w);
-            for (int64_t q = p0 + tid; q < p1; q += kSpT) {
-                T acc = T(0);
-                for (int k = 0; k < wd; ++k) acc += Ld[(int64_t)k * ldd + q] * __ldcg(v + fd + k);
-                t_sh[rd[q] - f] -= acc;
-            }
+        for (int64_t ci = D.c_off[s]; ci < D.c_off[s + 1]; ++ci) {
+            const int32_t c = D.clist[ci];
+            const int32_t wc = D.sn_first[c + 1] - D.sn_first[c];
+            const int64_t hc = D.rows_off[c + 1] - D.rows_off[c] - wc;
+            const T *uc = ua + D.u_off[c];
+            const int32_t *rel = D.rel + D.u_off[c];
+            for (int64_t i = tid; i < hc; i += kSpT) a[rel[i]] -= __ldcg(uc + i);
             __syncthreads();
         }
         const T *Ws = Wa + D.W_off[s];
-        T y = T(0);
-        if (tid < w)
-            for (int c = 0; c <= tid; ++c) y += Ws[(int64_t)c * w + tid] * t_sh[c];  // W(r, c), c <= r
-        if (tid < w) v[f + tid] = y;
+        if (tid < w) {
+            T y = T(0);
+            for (int c = 0; c <= tid; ++c) y += Ws[(int64_t)c * w + tid] * a[c];  // W(r, c), c <= r
+            y_sh[tid] = y;
+            v[f + tid] = y;
+        }
+        __syncthreads();
+        // update vector of the rows below, what the parent subtracts: L_below y
+        // plus the children's updates passed through (a_below holds minus those)
+        const T *Ls = L + D.L_off[s];
+        for (int64_t i = tid; i < hu; i += kSpT) {
+            T acc = -a[w + i];
+            for (int k = 0; k < w; ++k) acc += Ls[(int64_t)k * ld + w + i] * y_sh[k];
+            ua[D.u_off[s] + i] = acc;
+        }
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -344,15 +377,17 @@ int SparseChol<T>::nb() {
 }
 
 template <typename T>
-size_t SparseChol<T>::device_bytes(const SparseSym &S, int ctas) {
+size_t SparseChol<T>::device_bytes(const SparseSym &S, int /*ctas*/) {
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t ns = (size_t)S.ns, n = (size_t)S.n, ng = S.grow.size();
+    const size_t ns = (size_t)S.ns, n = (size_t)S.n, ng = S.grow.size(), nu = (size_t)S.u_off[S.ns];
     size_t b = 0;
-    b += up(4 * (ns + 1)) + up(8 * (ns + 1)) + up(4 * S.rows.size()) + 4 * up(8 * (ns + 1));
-    b += up(4 * S.dlist.size() + 4) + up(4 * S.alist.size() + 4);
+    b += up(4 * (ns + 1)) + up(8 * (ns + 1)) + up(4 * S.rows.size() + 4);  // sn_first, rows_off, rows
+    b += 6 * up(8 * (ns + 1));                                           // L, W, U, u, c, a offsets
+    b += up(4 * S.clist.size() + 4) + up(4 * S.alist.size() + 4) + up(4 * nu + 4);  // clist, alist, rel
     b += up(4 * n) + up(8 * (n + 1)) + 2 * up(4 * ng) + up(8 * ng) + up(8 * ng);  // perm, gptr, rows/cols, gpos, gval
     b += up(sizeof(T) * (size_t)S.L_off[ns]) + up(sizeof(T) * (size_t)S.W_off[ns]);
-    b += up(4 * n * (size_t)ctas) + up(4 * ns) + up(16) + up(4 * n) + up(sizeof(T) * n);
+    b += up(sizeof(T) * (size_t)S.U_off[ns]) + up(sizeof(T) * nu + 4);   // update matrices and vectors
+    b += up(4 * ns) + up(16) + up(4 * n);                                // flags, ticket / abort, permF
     return b + 256;
 }
 
@@ -360,6 +395,7 @@ template <typename T>
 cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, const int64_t *col_ptr,
                                  const int32_t *row_idx, const double *cval) {
     ctas = std::max(1, num_sms());
+    max_height = S.max_height;
     char *p = static_cast<char *>(mem);
     auto take = [&](size_t b) {
         p = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(p) + 255) / 256 * 256);
@@ -367,18 +403,21 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
         p += std::max<size_t>(b, 1);
         return q;
     };
-    const size_t ns = (size_t)S.ns, n = (size_t)S.n, ng = S.grow.size();
+    const size_t ns = (size_t)S.ns, n = (size_t)S.n, ng = S.grow.size(), nu = (size_t)S.u_off[S.ns];
     D.n = S.n;
     D.ns = S.ns;
     int32_t *sn_first = (int32_t *)take(4 * (ns + 1));
     int64_t *rows_off = (int64_t *)take(8 * (ns + 1));
-    int32_t *rows = (int32_t *)take(4 * S.rows.size());
+    int32_t *rows = (int32_t *)take(4 * S.rows.size() + 4);
     int64_t *L_off = (int64_t *)take(8 * (ns + 1));
     int64_t *W_off = (int64_t *)take(8 * (ns + 1));
-    int64_t *d_off = (int64_t *)take(8 * (ns + 1));
+    int64_t *U_off = (int64_t *)take(8 * (ns + 1));
+    int64_t *u_off = (int64_t *)take(8 * (ns + 1));
+    int64_t *c_off = (int64_t *)take(8 * (ns + 1));
     int64_t *a_off = (int64_t *)take(8 * (ns + 1));
-    int32_t *dlist = (int32_t *)take(4 * S.dlist.size() + 4);
+    int32_t *clist = (int32_t *)take(4 * S.clist.size() + 4);
     int32_t *alist = (int32_t *)take(4 * S.alist.size() + 4);
+    int32_t *rel = (int32_t *)take(4 * nu + 4);
     int32_t *perm = (int32_t *)take(4 * n);
     int64_t *gptr = (int64_t *)take(8 * (n + 1));
     int32_t *grow_orig = (int32_t *)take(4 * ng);
@@ -387,11 +426,11 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     double *gval = (double *)take(8 * ng);
     Lmem = (T *)take(sizeof(T) * (size_t)S.L_off[ns]);
     Wmem = (T *)take(sizeof(T) * (size_t)S.W_off[ns]);
-    int32_t *map = (int32_t *)take(4 * n * (size_t)ctas);
+    Umem = (T *)take(sizeof(T) * (size_t)S.U_off[ns]);
+    umem = (T *)take(sizeof(T) * nu + 4);
     int32_t *flags = (int32_t *)take(4 * ns);
     int32_t *ctl = (int32_t *)take(16);
     permF = (int32_t *)take(4 * n);
-    vec = (T *)take(sizeof(T) * n);
     // per-entry original column of the lower pattern
     std::vector<int32_t> gcol(ng);
     for (int64_t j = 0; j < S.n; ++j)
@@ -405,10 +444,13 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     up(rows, S.rows.data(), 4 * S.rows.size());
     up(L_off, S.L_off.data(), 8 * (ns + 1));
     up(W_off, S.W_off.data(), 8 * (ns + 1));
-    up(d_off, S.d_off.data(), 8 * (ns + 1));
+    up(U_off, S.U_off.data(), 8 * (ns + 1));
+    up(u_off, S.u_off.data(), 8 * (ns + 1));
+    up(c_off, S.c_off.data(), 8 * (ns + 1));
     up(a_off, S.a_off.data(), 8 * (ns + 1));
-    up(dlist, S.dlist.data(), 4 * S.dlist.size());
+    up(clist, S.clist.data(), 4 * S.clist.size());
     up(alist, S.alist.data(), 4 * S.alist.size());
+    up(rel, S.rel.data(), 4 * nu);
     up(perm, S.perm.data(), 4 * n);
     up(gptr, S.gptr.data(), 8 * (n + 1));
     up(grow_orig, S.gpair_orig_row.data(), 4 * ng);
@@ -423,17 +465,19 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     D.rows = rows;
     D.L_off = L_off;
     D.W_off = W_off;
-    D.d_off = d_off;
+    D.U_off = U_off;
+    D.u_off = u_off;
+    D.c_off = c_off;
     D.a_off = a_off;
-    D.dlist = dlist;
+    D.clist = clist;
     D.alist = alist;
+    D.rel = rel;
     D.perm = perm;
     D.gptr = gptr;
     D.grow_orig = grow_orig;
     D.gcol_orig = gcol_orig;
     D.gpos = gpos;
     D.gval = gval;
-    D.map = map;
     D.flags = flags;
     D.ticket = ctl;
     D.abort = ctl + 1;
@@ -458,7 +502,7 @@ cudaError_t SparseChol<T>::factor(cudaStream_t s, const uint8_t *inF, DevStatus 
                                          (int)smem);
     if (e == cudaSuccess) e = reset(s);
     if (e != cudaSuccess) return e;
-    sp_factor_kernel<T, NB><<<ctas, 256, smem, s>>>(D, inF, Lmem, Wmem, st);
+    sp_factor_kernel<T, NB><<<ctas, 256, smem, s>>>(D, inF, Lmem, Wmem, Umem, st);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -474,9 +518,11 @@ cudaError_t SparseChol<T>::perm_list(cudaStream_t s, const uint8_t *inF) {
 template <typename T>
 cudaError_t SparseChol<T>::solve(cudaStream_t s, T *v, DevStatus *st) {
     const int g = std::max(1, num_sms() * 4);
-    cudaError_t e = reset(s);
+    const size_t smem = sizeof(T) * (size_t)std::max<int64_t>(max_height, 1);
+    cudaError_t e = cudaFuncSetAttribute(sp_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = reset(s);
     if (e != cudaSuccess) return e;
-    sp_fwd_kernel<T><<<g, kSpT, 0, s>>>(D, Lmem, Wmem, v, st);
+    sp_fwd_kernel<T><<<g, kSpT, smem, s>>>(D, Lmem, Wmem, umem, v, st);
     e = reset(s);
     if (e != cudaSuccess) return e;
     sp_bwd_kernel<T><<<g, kSpT, 0, s>>>(D, Lmem, Wmem, v, st);

@@ -16,14 +16,13 @@ struct SpDev {
     const int32_t *sn_first;
     const int64_t *rows_off;
     const int32_t *rows;
-    const int64_t *L_off, *W_off, *d_off, *a_off;
-    const int32_t *dlist, *alist;
+    const int64_t *L_off, *W_off, *U_off, *u_off, *c_off, *a_off;
+    const int32_t *clist, *alist, *rel;
     const int32_t *perm;
     const int64_t *gptr;
     const int32_t *grow_orig, *gcol_orig;
     const int64_t *gpos;
     double *gval;        // A^T A on its lower pattern (FP64)
-    int32_t *map;        // per CTA of the factor: row -> panel row, n entries each
     int32_t *flags;      // per supernode: done
     int32_t *ticket;     // ticket counter, then the abort flag
     int32_t *abort;
@@ -38,8 +37,10 @@ struct SparseChol {
     SpDev D{};
     T *Lmem = nullptr;      // panels
     T *Wmem = nullptr;      // inverses of the diagonal blocks
+    T *Umem = nullptr;      // update matrices
+    T *umem = nullptr;      // update vectors of the forward solve
     int32_t *permF = nullptr;  // per position of the order: its variable if in F, else -1
-    T *vec = nullptr;       // n entries of scratch in the factor's type
+    int64_t max_height = 0;
     int ctas = 1;
 
     static int nb();  // widest supernode: the dense block size of the factor

@@ -14,11 +14,13 @@
 //   4. the row structure of every column of L by merging each column's own
 //      pattern with its children's structures;
 //   5. fundamental supernodes (a column joins its only child when their
-//      structures nest), at most max_width columns wide;
-//   6. per supernode: its rows, the earlier supernodes whose columns update
-//      it, the later supernodes that hold its off-diagonal rows, the offsets
-//      of its panel of L and of its diagonal block's inverse, and where every
-//      entry of the lower triangle of P G P^T lands in the panels.
+//      structures nest), at most max_width columns wide, then relaxed
+//      amalgamation of small ones with their parents (a few stored zeros);
+//   6. per supernode: its rows, its parent and children in the supernodal
+//      tree, where its rows below sit among its parent's rows, the later
+//      supernodes that hold its rows below, the offsets of its panel of L,
+//      of its update matrix and of its diagonal block's inverse, and where
+//      every entry of the lower triangle of P G P^T lands in the panels.
 // Plain C++; deterministic (no hashing, no threads).
 #include "sparse_sym.h"
 
@@ -307,70 +309,136 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
         }
     }
 
-    // 5. fundamental supernodes, at most max_width wide
-    S.sn_first.clear();
-    S.col_sn.assign(n, 0);
+    // 5. fundamental supernodes, at most max_width wide ...
+    std::vector<int32_t> fund;  // first column of each fundamental supernode
     for (int64_t j = 0; j < n; ++j) {
         bool join = false;
-        if (j > 0 && !S.sn_first.empty()) {
-            const int64_t f = S.sn_first.back();
+        if (j > 0 && !fund.empty()) {
+            const int64_t f = fund.back();
             join = parent[j - 1] == j && nchild[j] == 1 && cs[j - 1].size() == cs[j].size() + 1 &&
                    j - f < max_width;
         }
-        if (!join) S.sn_first.push_back((int32_t)j);
-        S.col_sn[j] = (int32_t)S.sn_first.size() - 1;
+        if (!join) fund.push_back((int32_t)j);
+    }
+    const int64_t nf = (int64_t)fund.size();
+    fund.push_back((int32_t)n);
+    // ... then relaxed amalgamation, from the top of the tree down: a group
+    // of columns [F, L] (L the last column of its top supernode) takes the
+    // fundamental supernode just below F when that supernode's parent column
+    // lies in the group, while the group stays at most max_width wide and
+    // the explicit zeros it stores stay few (more are allowed in narrow
+    // groups, whose per-supernode costs dominate).  Rows of a group: [F, L]
+    // and the structure of L, which contains every merged column's structure.
+    S.exact_nnz_L = 0;
+    for (int64_t j = 0; j < n; ++j) S.exact_nnz_L += 1 + (int64_t)cs[j].size();
+    std::vector<int32_t> groups;  // first columns, descending
+    {
+        std::vector<int32_t> fsn(n);
+        for (int64_t t = 0; t < nf; ++t)
+            for (int32_t j = fund[t]; j < fund[t + 1]; ++j) fsn[j] = (int32_t)t;
+        auto exact = [&](int64_t t) {
+            int64_t e = 0;
+            for (int32_t j = fund[t]; j < fund[t + 1]; ++j) e += 1 + (int64_t)cs[j].size();
+            return e;
+        };
+        int64_t top = nf - 1;
+        while (top >= 0) {
+            const int32_t L = fund[top + 1] - 1;
+            int32_t F = fund[top];
+            const int64_t below = (int64_t)cs[L].size();
+            int64_t E = exact(top);
+            int64_t t = top - 1;
+            for (; t >= 0; --t) {
+                const int32_t lt = fund[t + 1] - 1;  // == F - 1
+                if (parent[lt] < F || parent[lt] > L) break;  // not a child of the group
+                const int64_t W = (int64_t)L - fund[t] + 1;
+                if (W > max_width) break;
+                const int64_t Et = E + exact(t);
+                const int64_t stored = W * (W + 1) / 2 + W * below;
+                const double z = 1.0 - (double)Et / (double)stored;
+                const bool ok = W <= 4 || (W <= 16 && z <= 0.5) || (W <= 32 && z <= 0.25) || z <= 0.1;
+                if (!ok) break;
+                E = Et;
+                F = fund[t];
+            }
+            groups.push_back(F);
+            top = t;
+        }
+    }
+    S.sn_first.assign(groups.rbegin(), groups.rend());
+    S.col_sn.assign(n, 0);
+    for (size_t g2 = 0; g2 < S.sn_first.size(); ++g2) {
+        const int32_t e2 = g2 + 1 < S.sn_first.size() ? S.sn_first[g2 + 1] : (int32_t)n;
+        for (int32_t j = S.sn_first[g2]; j < e2; ++j) S.col_sn[j] = (int32_t)g2;
     }
     const int64_t ns = (int64_t)S.sn_first.size();
     S.ns = ns;
     S.sn_first.push_back((int32_t)n);
 
-    // 6. rows, panel and inverse offsets, update and ancestor lists
+    // 6. rows, panel / update / inverse offsets, the supernodal tree, the
+    // positions of a supernode's rows below in its parent's rows
     S.rows_off.assign(ns + 1, 0);
     S.rows.clear();
     S.L_off.assign(ns + 1, 0);
     S.W_off.assign(ns + 1, 0);
+    S.U_off.assign(ns + 1, 0);
+    S.u_off.assign(ns + 1, 0);
+    S.sparent.assign(ns, -1);
     S.nnz_L = 0;
     S.flops = 0.0;
     S.max_height = 0;
-    for (int64_t s = 0; s < ns; ++s) {
-        const int32_t f = S.sn_first[s], l = S.sn_first[s + 1] - 1, w = l - f + 1;
+    for (int64_t sn = 0; sn < ns; ++sn) {
+        const int32_t f = S.sn_first[sn], l = S.sn_first[sn + 1] - 1, w = l - f + 1;
         for (int32_t c = f; c <= l; ++c) S.rows.push_back(c);
         S.rows.insert(S.rows.end(), cs[l].begin(), cs[l].end());
-        S.rows_off[s + 1] = (int64_t)S.rows.size();
-        const int64_t h = S.rows_off[s + 1] - S.rows_off[s];
+        S.rows_off[sn + 1] = (int64_t)S.rows.size();
+        const int64_t h = S.rows_off[sn + 1] - S.rows_off[sn], hu = h - w;
         S.max_height = std::max<int64_t>(S.max_height, h);
-        S.L_off[s + 1] = S.L_off[s] + ((h + 3) / 4 * 4) * w;
-        S.W_off[s + 1] = S.W_off[s] + (int64_t)w * w;
+        S.L_off[sn + 1] = S.L_off[sn] + ((h + 3) / 4 * 4) * w;
+        S.W_off[sn + 1] = S.W_off[sn] + (int64_t)w * w;
+        S.U_off[sn + 1] = S.U_off[sn] + ((hu + 3) / 4 * 4) * hu;
+        S.u_off[sn + 1] = S.u_off[sn] + hu;
         S.nnz_L += h * w - (int64_t)w * (w - 1) / 2;
         for (int32_t c = 0; c < w; ++c) {
             const double cc = (double)(h - c);  // entries in column f + c, diagonal included
             S.flops += cc * cc;
         }
+        if (parent[l] >= 0) S.sparent[sn] = S.col_sn[parent[l]];
     }
-    // D(s): supernodes d < s with a row in s's columns; A(d): supernodes
-    // above d holding its off-diagonal rows (both ascending)
-    S.d_off.assign(ns + 1, 0);
+    S.c_off.assign(ns + 1, 0);
+    for (int64_t sn = 0; sn < ns; ++sn)
+        if (S.sparent[sn] >= 0) S.c_off[S.sparent[sn] + 1] += 1;
+    for (int64_t sn = 0; sn < ns; ++sn) S.c_off[sn + 1] += S.c_off[sn];
+    S.clist.assign(S.c_off[ns], 0);
+    {
+        std::vector<int64_t> fill(S.c_off.begin(), S.c_off.end() - 1);
+        for (int64_t sn = 0; sn < ns; ++sn)
+            if (S.sparent[sn] >= 0) S.clist[fill[S.sparent[sn]]++] = (int32_t)sn;
+    }
+    S.rel.assign(S.u_off[ns], 0);
+    for (int64_t sn = 0; sn < ns; ++sn) {
+        const int32_t pa = S.sparent[sn];
+        if (pa < 0) continue;
+        const int32_t w = S.sn_first[sn + 1] - S.sn_first[sn];
+        const int32_t *pb = S.rows.data() + S.rows_off[pa], *pe = S.rows.data() + S.rows_off[pa + 1];
+        int64_t k = S.u_off[sn];
+        for (int64_t q = S.rows_off[sn] + w; q < S.rows_off[sn + 1]; ++q)
+            S.rel[k++] = (int32_t)(std::lower_bound(pb, pe, S.rows[q]) - pb);
+    }
+    // A(s): the supernodes holding s's rows below (ascending), for the backward solve
     S.a_off.assign(ns + 1, 0);
     S.alist.clear();
     for (int64_t d = 0; d < ns; ++d) {
         const int32_t w = S.sn_first[d + 1] - S.sn_first[d];
         int32_t lastsn = -1;
-        for (int64_t p = S.rows_off[d] + w; p < S.rows_off[d + 1]; ++p) {
-            const int32_t t = S.col_sn[S.rows[p]];
+        for (int64_t q = S.rows_off[d] + w; q < S.rows_off[d + 1]; ++q) {
+            const int32_t t = S.col_sn[S.rows[q]];
             if (t != lastsn) {
                 S.alist.push_back(t);
-                S.d_off[t + 1] += 1;
                 lastsn = t;
             }
         }
         S.a_off[d + 1] = (int64_t)S.alist.size();
-    }
-    for (int64_t s = 0; s < ns; ++s) S.d_off[s + 1] += S.d_off[s];
-    S.dlist.assign(S.d_off[ns], 0);
-    {
-        std::vector<int64_t> fill(S.d_off.begin(), S.d_off.end() - 1);
-        for (int64_t d = 0; d < ns; ++d)
-            for (int64_t p = S.a_off[d]; p < S.a_off[d + 1]; ++p) S.dlist[fill[S.alist[p]]++] = (int32_t)d;
     }
     // where each lower entry of P G P^T lands: panel of its column's
     // supernode, column j - f, local row = position of i among the rows

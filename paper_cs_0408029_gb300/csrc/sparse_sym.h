@@ -24,11 +24,18 @@ struct SparseSym {
     std::vector<int32_t> rows;       //   its own columns first, then the rows below
     std::vector<int64_t> L_off;      // ns + 1: panel s is ld x w, ld = rows rounded up to 4
     std::vector<int64_t> W_off;      // ns + 1: inverse of the diagonal block, w x w
-    std::vector<int64_t> d_off;      // ns + 1: dlist[d_off[s] ..] = supernodes updating s, ascending
-    std::vector<int32_t> dlist;
+    std::vector<int64_t> U_off;      // ns + 1: update matrix (rows below)^2, ld = rows below rounded up to 4
+    std::vector<int64_t> u_off;      // ns + 1: u_off[s] .. = one entry per row below (update
+                                     //   vectors of the forward solve, and rel)
+    std::vector<int32_t> rel;        // position of each row below among the parent's rows
+    std::vector<int32_t> sparent;    // supernodal tree, -1 at a root
+    std::vector<int64_t> c_off;      // ns + 1: clist[c_off[s] ..] = children of s, ascending
+    std::vector<int32_t> clist;
     std::vector<int64_t> a_off;      // ns + 1: alist[a_off[s] ..] = supernodes holding s's rows below
     std::vector<int32_t> alist;
-    int64_t nnz_L = 0;               // entries of L's structure (lower trapezoids of the panels)
+    int64_t nnz_L = 0;               // entries stored in the panels (lower trapezoids, with the
+                                     //   zeros that amalgamation adds)
+    int64_t exact_nnz_L = 0;         // entries of L's structure
     int64_t max_height = 0;          // rows of the tallest panel
     double flops = 0.0;              // sum over columns of (entries in the column)^2
     double analysis_ms = 0.0;        // host wall time of the analysis

@@ -47,13 +47,17 @@ def test_structure_matches_boolean_elimination(case):
     perm, parent, st = ts.sparse_analyze(p.m, p.n, p.row_ptr, p.col_idx)
     n = p.n
     assert np.array_equal(np.sort(perm), np.arange(n))
+    assert st["nnz_l_stored"] >= st["nnz_l"]
     g = _gram_pattern(p)
     pg = g[np.ix_(perm, perm)]
     assert st["nnz_gram"] == np.tril(pg).sum()
     L = _elimination_fill(pg)
     assert st["nnz_l"] == L.sum()
     counts = L.sum(axis=0)
-    assert st["factor_flops"] == pytest.approx(float((counts.astype(np.float64) ** 2).sum()))
+    # without merging (one column per supernode) the stored structure is L's own
+    _, _, narrow = ts.sparse_analyze(p.m, p.n, p.row_ptr, p.col_idx, max_width=1)
+    assert narrow["nnz_l_stored"] == narrow["nnz_l"] == L.sum()
+    assert narrow["factor_flops"] == pytest.approx(float((counts.astype(np.float64) ** 2).sum()))
     # elimination tree: the first row below the diagonal in each column of L
     for j in range(n):
         below = np.nonzero(L[j + 1:, j])[0]
