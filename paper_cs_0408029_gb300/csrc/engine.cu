@@ -423,9 +423,12 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 if (steps >= o.max_refine || (steps > 4 && d > prev))
                     return d <= 1e-9 * xn ? TSNNLS_OK : TSNNLS_ENOCONV;
                 if (allow_settle && d <= 0.1 * prev) {
-                    // contraction <= 0.1 observed: the error left in x is below
-                    // d / 9 in the max norm; E allows a factor of 4.5 on that
-                    const double E = 0.5 * d + 1e-15 * xn;
+                    // contraction rho = d / prev <= 0.1 observed: while it holds
+                    // the error left in x is about rho d / (1 - rho) in the max
+                    // norm; E allows 20 times that, at most 0.5 d, plus the
+                    // rounding floor
+                    const double rho = d / prev;
+                    const double E = std::min(0.5, 20.0 * rho) * d + 1e-15 * xn;
                     prof_begin(lane, TSNNLS_PHASE_VECTOR);
                     e = launch_settled(s, n, inF, x, sv, cbound, E, o.zero_tol, lane.st_dev);
                     prof_end(lane, 25.0 * n, 0.0);

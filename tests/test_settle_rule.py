@@ -2,9 +2,12 @@
 
 Before the last pivot only the signs of x_F and y_G after the 1e-12 zeroing
 enter the method (Section 3).  The solver stops a pivot's refinement once the
-observed contraction is <= 0.1 and no entry lies within its error bound of 0
-or +-1e-12: E = 0.5 ||dx||_inf + 1e-15 ||x_F||_inf for x_F, and c_i E for
-s_i = a_i^T (b - A x), c = |A|^T |A| 1.  These tests restate that rule on top
+observed contraction rho = ||dx||_inf / ||dx_prev||_inf is <= 0.1 and no entry
+lies within its error bound of 0 or +-1e-12:
+E = min(0.5, 20 rho) ||dx||_inf + 1e-15 ||x_F||_inf for x_F (the error left
+after the step is about rho ||dx|| / (1 - rho) while the contraction holds;
+the bound allows 20 times that, at most 0.5 ||dx||_inf), and
+c_i E for s_i = a_i^T (b - A x), c = |A|^T |A| 1.  These tests restate that rule on top
 of an FP32 factor and FP64 residuals in numpy and check that whenever it
 fires, every decision equals the one of the exact FP64 solution, and that it
 does fire well before full accuracy on ordinary problems.
@@ -46,7 +49,7 @@ def _refine_until_settled(a, b, F, max_steps=30):
         d = np.max(np.abs(dx))
         xn = np.max(np.abs(x[F]))
         if prev is not None and d <= 0.1 * prev:
-            E = 0.5 * d + 1e-15 * xn
+            E = min(0.5, 20.0 * d / prev) * d + 1e-15 * xn
             inF = np.zeros(n, dtype=bool)
             inF[F] = True
             v = np.where(inF, np.abs(x), np.abs(s))
@@ -80,6 +83,28 @@ def test_settled_decisions_equal_exact_ones(seed):
     inF[F] = True
     assert np.array_equal(_categories(x[inF]), _categories(xe[inF]))
     assert np.array_equal(_categories(-s[~inF]), _categories(-se[~inF]))
+
+
+def test_rule_fires_after_one_correction_on_a_wide_sweep():
+    """Random intermediate pivots of well-conditioned sparse problems (an FP32
+    factor leaves about 1e-6 relative error): the rule fires after the first
+    correction, and every decision equals the exact solution's."""
+    fired_early = 0
+    for seed in range(30):
+        rng = np.random.default_rng(300 + seed)
+        p = workloads.random_sparse(300, 140, 0.06, seed=400 + seed, zero_frac=0.4, noise=0.05)
+        a = p.dense()
+        F = np.sort(rng.permutation(p.n)[: int(rng.integers(20, p.n))])
+        got = _refine_until_settled(a, p.b, F)
+        assert got is not None, seed
+        x, s, steps = got
+        fired_early += steps <= 2
+        xe, se = _exact(a, p.b, F)
+        inF = np.zeros(p.n, dtype=bool)
+        inF[F] = True
+        assert np.array_equal(_categories(x[inF]), _categories(xe[inF])), seed
+        assert np.array_equal(_categories(-s[~inF]), _categories(-se[~inF])), seed
+    assert fired_early >= 25
 
 
 @pytest.mark.parametrize("kappa", [1e1, 1e2, 1e3])
