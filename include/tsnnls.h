@@ -235,13 +235,25 @@ int tsnnls_queue_stats_read(tsnnls_ctx *ctx, tsnnls_queue_stats *out);
  * (m[i] doubles, device) and x_i = x_out[i] (n[i] doubles, device).  The
  * pointer arrays a, b, x_out, m and n are host arrays of `count` entries.
  * All pivot iterations of all problems run in one persistent kernel launched
- * from a captured CUDA graph; A^T A is formed by one batched GEMM.  status_out
+ * from a captured CUDA graph; A^T A is formed by one batched GEMM.  MIXED
+ * refines each intermediate pivot only until its sign decisions are settled
+ * (opts.full_refine = 1: every pivot to rel_tol), as tsnnls_solve does.  status_out
  * (host, count entries, may be NULL) receives each problem's status.
  * Returns TSNNLS_OK if every problem succeeded, else the first failure. */
 int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
                              const float *const *a, const double *const *b,
                              double *const *x_out, const tsnnls_opts *opts,
                              int32_t *status_out, tsnnls_info *info);
+
+/* tsnnls_solve_batch_dense with each problem's pivot trace: trace (host
+ * array of count host pointers, may be NULL; an entry may be NULL) receives
+ * for problem i up to trace_cap (1 .. 2^20) rows of six int64 in the layout
+ * of tsnnls_solve_ex (infeasible count, N before the branch, p after it,
+ * branch, |F| after the exchange, the index a single exchange moved). */
+int tsnnls_solve_batch_dense_ex(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
+                                const float *const *a, const double *const *b, double *const *x_out,
+                                const tsnnls_opts *opts, int32_t *status_out, tsnnls_info *info,
+                                int64_t *const *trace, int64_t trace_cap);
 
 /* Autotuner of the batched path's Cholesky panel width.  For each problem
  * size bucket (n <= 64, 128, 256, 512, 1024) it times the batched solve of a

@@ -28,7 +28,7 @@ EXPORTS = (
     "tsnnls_chol_solve", "tsnnls_spmv", "tsnnls_profile_enable", "tsnnls_profile_read",
     "tsnnls_chol_solve_noalloc", "tsnnls_batch_autotune", "tsnnls_batch_set_panel",
     "tsnnls_queue_stats_read", "tsnnls_wait_probe", "tsnnls_submit_batch",
-    "tsnnls_batch_member_info", "tsnnls_sparse_analyze",
+    "tsnnls_batch_member_info", "tsnnls_sparse_analyze", "tsnnls_solve_batch_dense_ex",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
         "tsnnls_wait": ([p, i64, i64, ctypes.POINTER(Info)], ctypes.c_int),
         "tsnnls_solve_batch_dense": ([p, i32, p, p, p, p, p, ctypes.POINTER(Opts), p,
                                       ctypes.POINTER(Info)], ctypes.c_int),
+        "tsnnls_solve_batch_dense_ex": ([p, i32, p, p, p, p, p, ctypes.POINTER(Opts), p,
+                                         ctypes.POINTER(Info), p, i64], ctypes.c_int),
         "tsnnls_gram": ([p, ctypes.POINTER(CSR), p, i32, p, i64, p], ctypes.c_int),
         "tsnnls_gather": ([p, i32, p, i64, p, i64, p, i64], ctypes.c_int),
         "tsnnls_cholesky": ([p, i32, p, i64, i64, ctypes.POINTER(i32)], ctypes.c_int),
@@ -358,9 +360,10 @@ class Context:
         _check(self._lib.tsnnls_queue_stats_read(self._h, ctypes.byref(q)), "queue_stats")
         return {f: getattr(q, f) for f, _ in q._fields_}
 
-    def solve_batch_dense(self, a_list, b_list, x_list, opts=None, **kw):
+    def solve_batch_dense(self, a_list, b_list, x_list, opts=None, trace_cap=0, **kw):
         """Dense batched solve; a_list: CUDA float32 [m_i, n_i] row-major, b_list,
-        x_list: CUDA float64.  Returns (status array, Info)."""
+        x_list: CUDA float64.  Returns (status, status array, Info), plus the
+        list of per-problem pivot traces [iters_i, 6] when trace_cap > 0."""
         o = opts if opts is not None else default_opts(**kw)
         cnt = len(a_list)
         ms = np.array([a.shape[0] for a in a_list], dtype=np.int32)
@@ -370,10 +373,17 @@ class Context:
         xp = np.array([t.data_ptr() for t in x_list], dtype=np.uint64)
         stat = np.zeros(cnt, dtype=np.int32)
         info = Info()
-        st = self._lib.tsnnls_solve_batch_dense(self._h, cnt, _np_ptr(ms), _np_ptr(ns), _np_ptr(ap),
-                                                _np_ptr(bp), _np_ptr(xp), ctypes.byref(o),
-                                                _np_ptr(stat), ctypes.byref(info))
-        return st, stat, info
+        if trace_cap <= 0:
+            st = self._lib.tsnnls_solve_batch_dense(self._h, cnt, _np_ptr(ms), _np_ptr(ns), _np_ptr(ap),
+                                                    _np_ptr(bp), _np_ptr(xp), ctypes.byref(o),
+                                                    _np_ptr(stat), ctypes.byref(info))
+            return st, stat, info
+        trs = [np.full((trace_cap, 6), -7, dtype=np.int64) for _ in range(cnt)]
+        tp = np.array([t.ctypes.data for t in trs], dtype=np.uint64)
+        st = self._lib.tsnnls_solve_batch_dense_ex(self._h, cnt, _np_ptr(ms), _np_ptr(ns), _np_ptr(ap),
+                                                   _np_ptr(bp), _np_ptr(xp), ctypes.byref(o),
+                                                   _np_ptr(stat), ctypes.byref(info), _np_ptr(tp), trace_cap)
+        return st, stat, info, [t[t[:, 0] > 0] for t in trs]
 
     def batch_autotune(self, precision=MIXED, per_bucket=64):
         nb = np.zeros(5, dtype=np.int32)

@@ -21,6 +21,7 @@
 #include <numeric>
 #include <vector>
 
+#include "dense_block.cuh"
 #include "engine.h"
 
 namespace tsnnls {
@@ -33,10 +34,12 @@ struct BatchProb {
     void *S;         // n x ld factor workspace (float or double)
     double *Gd;      // FP64 path: n x ld lower Gram in FP64 (else null)
     double *c, *y, *s, *r;
+    double *cb;      // MIXED: c = |A|^T (|A| 1), the settle test's bound (else null)
     void *rhs;       // n (factor type)
     int32_t *F;
     uint8_t *inF;
-    int32_t m, n, ld, nb;
+    int64_t *trace;  // optional pivot trace, trace_cap rows of 6 (else null)
+    int32_t m, n, ld, nb, trace_cap;
 };
 
 struct BatchOut {
@@ -48,6 +51,7 @@ struct BatchParams {
     double zero_tol, rel_tol;
     int32_t p_max, max_iter, max_refine, mixed;
     int32_t scratch_bytes;  // bytes of the panel area free outside the factorisation
+    int32_t settle;         // MIXED: intermediate pivots stop refining once their signs are settled
 };
 
 // ---------------------------------------------------------------------------
@@ -172,11 +176,111 @@ constexpr int kBT = 512;            // threads per CTA
 constexpr int kBWarps = kBT / 32;
 constexpr int kMaxPanelRows = 1024;  // n <= 1024 for this path
 
+// pitch of the shared-memory panel rows P[row * pitch + l]
 template <typename T>
-struct BSmem {
-    // panel rows staged for the trailing update: P[row][l], padded
-    static constexpr size_t panel_bytes(int nb) { return sizeof(T) * (size_t)kMaxPanelRows * (nb + 1); }
-};
+__host__ __device__ __forceinline__ int panel_pitch(int nb) {
+    return (sizeof(T) == 4 && nb == 32) ? 36 : nb + 1;
+}
+
+// ---- trailing update on the tensor cores (FP32 path, panel width 32) ------
+// C(R0 + i, R0 + j) -= sum_l X(i, l) X(j, l) on the lower triangle, X the
+// 32-column panel in shared memory (pitch 36).  Each warp takes 32 x 32
+// tiles: 2 x 4 mma.sync.m16n8k8 TF32 tiles, K = 32 in four steps.  TF32 keeps
+// 10 mantissa bits, so every operand is split into hi (rounded to TF32) and
+// lo (the rest, rounded to TF32) and the product is accumulated as
+// hi*hi + hi*lo + lo*hi in FP32, which carries about FP32 accuracy.
+// Fragment layout of m16n8k8 (g = lane / 4, t = lane % 4): A (16 x 8)
+// a0 = (g, t), a1 = (g + 8, t), a2 = (g, t + 4), a3 = (g + 8, t + 4);
+// B (8 x 8) b0 = (t, g), b1 = (t + 4, g); C (16 x 8) c0 = (g, 2t),
+// c1 = (g, 2t + 1), c2 = (g + 8, 2t), c3 = (g + 8, 2t + 1).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __noinline__ void tc_trailing_update(float *S, int lds, int R0, int nr, const float *panel) {
+    constexpr int PP = 36;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int nt = (nr + 31) / 32, ntiles = nt * (nt + 1) / 2;
+    auto X = [&](int r, int l) -> float { return r < nr ? panel[r * PP + l] : 0.f; };
+    for (int tb = warp; tb < ntiles; tb += kBWarps) {
+        int I = (int)((sqrtf(8.f * tb + 1.f) - 1.f) * 0.5f);
+        while (I * (I + 1) / 2 > tb) --I;
+        while ((I + 1) * (I + 2) / 2 <= tb) ++I;
+        const int J = tb - I * (I + 1) / 2;
+        const int i0 = I * 32, j0 = J * 32;
+        float acc[2][4][4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+#pragma unroll
+        for (int k0 = 0; k0 < 32; k0 += 8) {
+            uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int ra = i0 + 16 * a + g;
+                split_tf32(X(ra, k0 + t), ah[a][0], al[a][0]);
+                split_tf32(X(ra + 8, k0 + t), ah[a][1], al[a][1]);
+                split_tf32(X(ra, k0 + t + 4), ah[a][2], al[a][2]);
+                split_tf32(X(ra + 8, k0 + t + 4), ah[a][3], al[a][3]);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int cj = j0 + 8 * b + g;  // B(l, j) = X(j, l)
+                split_tf32(X(cj, k0 + t), bh[b][0], bl[b][0]);
+                split_tf32(X(cj, k0 + t + 4), bh[b][1], bl[b][1]);
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    mma_tf32_16x8x8(acc[a][b], ah[a], bh[b]);
+                    mma_tf32_16x8x8(acc[a][b], ah[a], bl[b]);
+                    mma_tf32_16x8x8(acc[a][b], al[a], bh[b]);
+                }
+        }
+        // all 32 loads of C before any store (a store could alias a later
+        // load as far as the compiler can tell, which would serialise every
+        // read-modify-write on its memory latency)
+        float cv[2][4][4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = i0 + 16 * a + g + (q >= 2 ? 8 : 0);
+                    const int c = j0 + 8 * b + 2 * t + (q & 1);
+                    cv[a][b][q] = (r < nr && c < nr && r >= c) ? S[(R0 + r) + (int64_t)(R0 + c) * lds] : 0.f;
+                }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = i0 + 16 * a + g + (q >= 2 ? 8 : 0);
+                    const int c = j0 + 8 * b + 2 * t + (q & 1);
+                    if (r < nr && c < nr && r >= c)
+                        S[(R0 + r) + (int64_t)(R0 + c) * lds] = cv[a][b][q] - acc[a][b][q];
+                }
+    }
+}
 
 __device__ __forceinline__ double block_reduce_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -238,14 +342,47 @@ __device__ __forceinline__ int block_reduce_imax(int v, int *sh) {
     return sh[0];
 }
 
+// Warp 0: factor the kb x kb (kb <= 32) diagonal block at (K, K) of S in
+// registers (lane = row, the warp step of dense_block.cuh: the pivot chain
+// by shuffles, no CTA barrier); L into S and into diag (diag[c * 65 + r]).
+// Returns 0 or the 1-based column of the first non-positive pivot.
+template <typename T>
+__device__ __noinline__ int warp_factor_block(T *S, int lds, int K, int kb, T *diag, T (*col)[32]) {
+    const int lane = threadIdx.x & 31;
+    WarpCholL<T> s;
+#pragma unroll
+    for (int c = 0; c < 32; ++c)  // rows past kb hold the identity, so they factor to it and touch nothing
+        s.a[c] = (lane < kb && c <= lane) ? S[(K + lane) + (int64_t)(K + c) * lds] : (c == lane ? T(1) : T(0));
+    int bad = 0;
+    warp_chol_step_l<T, 0>(s, col, lane, bad, __shfl_sync(0xffffffffu, s.a[0], 0));
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+        if (lane < kb && c <= lane) {
+            S[(K + lane) + (int64_t)(K + c) * lds] = s.a[c];
+            diag[c * 65 + lane] = s.a[c];
+        }
+    return bad;
+}
+
 // In-CTA blocked right-looking Cholesky of the k x k lower matrix S (lds),
-// panel width nb <= 64.  Returns 0 or 1 + the failing column.
+// panel width nb <= 64.  Returns 0 or 1 + the failing column.  With nb = 32
+// warp 0 factors each diagonal block in registers; other widths factor it
+// column by column with the whole CTA.
 template <typename T>
 __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int *sh_int) {
+    __shared__ __align__(16) T col[2][32];
     const int tid = threadIdx.x;
     int info = 0;
     for (int K = 0; K < k; K += nb) {
         const int kb = min(nb, k - K);
+        if (nb == 32) {
+            if (tid < 32) {
+                const int bad = warp_factor_block<T>(S, lds, K, kb, diag, col);
+                if (tid == 0) sh_int[0] = (bad && !info) ? K + bad : info;
+            }
+            __syncthreads();
+            info = sh_int[0];
+        } else {
         // diagonal block in shared memory, factored column by column
         for (int e = tid; e < kb * kb; e += kBT) {
             const int c = e / kb, r = e % kb;
@@ -278,20 +415,64 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
             const int c = e / kb, r = e % kb;
             if (r >= c) S[(K + r) + (int64_t)(K + c) * lds] = diag[c * 65 + r];
         }
+        }
         // panel: X L_KK^T = B for rows below, one thread per row, into smem
+        // (pitch PP: 36 for the tensor-core update's fragment loads, whose rows
+        // then fall on distinct banks; columns kb..nb of the last panel are 0)
         const int R0 = K + kb, nr = k - R0;
-        // (the row's kb entries are loaded into the panel first, all in flight)
-        for (int r = tid; r < nr; r += kBT) {
-            for (int c = 0; c < kb; ++c) panel[r * (nb + 1) + c] = S[(R0 + r) + (int64_t)(K + c) * lds];
-            for (int c = 0; c < kb; ++c) {
-                T s = panel[r * (nb + 1) + c];
-                for (int l = 0; l < c; ++l) s -= panel[r * (nb + 1) + l] * diag[l * 65 + c];
-                s /= diag[c * 65 + c];
-                panel[r * (nb + 1) + c] = s;
+        const int PP = panel_pitch<T>(nb);
+        // (the row's entries are loaded 16 at a time into registers, all 16 in
+        // flight, then stored to the panel)
+        if (nb == 32) {
+            // the row in registers, L_KK read from shared memory (the same
+            // entry for every lane: a broadcast)
+            for (int r = tid; r < nr; r += kBT) {
+                T xr[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) xr[c] = c < kb ? S[(R0 + r) + (int64_t)(K + c) * lds] : T(0);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    if (c < kb) {
+                        T s = xr[c];
+#pragma unroll
+                        for (int l = 0; l < c; ++l) s -= xr[l] * diag[l * 65 + c];
+                        xr[c] = s / diag[c * 65 + c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    panel[r * PP + c] = xr[c];
+                    if (c < kb) S[(R0 + r) + (int64_t)(K + c) * lds] = xr[c];
+                }
             }
-            for (int c = 0; c < kb; ++c) S[(R0 + r) + (int64_t)(K + c) * lds] = panel[r * (nb + 1) + c];
+        } else {
+        for (int r = tid; r < nr; r += kBT) {
+            for (int c0 = 0; c0 < nb; c0 += 16) {
+                T rowv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    rowv[u] = c0 + u < kb ? S[(R0 + r) + (int64_t)(K + c0 + u) * lds] : T(0);
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    if (c0 + u < nb) panel[r * PP + c0 + u] = rowv[u];
+            }
+            for (int c = 0; c < kb; ++c) {
+                T s = panel[r * PP + c];
+                for (int l = 0; l < c; ++l) s -= panel[r * PP + l] * diag[l * 65 + c];
+                s /= diag[c * 65 + c];
+                panel[r * PP + c] = s;
+            }
+            for (int c = 0; c < kb; ++c) S[(R0 + r) + (int64_t)(K + c) * lds] = panel[r * PP + c];
+        }
         }
         __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            if (nb == 32 && nr > 0) {
+                tc_trailing_update(S, lds, R0, nr, panel);
+                __syncthreads();
+                continue;
+            }
+        }
         // trailing update of the lower triangle, 4 x 4 register tiles over 64 x 64 tiles
         if (nr > 0) {
             const int t64 = (nr + 63) / 64;
@@ -317,12 +498,12 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         const int rr = ri + ty + 16 * a;
-                        av[a] = rr < nr ? panel[rr * (nb + 1) + l] : T(0);
+                        av[a] = rr < nr ? panel[rr * PP + l] : T(0);
                     }
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const int cc = cj + tx + 16 * b;
-                        bv[b] = cc < nr ? panel[cc * (nb + 1) + l] : T(0);
+                        bv[b] = cc < nr ? panel[cc * PP + l] : T(0);
                     }
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
@@ -566,8 +747,8 @@ __global__ void __launch_bounds__(kBT, 1)
     T *panel = reinterpret_cast<T *>(smem_raw + sizeof(T) * 64 * 65);  // up to 1024 x (nb+1)
     __shared__ double shd[kBWarps];
     __shared__ int shi[kBWarps];
-    __shared__ int sh_p, sh_dec, sh_k, sh_big;
-    __shared__ int64_t sh_N;
+    __shared__ int sh_p, sh_dec, sh_k, sh_big, sh_ninf;
+    __shared__ int64_t sh_N, sh_Nprev;
     __shared__ int sh_pcount, sh_iters;
     const int tid = threadIdx.x;
 
@@ -594,8 +775,94 @@ __global__ void __launch_bounds__(kBT, 1)
             sh_pcount = prm.p_max;
             sh_iters = 0;
         }
+        if (prm.mixed && prm.settle) {
+            // the settle test's bound c = |A|^T (|A| 1); P.r serves as scratch
+            // until the first residual
+            const int lane = tid & 31, warp = tid >> 5;
+            for (int i = warp; i < P.m; i += kBWarps) {
+                double v = 0.0;
+                for (int j = lane; j < n; j += 32) v += fabs((double)P.A[(int64_t)i * n + j]);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) P.r[i] = v;
+            }
+            __syncthreads();
+            for (int j = tid; j < n; j += kBT) {
+                double v = 0.0;
+                for (int i = 0; i < P.m; ++i) v += fabs((double)P.A[(int64_t)i * n + j]) * P.r[i];
+                P.cb[j] = v;
+            }
+        }
         __syncthreads();
         int k = 0;
+        bool open = false;    // the last pivot stopped refining once its signs were settled
+        double last_dm = 0.0;  // its last correction
+        // refinement of the current pivot's x_F on its factor (MIXED: FP32
+        // solves, FP64-accurate residuals; FP64: only the residual for y_G).
+        // allow_settle: before the last pivot only the signs matter (Section
+        // 3), so the loop may stop once the contraction rho observed between
+        // corrections bounds the error left (E = min(0.5, 20 rho) ||dx|| +
+        // 1e-15 ||x_F||, c_j E on s_j) below every entry's distance to 0 and
+        // +-zero_tol -- the rule of the single-problem path.  Returns 1 then,
+        // 0 once converged to rel_tol, -1 on failure (status set).
+        auto refine_loop = [&](bool allow_settle, double prev, int steps) -> int {
+            const int lds = P.ld;
+            bool conv = !prm.mixed || k == 0;
+            bool check = false;
+            double E = 0.0;
+            for (;;) {
+                if (prm.mixed) {
+                    // in-loop steps need s on F only; a settle check and the
+                    // last pass all of it (y_G)
+                    cta_residual_ff(P, k, panel, prm.scratch_bytes);
+                    cta_atr_ff(P, conv || check, panel, prm.scratch_bytes);
+                    flops += 2.0 * P.m * ((double)k + (conv || check ? n : k));
+                } else {
+                    cta_residual(P, k);
+                    cta_atr(P);
+                    flops += 2.0 * P.m * ((double)k + n);
+                }
+                if (conv) return 0;
+                if (check) {
+                    int unsettled = 0;
+                    for (int j = tid; j < n; j += kBT) {
+                        const bool f = P.inF[j] != 0;
+                        const double v = fabs(f ? P.x[j] : P.s[j]);
+                        const double e = f ? E : P.cb[j] * E;
+                        if (!(v >= prm.zero_tol + e || v + e < prm.zero_tol)) ++unsettled;
+                    }
+                    if (block_reduce_isum(unsettled, shi) == 0) return 1;
+                    check = false;
+                }
+                for (int a = tid; a < k; a += kBT) rhs[a] = (T)P.s[P.F[a]];
+                __syncthreads();
+                cta_chol_solve<T>(S, k, lds, rhs);
+                flops += 2.0 * (double)k * k;
+                double dm = 0.0, xm = 0.0;
+                for (int a = tid; a < k; a += kBT) {
+                    const int j = P.F[a];
+                    const double dd = (double)rhs[a];
+                    const double xn = P.x[j] + dd;
+                    P.x[j] = xn;
+                    dm = fmax(dm, fabs(dd));
+                    xm = fmax(xm, fabs(xn));
+                }
+                dm = block_reduce_max(dm, shd);
+                xm = block_reduce_max(xm, shd);
+                ++steps;
+                ++refine;
+                last_dm = dm;
+                if (dm <= prm.rel_tol * xm) conv = true;
+                else if (steps > 2 && dm > 0.5 * prev && dm <= 1e-9 * xm) conv = true;
+                else if (steps >= prm.max_refine || (steps > 4 && dm > prev)) {
+                    if (dm <= 1e-9 * xm) conv = true;
+                    else { status = TSNNLS_ENOCONV; return -1; }
+                } else if (allow_settle && dm <= 0.1 * prev) {
+                    E = fmin(0.5, 20.0 * dm / prev) * dm + 1e-15 * xm;
+                    check = true;
+                }
+                prev = dm;
+            }
+        };
         for (;;) {
             // zeroing (after the first pivot), infeasible count, largest index
             const bool zero = sh_iters > 0;
@@ -623,6 +890,8 @@ __global__ void __launch_bounds__(kBT, 1)
             const int big = block_reduce_imax(largest, shi);
             if (tid == 0) {
                 int d;
+                sh_ninf = ninf;
+                sh_Nprev = sh_N;
                 if (ninf == 0) d = -1;
                 else if (sh_iters >= prm.max_iter) d = -2;
                 else if (ninf < sh_N) { sh_N = ninf; sh_pcount = prm.p_max; d = 0; }
@@ -633,6 +902,15 @@ __global__ void __launch_bounds__(kBT, 1)
             }
             __syncthreads();
             const int d = sh_dec;
+            if (d == -1 && open) {
+                // feasible: that was the last pivot, refined on to rel_tol now;
+                // its decisions were settled, so the test passes again
+                open = false;
+                if (refine_loop(false, last_dm, 0) < 0) break;
+                for (int j = tid; j < n; j += kBT) P.y[j] = P.inF[j] ? 0.0 : -P.s[j];
+                __syncthreads();
+                continue;
+            }
             if (d == -1) break;
             if (d == -2) { status = TSNNLS_EMAXITER; break; }
             if (d == 2) {
@@ -654,6 +932,15 @@ __global__ void __launch_bounds__(kBT, 1)
                 }
                 if (tid == 0) {
                     sh_k = base;
+                    if (P.trace && sh_iters < P.trace_cap) {
+                        int64_t *tr = P.trace + 6 * (int64_t)sh_iters;
+                        tr[0] = sh_ninf;
+                        tr[1] = sh_Nprev;
+                        tr[2] = sh_pcount;
+                        tr[3] = sh_dec;
+                        tr[4] = base;
+                        tr[5] = sh_dec == 2 ? sh_big : -1;
+                    }
                     sh_iters += 1;
                 }
             }
@@ -678,47 +965,13 @@ __global__ void __launch_bounds__(kBT, 1)
                 __syncthreads();
                 ++refine;
             }
-            double prev = 0.0;
-            bool conv = !prm.mixed || k == 0;
-            int steps = 1;
-            for (;;) {
-                if (prm.mixed) {
-                    // in-loop steps need s on F only; the last pass all of it (y_G)
-                    cta_residual_ff(P, k, panel, prm.scratch_bytes);
-                    cta_atr_ff(P, conv, panel, prm.scratch_bytes);
-                    flops += 2.0 * P.m * ((double)k + (conv ? n : k));
-                } else {
-                    cta_residual(P, k);
-                    cta_atr(P);
-                    flops += 2.0 * P.m * ((double)k + n);
-                }
-                if (conv) break;
-                for (int a = tid; a < k; a += kBT) rhs[a] = (T)P.s[P.F[a]];
-                __syncthreads();
-                cta_chol_solve<T>(S, k, lds, rhs);
-                flops += 2.0 * (double)k * k;
-                double dm = 0.0, xm = 0.0;
-                for (int a = tid; a < k; a += kBT) {
-                    const int j = P.F[a];
-                    const double dd = (double)rhs[a];
-                    const double xn = P.x[j] + dd;
-                    P.x[j] = xn;
-                    dm = fmax(dm, fabs(dd));
-                    xm = fmax(xm, fabs(xn));
-                }
-                dm = block_reduce_max(dm, shd);
-                xm = block_reduce_max(xm, shd);
-                ++steps;
-                ++refine;
-                if (dm <= prm.rel_tol * xm) conv = true;
-                else if (steps > 2 && dm > 0.5 * prev && dm <= 1e-9 * xm) conv = true;
-                else if (steps >= prm.max_refine || (steps > 4 && dm > prev)) {
-                    if (dm <= 1e-9 * xm) conv = true;
-                    else { status = TSNNLS_ENOCONV; break; }
-                }
-                prev = dm;
-            }
-            if (status != TSNNLS_OK) break;
+            // the first solve's correction is x_F itself
+            double x0 = 0.0;
+            for (int a = tid; a < k; a += kBT) x0 = fmax(x0, fabs(P.x[P.F[a]]));
+            x0 = block_reduce_max(x0, shd);
+            const int rr = refine_loop(prm.mixed && prm.settle, x0, 1);
+            if (rr < 0) break;
+            open = rr == 1;
             // Eq. 5: y_G = -s_G
             for (int j = tid; j < n; j += kBT) P.y[j] = P.inF[j] ? 0.0 : -P.s[j];
             __syncthreads();
@@ -753,13 +1006,14 @@ static int pick_nb(int n, bool mixed) {
 
 size_t batch_smem_bytes(bool mixed, int max_nb) {
     const size_t t = mixed ? sizeof(float) : sizeof(double);
-    return t * 64 * 65 + t * (size_t)kMaxPanelRows * (max_nb + 1);
+    const int pitch = std::max(max_nb + 1, mixed && max_nb >= 32 ? 36 : 0);
+    return t * 64 * 65 + t * (size_t)kMaxPanelRows * pitch;
 }
 
 int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const int32_t *n,
                     const float *const *a, const double *const *b, double *const *x,
                     const tsnnls_opts &o, int32_t *status_out, tsnnls_info *info,
-                    const int *nb_override) {
+                    const int *nb_override, int64_t *const *trace, int64_t trace_cap) {
     const bool mixed = o.precision == TSNNLS_MIXED;
     const size_t tsz = mixed ? sizeof(float) : sizeof(double);
     cudaStream_t s = lane.stream;
@@ -781,9 +1035,11 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
         bytes += up(tsz * (size_t)n[i] * ld);                     // S
         if (!mixed) bytes += up(sizeof(double) * (size_t)n[i] * ld);  // Gd
         bytes += 3 * up(sizeof(double) * n[i]);                   // c, y, s
+        if (mixed) bytes += up(sizeof(double) * n[i]);            // cb
         bytes += up(sizeof(double) * m[i]);                       // r
         bytes += up(tsz * n[i]);                                  // rhs
         bytes += up(sizeof(int32_t) * n[i]) + up(n[i]);           // F, inF
+        if (trace) bytes += up(sizeof(int64_t) * 6 * (size_t)trace_cap);  // pivot trace
         off[q] = total;
         total += bytes;
         BatchProb &P = hp[q];
@@ -820,10 +1076,13 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
         P.c = reinterpret_cast<double *>(take(sizeof(double) * P.n));
         P.y = reinterpret_cast<double *>(take(sizeof(double) * P.n));
         P.s = reinterpret_cast<double *>(take(sizeof(double) * P.n));
+        P.cb = mixed ? reinterpret_cast<double *>(take(sizeof(double) * P.n)) : nullptr;
         P.r = reinterpret_cast<double *>(take(sizeof(double) * P.m));
         P.rhs = take(tsz * P.n);
         P.F = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * P.n));
         P.inF = reinterpret_cast<uint8_t *>(take(P.n));
+        P.trace = trace ? reinterpret_cast<int64_t *>(take(sizeof(int64_t) * 6 * (size_t)trace_cap)) : nullptr;
+        P.trace_cap = trace ? (int32_t)trace_cap : 0;
     }
     BatchProb *d_probs = reinterpret_cast<BatchProb *>(arena + total);
     BatchOut *d_out = reinterpret_cast<BatchOut *>(arena + total + desc_bytes);
@@ -832,7 +1091,8 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
     std::vector<BatchOut> hout(count);
     BatchParams prm{o.zero_tol, o.rel_tol, o.p_max,
                     o.max_iter > 0 ? o.max_iter : 0, o.max_refine, mixed ? 1 : 0,
-                    (int32_t)((mixed ? sizeof(float) : sizeof(double)) * (size_t)kMaxPanelRows * (max_nb + 1))};
+                    (int32_t)(batch_smem_bytes(mixed, max_nb) - (mixed ? sizeof(float) : sizeof(double)) * 64 * 65),
+                    mixed && o.full_refine == 0 ? 1 : 0};
     int status = TSNNLS_OK;
     const size_t smem = batch_smem_bytes(mixed, max_nb);
     cudaGraph_t graph = nullptr;
@@ -844,6 +1104,10 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
         if (!items.empty())
             e = cudaMemcpyAsync(d_items, items.data(), sizeof(GramItem) * items.size(),
                                 cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) break;
+        if (trace)  // rows past a problem's last pivot read -1 (a real row has a count >= 1)
+            for (int q = 0; q < count && e == cudaSuccess; ++q)
+                e = cudaMemsetAsync(hp[q].trace, 0xFF, sizeof(int64_t) * 6 * (size_t)trace_cap, s);
         if (e != cudaSuccess) break;
         if (prm.max_iter == 0) {
             int nmax = 0;
@@ -886,6 +1150,13 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
         if (e != cudaSuccess) break;
         e = cudaMemcpyAsync(hout.data(), d_out, sizeof(BatchOut) * count, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) break;
+        if (trace) {
+            for (int q = 0; q < count && e == cudaSuccess; ++q)
+                if (trace[order[q]])
+                    e = cudaMemcpyAsync(trace[order[q]], hp[q].trace, sizeof(int64_t) * 6 * (size_t)trace_cap,
+                                        cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) break;
+        }
         e = cudaStreamSynchronize(s);
     } while (0);
     if (e != cudaSuccess) {
@@ -995,7 +1266,7 @@ int batch_autotune(Context &ctx, Lane &lane, bool mixed, int per_bucket) {
             for (int rep = 0; rep < 2 && ok; ++rep) {
                 tsnnls_info info;
                 int st = run_batch_dense(ctx, lane, cnt, mv.data(), nv.data(), av.data(), bv.data(),
-                                         xv.data(), o, nullptr, &info, nbv.data());
+                                         xv.data(), o, nullptr, &info, nbv.data(), nullptr, 0);
                 ok = st == TSNNLS_OK;
                 if (rep == 1) total = (float)info.time_ms;
             }

@@ -621,11 +621,24 @@ int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, c
 
 extern "C" {
 
+int tsnnls_solve_batch_dense_ex(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
+                                const float *const *a, const double *const *b, double *const *x_out,
+                                const tsnnls_opts *opts, int32_t *status_out, tsnnls_info *info,
+                                int64_t *const *trace, int64_t trace_cap);
+
 int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
                              const float *const *a, const double *const *b, double *const *x_out,
                              const tsnnls_opts *opts, int32_t *status_out, tsnnls_info *info) {
+    return tsnnls_solve_batch_dense_ex(ctx, count, m, n, a, b, x_out, opts, status_out, info, nullptr, 0);
+}
+
+int tsnnls_solve_batch_dense_ex(tsnnls_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
+                                const float *const *a, const double *const *b, double *const *x_out,
+                                const tsnnls_opts *opts, int32_t *status_out, tsnnls_info *info,
+                                int64_t *const *trace, int64_t trace_cap) {
     if (info) std::memset(info, 0, sizeof(*info));
     if (!ctx || count <= 0 || !m || !n || !a || !b || !x_out) return TSNNLS_EINVAL;
+    if (trace && (trace_cap <= 0 || trace_cap > (1 << 20))) return TSNNLS_EINVAL;
     for (int i = 0; i < count; ++i) {
         if (n[i] <= 0 || m[i] <= n[i] || n[i] > 1024 || !a[i] || !b[i] || !x_out[i]) {
             if (info) info->status = TSNNLS_EINVAL;
@@ -636,7 +649,8 @@ int tsnnls_solve_batch_dense(tsnnls_ctx *ctx, int32_t count, const int32_t *m, c
     Context &c = ctx->c;
     std::lock_guard<std::mutex> g(c.solve_mu);
     cudaSetDevice(c.device);
-    return run_batch_dense(c, c.lane0, count, m, n, a, b, x_out, o, status_out, info, nullptr);
+    return run_batch_dense(c, c.lane0, count, m, n, a, b, x_out, o, status_out, info, nullptr,
+                           trace, trace ? trace_cap : 0);
 }
 
 int tsnnls_batch_autotune(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket, int32_t *nb_out) {

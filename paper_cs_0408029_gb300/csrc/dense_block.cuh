@@ -95,6 +95,40 @@ __device__ __forceinline__ void warp_chol_step(WarpChol<T> &s, T (*col)[32], int
     }
 }
 
+// The same step without the inverse (L only, half the registers), for
+// callers that solve with L directly.
+template <typename T>
+struct WarpCholL {
+    T a[32];
+};
+
+template <typename T, int J>
+__device__ __forceinline__ void warp_chol_step_l(WarpCholL<T> &s, T (*col)[32], int lane, int &bad, T d) {
+    if (!(d > T(0))) {
+        if (!bad) bad = J + 1;
+        d = T(1);
+    }
+    const T inv = rsqrt_t(d);
+    const T lij = (lane > J) ? s.a[J] * inv : (lane == J ? d * inv : s.a[J]);
+    s.a[J] = lij;
+    if constexpr (J + 1 < 32) {
+        const T dn = __shfl_sync(0xffffffffu, s.a[J + 1] - lij * lij, J + 1);
+        col[J & 1][lane] = lij;
+        __syncwarp();
+#pragma unroll
+        for (int g = (J + 1) / 4; g < 8; ++g) {
+            T v[4];
+            ld4(&col[J & 1][4 * g], v);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = 4 * g + u;
+                if (l > J) s.a[l] -= lij * v[u];
+            }
+        }
+        warp_chol_step_l<T, J + 1>(s, col, lane, bad, dn);
+    }
+}
+
 // Factor A(j0.., j0..) (32 x 32, lower) in place and write its inverse to W
 // (W[col][row]) and, transposed, to the strict upper triangle of the block
 // in A.  col: 2 x 32 shared scratch, 16-byte aligned.

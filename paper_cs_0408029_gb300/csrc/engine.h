@@ -132,10 +132,12 @@ int status_from_cuda(cudaError_t e);
 
 // Batched dense solves (batch.cu).  nb_override (count entries) forces the
 // Cholesky panel width per problem; NULL uses the tuned table.
+// trace (count host pointers, may be NULL; entries may be NULL): each
+// problem's pivot trace, trace_cap rows of 6 (as tsnnls_solve_ex).
 int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const int32_t *n,
                     const float *const *a, const double *const *b, double *const *x,
                     const tsnnls_opts &o, int32_t *status_out, tsnnls_info *info,
-                    const int *nb_override);
+                    const int *nb_override, int64_t *const *trace = nullptr, int64_t trace_cap = 0);
 int batch_autotune(Context &ctx, Lane &lane, bool mixed, int per_bucket);
 extern int g_batch_nb_table[2][5];
 

@@ -97,3 +97,54 @@ def test_autotune_picks_candidate_widths(env):
     probs = _batch(103, 8, 32, 512)
     st, stat, info, xs = _run(ts, ctx, torch, probs, "mixed")
     assert st == ts.OK
+
+
+def test_batch_traces_match_oracle_and_full_refinement(env, oracle_mod):
+    """Every problem's pivot trace equals the oracle's (A rounded to FP32 on
+    both sides); refining intermediate pivots only until their signs are
+    settled (the default) gives the same traces and x as refining every pivot
+    to rel_tol, with fewer refinement steps."""
+    ts, ctx, torch = env
+    probs = _batch(104, 20, 32, 1024)
+    a = [torch.as_tensor(p.a, device="cuda") for p in probs]
+    b = [torch.as_tensor(p.b, device="cuda") for p in probs]
+    out = {}
+    for full in (0, 1):
+        x = [torch.empty(p.n, dtype=torch.float64, device="cuda") for p in probs]
+        st, stat, info, trs = ctx.solve_batch_dense(a, b, x, trace_cap=400, full_refine=full)
+        assert st == ts.OK, stat
+        out[full] = ([t.cpu().numpy() for t in x], trs, info.refine_steps)
+    assert out[0][2] < out[1][2]
+    for i, p in enumerate(probs):
+        csr = workloads.dense_to_csr(p.a.astype(np.float64), p.b)
+        ref = oracle_mod.bpp_solve(csr)
+        assert np.array_equal(out[0][1][i], ref.trace), p.name
+        assert np.array_equal(out[1][1][i], ref.trace), p.name
+        x0, x1 = out[0][0][i], out[1][0][i]
+        assert np.linalg.norm(x0 - x1) <= 1e-12 * np.linalg.norm(x1), p.name
+
+
+def test_batch_single_exchange_fallback(env, oracle_mod):
+    """p_max = 0 on conditioned problems (A rounded to FP32): the persistent
+    kernel's single-variable fallback moves the largest infeasible index,
+    row by row as the oracle does."""
+    ts, ctx, torch = env
+    probs = []
+    for seed, (m, n) in enumerate([(60, 40), (200, 150), (400, 300)]):
+        prob, _, _ = workloads.conditioned_dense(m, n, 1e3, seed=seed + 2, active_frac=1.0)
+        a32 = prob.a.astype(np.float32)
+        probs.append(workloads.DenseProblem(m, n, a32, prob.b, prob.x_planted, f"cond{n}"))
+    a = [torch.as_tensor(p.a, device="cuda") for p in probs]
+    b = [torch.as_tensor(p.b, device="cuda") for p in probs]
+    x = [torch.empty(p.n, dtype=torch.float64, device="cuda") for p in probs]
+    st, stat, info, trs = ctx.solve_batch_dense(a, b, x, trace_cap=400, p_max=0)
+    assert st == ts.OK, stat
+    singles = 0
+    for p, tr, xt in zip(probs, trs, x):
+        csr = workloads.dense_to_csr(p.a.astype(np.float64), p.b)
+        ref = oracle_mod.bpp_solve(csr, p_max=0)
+        assert np.array_equal(tr, ref.trace), p.name
+        singles += int((ref.trace[:, 3] == 2).sum())
+        xv = xt.cpu().numpy()
+        assert np.linalg.norm(xv - ref.x) <= 1e-9 * np.linalg.norm(ref.x), p.name
+    assert singles >= 3
