@@ -2,9 +2,9 @@
 //
 // Each problem i has a dense FP32 A_i (m_i x n_i, row-major), FP64 b_i and x_i.
 // The work is two kernels, captured once into a CUDA graph and replayed:
-//   1. batched precompute (Section 3): G_i = A_i^T A_i (lower tiles, FP32
-//      accumulate) and c_i = A_i^T b_i (FP64), over one flat list of
-//      (problem, tile) work items;
+//   1. batched precompute (Section 3): G_i = A_i^T A_i (lower tiles; MIXED
+//      on the tensor cores, TF32 with a hi/lo split) and c_i = A_i^T b_i
+//      (FP64), over one flat list of (problem, tile) work items;
 //   2. one persistent kernel: each CTA takes problems from an atomic queue,
 //      largest first, and runs the whole pivot loop of Section 2 for it --
 //      exchange, gather of G_FF, blocked Cholesky, triangular solves, FP64
@@ -55,58 +55,12 @@ struct BatchParams {
 };
 
 // ---------------------------------------------------------------------------
-// 1. precompute: G = A^T A lower 64 x 64 tiles, FP32; c = A^T b in FP64.
+// 1. precompute: G = A^T A lower 64 x 64 tiles (MIXED: FP32 on the tensor
+//    cores, batch_gram_tc_kernel below; FP64: FP64 products); c = A^T b in FP64.
 
 struct GramItem {
     int32_t prob, I, J;
 };
-
-__global__ void __launch_bounds__(256)
-    batch_gram_kernel(const BatchProb *__restrict__ probs, const GramItem *__restrict__ items,
-                      int32_t nitems) {
-    __shared__ float As[16][68];
-    __shared__ float Bs[16][68];
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const GramItem w = items[it];
-        const BatchProb P = probs[w.prob];
-        const int n = P.n, m = P.m;
-        const int r0 = w.I * 64, c0 = w.J * 64;
-        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-        float acc[4][4] = {};
-        for (int k0 = 0; k0 < m; k0 += 16) {
-            for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-                const int kk = e / 64, i = e % 64;
-                const int row = k0 + kk;
-                As[kk][i] = (row < m && r0 + i < n) ? P.A[(int64_t)row * n + r0 + i] : 0.f;
-                Bs[kk][i] = (row < m && c0 + i < n) ? P.A[(int64_t)row * n + c0 + i] : 0.f;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-                float a[4], bb[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    a[q] = As[kk][ty + 16 * q];
-                    bb[q] = Bs[kk][tx + 16 * q];
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) acc[q][t] += a[q] * bb[t];
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = r0 + ty + 16 * q;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = c0 + tx + 16 * t;
-                if (i < n && j < n && i >= j) P.G[i + (int64_t)j * P.ld] = acc[q][t];
-            }
-        }
-    }
-}
 
 // FP64 Gram for the plain FP64 path (same tiling, FP64 products of the FP32 data).
 __global__ void __launch_bounds__(256)
@@ -362,6 +316,67 @@ __device__ __noinline__ int warp_factor_block(T *S, int lds, int K, int kb, T *d
             diag[c * 65 + lane] = s.a[c];
         }
     return bad;
+}
+
+// G = A^T A on the tensor cores (MIXED precompute): one 64 x 64 lower tile
+// per CTA and work item, 8 warps of 16 x 32, rows of A staged 32 at a time
+// (pitch 72, so the fragment loads of a warp hit distinct banks);
+// mma.sync m16n8k8 TF32 with the hi/lo split as in tc_trailing_update.
+// A_mma(i, r) = A(r, r0 + i), B_mma(r, j) = A(r, c0 + j).
+__global__ void __launch_bounds__(256)
+    batch_gram_tc_kernel(const BatchProb *__restrict__ probs, const GramItem *__restrict__ items,
+                         int32_t nitems) {
+    constexpr int KC = 32, PT = 72;
+    __shared__ __align__(16) float As[KC][PT];
+    __shared__ __align__(16) float Bs[KC][PT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int mi = (warp & 3) * 16, nj0 = (warp >> 2) * 32;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const GramItem w = items[it];
+        const BatchProb P = probs[w.prob];
+        const int n = P.n, m = P.m;
+        const int r0 = w.I * 64, c0 = w.J * 64;
+        float acc[4][4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[b][q] = 0.f;
+        for (int k0 = 0; k0 < m; k0 += KC) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < KC * 64; e += 256) {
+                const int kk = e / 64, i = e % 64;
+                const int row = k0 + kk;
+                As[kk][i] = (row < m && r0 + i < n) ? P.A[(int64_t)row * n + r0 + i] : 0.f;
+                Bs[kk][i] = (row < m && c0 + i < n) ? P.A[(int64_t)row * n + c0 + i] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < KC; kk += 8) {
+                uint32_t ah[4], al[4];
+                split_tf32(As[kk + t][mi + g], ah[0], al[0]);
+                split_tf32(As[kk + t][mi + g + 8], ah[1], al[1]);
+                split_tf32(As[kk + t + 4][mi + g], ah[2], al[2]);
+                split_tf32(As[kk + t + 4][mi + g + 8], ah[3], al[3]);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    uint32_t bh[2], bl[2];
+                    split_tf32(Bs[kk + t][nj0 + 8 * b + g], bh[0], bl[0]);
+                    split_tf32(Bs[kk + t + 4][nj0 + 8 * b + g], bh[1], bl[1]);
+                    mma_tf32_16x8x8(acc[b], ah, bh);
+                    mma_tf32_16x8x8(acc[b], ah, bl);
+                    mma_tf32_16x8x8(acc[b], al, bh);
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = r0 + mi + g + (q >= 2 ? 8 : 0);
+                const int j = c0 + nj0 + 8 * b + 2 * t + (q & 1);
+                if (i < n && j < n && i >= j) P.G[i + (int64_t)j * P.ld] = acc[b][q];
+            }
+    }
 }
 
 // In-CTA blocked right-looking Cholesky of the k x k lower matrix S (lds),
@@ -1127,7 +1142,7 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
         cudaMemsetAsync(d_queue, 0, sizeof(int32_t), s);
         const int gitems = (int)items.size();
         const int ggrid = std::max(1, std::min(gitems, num_sms() * 8));
-        if (mixed) batch_gram_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
+        if (mixed) batch_gram_tc_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
         else batch_gram64_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
         note_launches(1);
         batch_atb_kernel<<<std::min(count, num_sms() * 8), 256, 0, s>>>(d_probs, count);
