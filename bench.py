@@ -511,37 +511,134 @@ def run_lsqr(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, peaks
         gpu_launches=int(info.kernel_launches), clocks=clk.summary())
 
 
+class RequestStream:
+    """The serving trace's requests, generated ahead of their arrival by a
+    pool of spawned worker processes and dropped once served, so that a long
+    trace never sits in host memory at once.  Requests are fetched in index
+    (= arrival) order; stall_s counts the time a fetch waited for a worker."""
+
+    def __init__(self, count, workers, ahead=64):
+        import multiprocessing as mp
+
+        self._pool = mp.get_context("spawn").Pool(workers)
+        self._count, self._ahead = count, ahead
+        self._next, self._fetched, self._res = 0, 0, {}
+        self.stall_s = 0.0
+        self._fill()
+
+    def _fill(self):
+        import workloads
+
+        while self._next < self._count and self._next < self._fetched + self._ahead:
+            self._res[self._next] = self._pool.apply_async(workloads.serving_request, (self._next,))
+            self._next += 1
+
+    def __len__(self):
+        return self._count
+
+    def __getitem__(self, i):
+        self._fetched = max(self._fetched, i + 1)
+        self._fill()
+        r = self._res[i]
+        if not r.ready():
+            t = time.perf_counter()
+            r.wait()
+            self.stall_s += time.perf_counter() - t
+        return r.get()
+
+    def release(self, i):
+        self._res.pop(i, None)
+
+    def close(self):
+        self._pool.terminate()
+        self._pool.join()
+
+
+def _latency_summary(out, count):
+    lat = out["latency_s"] * 1e3
+    return {"solves_s": count / out["wall_s"], "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "wall_s": out["wall_s"]}
+
+
 def run_serving(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, peaks):
-    """A Poisson trace of mixed-size requests through submit/poll (continuous batching)."""
-    import workloads
+    """A Poisson trace of mixed-size requests through submit/poll (continuous batching).
+
+    Without --rate-frac: ``--requests`` requests at ``--rate`` per second.
+    With --rate-frac F: the saturation rate of each path is measured first
+    (every request of a prefix of the trace submitted at once), then the
+    full trace is replayed through both paths at F x the FP64 path's
+    saturation rate, and --sweep replays a prefix at other fractions of each
+    path's own saturation rate."""
     from paper_cs_0408029_gb300 import serving
 
     count = args.requests
-    probs = [workloads.serving_request(i) for i in range(count)]
-    arrivals = workloads.serving_arrivals(count, rate_per_s=args.rate)
-    serving.replay(ctx, probs[:8], np.zeros(8))  # warm-up: pools, lanes
+    workers = max(1, min(12, (os.cpu_count() or 2) - 2))
+    pre_n = min(count, max(args.sat_requests, args.sweep_requests))
+    pre = RequestStream(pre_n, workers, ahead=pre_n)
+    prefix = [pre[i] for i in range(pre_n)]
+    pre.close()
+    serving.replay(ctx, prefix[:8], np.zeros(8), keep_x=False)  # warm-up: pools, lanes
+    extra = {}
+    if args.rate_frac is None:
+        rate = args.rate
+    else:
+        sat = {}
+        for prec, k in (("fp64", min(args.sat_requests, pre_n)), ("mixed", pre_n)):
+            o = serving.replay(ctx, prefix[:k], np.zeros(k), precision=prec, keep_x=False)
+            assert (o["status"] == ts.OK).all()
+            sat[prec] = {"solves_s": k / o["wall_s"], "requests": k}
+        rate = args.rate_frac * sat["fp64"]["solves_s"]
+        extra["saturation"] = sat
+        extra["rate_frac_of_fp64_saturation"] = args.rate_frac
+    arrivals = workloads_arrivals(count, rate)
     barrier()
+    src = prefix if count <= pre_n else RequestStream(count, workers)
     with ClockSampler(dev.index) as clk:
-        out = serving.replay(ctx, probs, arrivals, precision="mixed")
-    out64 = serving.replay(ctx, probs, arrivals, precision="fp64")
+        out = serving.replay(ctx, src, arrivals, precision="mixed")
+    stall = getattr(src, "stall_s", 0.0)
+    if src is not prefix:
+        src.close()
+        src = RequestStream(count, workers)
+    out64 = serving.replay(ctx, src, arrivals, precision="fp64")
+    stall64 = getattr(src, "stall_s", 0.0)
+    if src is not prefix:
+        src.close()
     wall = max_over_ranks(out["wall_s"])
     if rank != 0:
         return None
     assert (out["status"] == ts.OK).all() and (out64["status"] == ts.OK).all()
-    lat, lat64 = out["latency_s"] * 1e3, out64["latency_s"] * 1e3
     rel = max(np.linalg.norm(u - v) / max(np.linalg.norm(v), 1e-300) for u, v in zip(out["x"], out64["x"]))
+    del out["x"], out64["x"]
+    if args.rate_frac is not None and args.sweep:
+        sweep = []
+        for frac in [float(f) for f in args.sweep.split(",") if f]:
+            for prec, k in (("mixed", pre_n), ("fp64", min(args.sat_requests, pre_n))):
+                r = frac * extra["saturation"][prec]["solves_s"]
+                o = serving.replay(ctx, prefix[:k], workloads_arrivals(k, r), precision=prec, keep_x=False)
+                assert (o["status"] == ts.OK).all()
+                sweep.append({"path": prec, "frac_of_own_saturation": frac, "rate": r, "requests": k,
+                              **_latency_summary(o, k)})
+        extra["sweep"] = sweep
+    s_mixed, s64 = _latency_summary(out, count), _latency_summary(out64, count)
     return _common_line(
         "served NNLS solves/s and p50/p99 latency (Poisson arrivals)", ws * count / wall, "solves/s", ws,
         args, 1e3 * wall / count, "f32+f64",
         {"workload": f"serving: {count} requests, n log-uniform in [64,8192], m = 2n, density U(1%,5%), "
-                     f"Poisson arrivals at {args.rate}/s, request i drawn with seed (20040814, i)",
+                     f"Poisson arrivals at {rate:.2f}/s, request i drawn with seed (20040814, i)",
          "precision": "mixed", "lanes": out["queue"]["lanes"]},
-        p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-        fp64_plain={"value": count / out64["wall_s"], "unit": "solves/s",
-                    "p50_ms": float(np.percentile(lat64, 50)), "p99_ms": float(np.percentile(lat64, 99))},
+        rate=rate, p50_ms=s_mixed["p50_ms"], p99_ms=s_mixed["p99_ms"],
+        fp64_plain={"value": s64["solves_s"], "unit": "solves/s", "p50_ms": s64["p50_ms"],
+                    "p99_ms": s64["p99_ms"]},
         accuracy={"max_rel_diff_mixed_vs_fp64": float(rel)},
+        generator_stall_s={"mixed": stall, "fp64": stall64},
         queue={k: int(v) for k, v in out["queue"].items()},
-        device_ms_sum=float(np.nansum(out["device_ms"])), clocks=clk.summary())
+        device_ms_sum=float(np.nansum(out["device_ms"])), clocks=clk.summary(), **extra)
+
+
+def workloads_arrivals(count, rate):
+    import workloads
+
+    return workloads.serving_arrivals(count, rate_per_s=rate)
 
 
 def run_sparse(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, peaks):
@@ -691,6 +788,13 @@ def main():
                     choices=("larger_sparse",) + tuple(EXTRA_WORKLOADS))
     ap.add_argument("--requests", type=int, default=200, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per second")
+    ap.add_argument("--rate-frac", type=float, default=None,
+                    help="serving workload: arrival rate as this fraction of the FP64 path's measured saturation")
+    ap.add_argument("--sat-requests", type=int, default=300,
+                    help="serving workload: FP64 saturation is measured on this prefix of the trace")
+    ap.add_argument("--sweep-requests", type=int, default=1000,
+                    help="serving workload: prefix for the mixed saturation and the sweep")
+    ap.add_argument("--sweep", default="", help="serving workload: fractions of each path's saturation, e.g. 0.5,0.9")
     ap.add_argument("--sweep-m", type=int, default=1200, help="kappa_sweep workload: rows")
     ap.add_argument("--sweep-n", type=int, default=800, help="kappa_sweep workload: columns")
     ap.add_argument("--grid", type=int, default=256, help="sparse workload: grid side (n = grid^2)")

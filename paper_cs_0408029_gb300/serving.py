@@ -16,16 +16,22 @@ import numpy as np
 from . import PENDING, HostCSR
 
 
-def replay(ctx, problems, arrivals, precision="mixed", poll_s=0.0002):
+def replay(ctx, problems, arrivals, precision="mixed", poll_s=0.0002, keep_x=True):
     """Submit problems[i] at time arrivals[i] (seconds from the start).
 
-    Returns dict with x (list), status, latency_s (per request), wall_s,
-    device_ms (per request), and the queue statistics."""
-    n = len(problems)
+    ``problems`` is a sequence of problems (m, n, row_ptr, col_idx, val, b).
+    It may also be a lazy source: indexing may block until request i is
+    ready, and if it has a ``release(i)`` method that is called once request
+    i has completed, so that a long trace never holds every request in host
+    memory at once.  Requests are fetched in arrival order.
+
+    Returns dict with x (list; None entries unless keep_x), status,
+    latency_s (per request), wall_s, device_ms (per request), and the queue
+    statistics."""
+    n = len(arrivals)
     order = np.argsort(arrivals, kind="stable")
-    hosts = [HostCSR.from_problem(p) for p in problems]
-    bs = [np.ascontiguousarray(p.b, dtype=np.float64) for p in problems]
-    xs = [np.empty(p.n) for p in problems]
+    release = getattr(problems, "release", None)
+    xs = [None] * n
     lat = np.full(n, np.nan)
     dev_ms = np.full(n, np.nan)
     status = np.full(n, -1, dtype=np.int64)
@@ -38,17 +44,24 @@ def replay(ctx, problems, arrivals, precision="mixed", poll_s=0.0002):
             st, info = ctx.poll(t)
             if st == PENDING:
                 continue
-            i, arr = pending.pop(t)
+            i, arr, x = pending.pop(t)
             lat[i] = time.perf_counter() - (t0 + arr)
             dev_ms[i] = info.time_ms
             status[i] = st
+            if keep_x:
+                xs[i] = x
+            if release is not None:
+                release(i)
 
     while nxt < n or pending:
         now = time.perf_counter() - t0
         while nxt < n and arrivals[order[nxt]] <= now:
             i = int(order[nxt])
-            t = ctx.submit(hosts[i], bs[i], xs[i], precision=precision)
-            pending[t] = (i, float(arrivals[i]))
+            p = problems[i]
+            x = np.empty(p.n)
+            t = ctx.submit(HostCSR.from_problem(p), np.ascontiguousarray(p.b, dtype=np.float64), x,
+                           precision=precision)
+            pending[t] = (i, float(arrivals[i]), x)
             nxt += 1
         drain()
         if nxt < n:
