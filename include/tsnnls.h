@@ -52,6 +52,9 @@ extern "C" {
 #define TSNNLS_PENDING 8   /* tsnnls_poll: the ticket has not finished yet */
 #define TSNNLS_ECUDA 9     /* a CUDA runtime call failed */
 #define TSNNLS_ENODEV 10   /* no usable CUDA device / the requested device does not exist */
+#define TSNNLS_ENOTFOUND 11 /* tsnnls_tune_cache_get: the cache holds no entry for the key */
+#define TSNNLS_EBOUNDS 12  /* bounds-checked build only: a kernel met an index outside its buffer
+                              (the access was skipped; tsnnls_check_report says where) */
 
 /* ---- precision / path selectors ---------------------------------------- */
 /* MIXED: Gram block gathered and factored in FP32 (tensor-core trailing
@@ -266,6 +269,48 @@ int tsnnls_batch_autotune(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket
 /* Set the table directly (e.g. from a cached autotune result); 5 widths in
  * [4, 64], clamped to what the kernel's shared memory allows. */
 int tsnnls_batch_set_panel(int32_t precision, const int32_t *nb);
+
+/* The autotuner with a JSON cache on disk.  The cache key names the device
+ * (its name, compute capability and SM count), the precision, per_bucket and
+ * the build of this library; on a hit the cached widths are installed
+ * without timing anything (*hit_out = 1), on a miss the autotuner runs and
+ * its result is added to the file (*hit_out = 0), which is created if
+ * absent.  cache_path: a file path (host string).  nb_out (5 entries) and
+ * hit_out may be NULL.  TSNNLS_EINVAL if the file exists but is not a cache
+ * of this format (it is then left untouched) or cannot be written. */
+int tsnnls_batch_autotune_cached(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket,
+                                 const char *cache_path, int32_t *nb_out, int32_t *hit_out);
+
+/* The cache key tsnnls_batch_autotune_cached uses on this context, as a
+ * NUL-terminated string in buf (len bytes); TSNNLS_EINVAL if it does not fit. */
+int tsnnls_batch_tune_key(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket, char *buf, size_t len);
+
+/* Direct access to the cache file (host only, no device needed).  The file
+ * is one JSON object {"format": "tsnnls-batch-panel-widths/1", "entries":
+ * {key: [5 widths], ...}}.  get: TSNNLS_OK and the 5 widths in nb_out,
+ * TSNNLS_ENOTFOUND if the file or the key is absent, TSNNLS_EINVAL if the
+ * file does not parse.  put: adds or replaces the key's entry, keeping the
+ * others, and replaces the file through a rename (a concurrent reader sees
+ * the old or the new file, never a mix); TSNNLS_EINVAL if the existing file
+ * does not parse (it is left untouched) or cannot be written.  Keys are
+ * non-empty strings without control characters. */
+int tsnnls_tune_cache_get(const char *path, const char *key, int32_t *nb_out);
+int tsnnls_tune_cache_put(const char *path, const char *key, const int32_t *nb);
+
+/* ---- bounds-checked build ------------------------------------------------
+ * Built with -DTSNNLS_CHECK (libtsnnls_check.so), the kernels test every
+ * data-dependent index (the F lists, CSR column and row indices, the sparse
+ * factor's assembly maps, the exchange's moved index) against the buffer it
+ * addresses.  A failing access is skipped, never trapped; the call that ran
+ * the kernel returns TSNNLS_EBOUNDS once its stream is idle.  It stands in
+ * for a memory checker in tests.  tsnnls_check_build: 1 in that build, else
+ * 0.  tsnnls_check_report: the failing accesses since the previous call (0
+ * if none, always 0 in the normal build), and in buf (len bytes, may be
+ * NULL) "file:line: index i outside [0, bound)" for the first of them;
+ * clears the record.  Process-wide: with several contexts or lanes at once
+ * a report names the site, not the request. */
+int tsnnls_check_build(void);
+int tsnnls_check_report(char *buf, size_t len);
 
 /* ---- per-phase device-time accounting ----------------------------------
  * When enabled, blocking solves on the context bracket every phase of the

@@ -15,7 +15,8 @@ import numpy as np
 
 from . import build as _build_mod
 
-OK, EINVAL, ENOMEM, EADMIT, ENOTPD, EMAXITER, ENOCONV, ETIMEOUT, PENDING, ECUDA, ENODEV = range(11)
+(OK, EINVAL, ENOMEM, EADMIT, ENOTPD, EMAXITER, ENOCONV, ETIMEOUT, PENDING, ECUDA, ENODEV, ENOTFOUND,
+ EBOUNDS) = range(13)
 MIXED, FP64 = 0, 1
 PATH_AUTO, PATH_FACTOR, PATH_LSQR, PATH_SPARSE = 0, 1, 2, 3
 WAIT_PROBE_MAX_POLLS = 1 << 22  # TSNNLS_WAIT_PROBE_MAX_POLLS
@@ -29,6 +30,8 @@ EXPORTS = (
     "tsnnls_chol_solve_noalloc", "tsnnls_batch_autotune", "tsnnls_batch_set_panel",
     "tsnnls_queue_stats_read", "tsnnls_wait_probe", "tsnnls_submit_batch",
     "tsnnls_batch_member_info", "tsnnls_sparse_analyze", "tsnnls_solve_batch_dense_ex",
+    "tsnnls_batch_autotune_cached", "tsnnls_batch_tune_key", "tsnnls_tune_cache_get",
+    "tsnnls_tune_cache_put", "tsnnls_check_build", "tsnnls_check_report",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
@@ -84,13 +87,15 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Load libtsnnls.so (building it first if needed)."""
+    """Load libtsnnls.so (building it first if needed); with TSNNLS_CHECK=1
+    in the environment, the bounds-checked libtsnnls_check.so instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build_mod.LIB
-    if build_if_missing and not _build_mod.up_to_date():
-        _build_mod.build()
+    variant = "check" if os.environ.get("TSNNLS_CHECK", "") not in ("", "0") else "normal"
+    path = _build_mod.VARIANTS[variant][0]
+    if build_if_missing and not _build_mod.up_to_date(variant):
+        _build_mod.build(variants=(variant,))
     if not os.path.exists(path):
         raise RuntimeError(f"libtsnnls is not built ({path}); run paper_cs_0408029_gb300.build")
     lib = ctypes.CDLL(path)
@@ -123,6 +128,12 @@ def load(build_if_missing: bool = True):
         "tsnnls_wait_probe": ([i64], ctypes.c_int),
         "tsnnls_batch_autotune": ([p, i32, i32, p], ctypes.c_int),
         "tsnnls_batch_set_panel": ([i32, p], ctypes.c_int),
+        "tsnnls_batch_autotune_cached": ([p, i32, i32, ctypes.c_char_p, p, ctypes.POINTER(i32)], ctypes.c_int),
+        "tsnnls_batch_tune_key": ([p, i32, i32, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+        "tsnnls_check_build": ([], ctypes.c_int),
+        "tsnnls_check_report": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+        "tsnnls_tune_cache_get": ([ctypes.c_char_p, ctypes.c_char_p, p], ctypes.c_int),
+        "tsnnls_tune_cache_put": ([ctypes.c_char_p, ctypes.c_char_p, p], ctypes.c_int),
         "tsnnls_queue_stats_read": ([p, p], ctypes.c_int),
         "tsnnls_submit_batch": ([p, i32, p, p, p, ctypes.POINTER(Opts), ctypes.POINTER(i64)],
                                 ctypes.c_int),
@@ -135,6 +146,35 @@ def load(build_if_missing: bool = True):
         f.restype = res
     _lib = lib
     return lib
+
+
+def check_build():
+    """True if the loaded library is the bounds-checked build."""
+    return bool(load().tsnnls_check_build())
+
+
+def check_report():
+    """(failing accesses since the last call, first one's description)."""
+    buf = ctypes.create_string_buffer(512)
+    hits = load().tsnnls_check_report(buf, len(buf))
+    return hits, buf.value.decode()
+
+
+def tune_cache_get(path, key):
+    """The 5 cached widths for key, or None if the file or the key is absent."""
+    nb = np.zeros(5, dtype=np.int32)
+    st = load().tsnnls_tune_cache_get(os.fsencode(path), key.encode(), _np_ptr(nb))
+    if st == ENOTFOUND:
+        return None
+    _check(st, "tune_cache_get")
+    return nb
+
+
+def tune_cache_put(path, key, nb):
+    arr = np.ascontiguousarray(nb, dtype=np.int32)
+    if arr.shape != (5,):
+        raise ValueError("five widths expected")
+    _check(load().tsnnls_tune_cache_put(os.fsencode(path), key.encode(), _np_ptr(arr)), "tune_cache_put")
 
 
 def strerror(status: int) -> str:
@@ -390,6 +430,19 @@ class Context:
         _check(self._lib.tsnnls_batch_autotune(self._h, precision, per_bucket, _np_ptr(nb)),
                "batch_autotune")
         return nb
+
+    def batch_autotune_cached(self, cache_path, precision=MIXED, per_bucket=64):
+        """Autotune through the JSON cache at cache_path: (widths, hit)."""
+        nb = np.zeros(5, dtype=np.int32)
+        hit = ctypes.c_int32(-1)
+        _check(self._lib.tsnnls_batch_autotune_cached(self._h, precision, per_bucket, os.fsencode(cache_path),
+                                                      _np_ptr(nb), ctypes.byref(hit)), "batch_autotune_cached")
+        return nb, bool(hit.value)
+
+    def batch_tune_key(self, precision=MIXED, per_bucket=64):
+        buf = ctypes.create_string_buffer(1024)
+        _check(self._lib.tsnnls_batch_tune_key(self._h, precision, per_bucket, buf, len(buf)), "batch_tune_key")
+        return buf.value.decode()
 
     @staticmethod
     def batch_set_panel(nb, precision=MIXED):

@@ -21,6 +21,7 @@
 #include <numeric>
 #include <vector>
 
+#include "check.cuh"
 #include "dense_block.cuh"
 #include "engine.h"
 
@@ -929,7 +930,7 @@ __global__ void __launch_bounds__(kBT, 1)
             if (d == -1) break;
             if (d == -2) { status = TSNNLS_EMAXITER; break; }
             if (d == 2) {
-                if (tid == 0) P.inF[sh_big] ^= 1;
+                if (tid == 0 && TS_IN(sh_big, n)) P.inF[sh_big] ^= 1;
             } else {
                 for (int j = tid; j < n; j += kBT)
                     if (P.inF[j] ? (P.x[j] < 0.0) : (P.y[j] < 0.0)) P.inF[j] ^= 1;
@@ -942,7 +943,8 @@ __global__ void __launch_bounds__(kBT, 1)
                     const int j = j0 + tid;
                     const int v = j < n ? P.inF[j] : 0;
                     const unsigned bal = __ballot_sync(0xffffffffu, v);
-                    if (v) P.F[base + __popc(bal & ((1u << tid) - 1u))] = j;
+                    const int pos = base + __popc(bal & ((1u << tid) - 1u));
+                    if (v && TS_IN(pos, n)) P.F[pos] = j;
                     base += __popc(bal);
                 }
                 if (tid == 0) {
@@ -1029,6 +1031,7 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
                     const float *const *a, const double *const *b, double *const *x,
                     const tsnnls_opts &o, int32_t *status_out, tsnnls_info *info,
                     const int *nb_override, int64_t *const *trace, int64_t trace_cap) {
+    NvtxSolve range(lane, "tsnnls_solve_batch_dense");
     const bool mixed = o.precision == TSNNLS_MIXED;
     const size_t tsz = mixed ? sizeof(float) : sizeof(double);
     cudaStream_t s = lane.stream;
@@ -1184,6 +1187,7 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
     if (graph) cudaGraphDestroy(graph);
     cudaFreeAsync(arena, s);
     cudaStreamSynchronize(s);
+    if (check_collect(nullptr, 0) > 0 && status == TSNNLS_OK) status = TSNNLS_EBOUNDS;
     int32_t iters = 0, refine = 0;
     double flops = 0.0, bytes = 0.0;
     if (status == TSNNLS_OK) {
@@ -1300,3 +1304,4 @@ int batch_autotune(Context &ctx, Lane &lane, bool mixed, int per_bucket) {
 
 }  // namespace tsnnls
 
+TSNNLS_CHECK_UNIT("batch")

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "common.cuh"
 
 namespace tsnnls {
@@ -72,11 +73,11 @@ __global__ void __launch_bounds__(kBThreads)
             }
         });
     const int64_t r = compact(
-        kb, [&](int64_t p) { return inF[Bl[p]] == 0; },
+        kb, [&](int64_t p) { return TS_IN(Bl[p], n) && inF[Bl[p]] == 0; },
         [&](int64_t pos, int64_t p) {
             if (pos < kBorderMax) Rpos[pos] = (int32_t)p;
         });
-    for (int64_t p = tid; p < kb; p += kBThreads) Ul[p] = inF[Bl[p]] ? Bl[p] : -1;
+    for (int64_t p = tid; p < kb; p += kBThreads) Ul[p] = TS_IN(Bl[p], n) && inF[Bl[p]] ? Bl[p] : -1;
     if (tid < kBorderMax && tid < a) Ul[kb + tid] = al[tid];
     if (tid == 0) {
         st->border_a = (int32_t)min(a, (int64_t)INT32_MAX);
@@ -116,7 +117,7 @@ __global__ void border_gather_kernel(const T *__restrict__ G, int64_t ldg, const
         const int64_t i = e % rows;
         const int al = (int)(e / rows);
         const int64_t ri = i < kb ? Bl[i] : Al[i - kb], cj = Al[al];
-        const T v = ri >= cj ? G[ri + cj * ldg] : G[cj + ri * ldg];
+        const T v = TS_IN(ri, ldg) && TS_IN(cj, ldg) ? (ri >= cj ? G[ri + cj * ldg] : G[cj + ri * ldg]) : T(0);
         if (i < kb) Pt[i + al * ldp] = v;
         else GAA[(i - kb) + al * kBorderMax] = (double)v;
     }
@@ -423,3 +424,5 @@ template cudaError_t launch_border_solve<double>(cudaStream_t, const double *, i
                                                  const BorderBuffers &, double *, void *, DevStatus *);
 
 }  // namespace tsnnls
+
+TSNNLS_CHECK_UNIT("border")

@@ -4,9 +4,12 @@
 #include <stdint.h>
 
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 
+#include "check.cuh"
 #include "engine.h"
 
 using namespace tsnnls;
@@ -115,6 +118,8 @@ const char *tsnnls_strerror(int s) {
         case TSNNLS_PENDING: return "pending";
         case TSNNLS_ECUDA: return "CUDA runtime error";
         case TSNNLS_ENODEV: return "no usable CUDA device";
+        case TSNNLS_ENOTFOUND: return "no cache entry for the key";
+        case TSNNLS_EBOUNDS: return "a kernel index left its buffer (bounds-checked build)";
         default: return "unknown status";
     }
 }
@@ -451,7 +456,9 @@ static int finish(Lane &l, cudaError_t e) {
         cudaStreamSynchronize(l.stream);
         return status_from_cuda(e);
     }
-    return status_from_cuda(cudaStreamSynchronize(l.stream));
+    const int st = status_from_cuda(cudaStreamSynchronize(l.stream));
+    if (check_collect(nullptr, 0) > 0 && st == TSNNLS_OK) return TSNNLS_EBOUNDS;
+    return st;
 }
 
 int tsnnls_gram(tsnnls_ctx *ctx, const tsnnls_csr *A, const double *b, int32_t precision,
@@ -585,7 +592,7 @@ int tsnnls_spmv(tsnnls_ctx *ctx, const tsnnls_csr *A, int32_t trans, double alph
     Lane &l = c.lane0;
     const int64_t m = A->m, n = A->n, nnz = A->nnz;
     if (!trans) {
-        cudaError_t e = launch_spmv(l.stream, m, A->row_ptr, A->col_idx, A->val, alpha, x, beta, z,
+        cudaError_t e = launch_spmv(l.stream, m, A->row_ptr, A->col_idx, A->val, alpha, x, n, beta, z,
                                     out, (double)nnz / (double)m);
         return finish(l, e);
     }
@@ -607,7 +614,7 @@ int tsnnls_spmv(tsnnls_ctx *ctx, const tsnnls_csr *A, int32_t trans, double alph
     e = launch_csr_to_csc(l.stream, m, n, nnz, A->row_ptr, A->col_idx, A->val, col_ptr, row_idx,
                           cval, cnt, next);
     if (e == cudaSuccess)
-        e = launch_spmv(l.stream, n, col_ptr, row_idx, cval, alpha, x, beta, z, out,
+        e = launch_spmv(l.stream, n, col_ptr, row_idx, cval, alpha, x, m, beta, z, out,
                         (double)nnz / (double)n);
     cudaFreeAsync(blk, l.stream);
     return finish(l, e);
@@ -664,6 +671,63 @@ int tsnnls_batch_autotune(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket
         for (int i = 0; i < 5; ++i) nb_out[i] = g_batch_nb_table[mixed ? 0 : 1][i];
     return st;
 }
+
+#ifndef TSNNLS_BUILD_ID
+#define TSNNLS_BUILD_ID "unversioned"
+#endif
+
+static std::string tune_key(const Context &c, int32_t precision, int32_t per_bucket) {
+    cudaDeviceProp p{};
+    if (cudaGetDeviceProperties(&p, c.device) != cudaSuccess) return std::string();
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|sm_%d%d|%d SMs|%s|per_bucket %d|build %s", p.name, p.major, p.minor,
+             p.multiProcessorCount, precision == TSNNLS_MIXED ? "mixed" : "fp64",
+             per_bucket > 0 ? per_bucket : 64, TSNNLS_BUILD_ID);
+    return std::string(buf);
+}
+
+int tsnnls_batch_tune_key(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket, char *buf, size_t len) {
+    if (!ctx || !buf || (precision != TSNNLS_MIXED && precision != TSNNLS_FP64)) return TSNNLS_EINVAL;
+    const std::string k = tune_key(ctx->c, precision, per_bucket);
+    if (k.empty()) return TSNNLS_ECUDA;
+    if (k.size() + 1 > len) return TSNNLS_EINVAL;
+    memcpy(buf, k.c_str(), k.size() + 1);
+    return TSNNLS_OK;
+}
+
+int tsnnls_batch_autotune_cached(tsnnls_ctx *ctx, int32_t precision, int32_t per_bucket,
+                                 const char *cache_path, int32_t *nb_out, int32_t *hit_out) {
+    if (!ctx || !cache_path || (precision != TSNNLS_MIXED && precision != TSNNLS_FP64)) return TSNNLS_EINVAL;
+    const std::string key = tune_key(ctx->c, precision, per_bucket);
+    if (key.empty()) return TSNNLS_ECUDA;
+    int32_t nb[5];
+    int st = tsnnls_tune_cache_get(cache_path, key.c_str(), nb);
+    if (st == TSNNLS_OK) {
+        st = tsnnls_batch_set_panel(precision, nb);
+        if (st != TSNNLS_OK) return st;  // an entry outside [4, 64]: not ours
+        if (hit_out) *hit_out = 1;
+        if (nb_out) memcpy(nb_out, nb, sizeof nb);
+        return TSNNLS_OK;
+    }
+    if (st != TSNNLS_ENOTFOUND) return st;
+    st = tsnnls_batch_autotune(ctx, precision, per_bucket, nb);
+    if (st != TSNNLS_OK) return st;
+    st = tsnnls_tune_cache_put(cache_path, key.c_str(), nb);
+    if (st != TSNNLS_OK) return st;
+    if (hit_out) *hit_out = 0;
+    if (nb_out) memcpy(nb_out, nb, sizeof nb);
+    return TSNNLS_OK;
+}
+
+int tsnnls_check_build(void) {
+#ifdef TSNNLS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int tsnnls_check_report(char *buf, size_t len) { return check_report(buf, len); }
 
 int tsnnls_batch_set_panel(int32_t precision, const int32_t *nb) {
     if (!nb || (precision != TSNNLS_MIXED && precision != TSNNLS_FP64)) return TSNNLS_EINVAL;

@@ -140,7 +140,7 @@ cudaError_t launch_wait_probe(cudaStream_t s, const int32_t *flag, int64_t limit
 
 // out = alpha * M x + beta * z over a CSR (or CSC viewed as CSR of M^T).
 cudaError_t launch_spmv(cudaStream_t s, int64_t rows, const int64_t *ptr, const int32_t *idx,
-                        const double *val, double alpha, const double *x, double beta,
+                        const double *val, double alpha, const double *x, int64_t xlen, double beta,
                         const double *z, double *out, double avg_nnz);
 
 // Pivot-loop glue kernels (exchange.cu).
@@ -150,11 +150,11 @@ cudaError_t launch_exchange(cudaStream_t s, int64_t n, double *x, double *y, uin
                             int32_t *F, double zero_tol, int32_t p_max, int32_t max_iter,
                             int32_t apply_zeroing, DevStatus *st);
 template <typename T>
-cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, const int32_t *F, int64_t k,
-                              T *out);
+cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, int64_t n, const int32_t *F, int64_t k,
+                              T *out);  // out[a] = v[F[a]], v of n entries
 template <typename T>
 cudaError_t launch_update_x(cudaStream_t s, const T *delta, const int32_t *F, int64_t k,
-                            double *x, DevStatus *st);
+                            double *x, int64_t n, DevStatus *st);  // x of n entries
 // ---- reuse of a factor across pivots (border.cu) ----
 constexpr int kBorderMax = 32;  // added and removed variables handled at most (each)
 struct BorderBuffers {

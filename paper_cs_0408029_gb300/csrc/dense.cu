@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "common.cuh"
 
 namespace tsnnls {
@@ -42,10 +43,12 @@ __global__ void __launch_bounds__(256)
     const int tid = threadIdx.x;
     if (tid < kGatherRows) {
         const int64_t a = a0 + tid;
-        fr[tid] = a < k ? F[a] : 0;
+        const int32_t f = a < k ? F[a] : 0;
+        fr[tid] = TS_IN(f, ldg) ? f : 0;
     } else if (tid < kGatherRows + kGatherCols) {
         const int64_t b = b0 + tid - kGatherRows;
-        fc[tid - kGatherRows] = b < k ? F[b] : 0;
+        const int32_t f = b < k ? F[b] : 0;
+        fc[tid - kGatherRows] = TS_IN(f, ldg) ? f : 0;
     }
     __syncthreads();
     const int tx = tid & 31, ty = tid >> 5;
@@ -108,10 +111,12 @@ __global__ void __launch_bounds__(256)
     const int tid = threadIdx.x;
     if (tid < kGatherRows) {
         const int64_t a = a0 + tid;
-        fr[tid] = a < k ? F[a] : 0;
+        const int32_t f = a < k ? F[a] : 0;
+        fr[tid] = TS_IN(f, ldg) ? f : 0;
     } else if (tid < kGatherRows + kGatherCols) {
         const int64_t b = b0 + tid - kGatherRows;
-        fc[tid - kGatherRows] = b < k ? F[b] : 0;
+        const int32_t f = b < k ? F[b] : 0;
+        fc[tid - kGatherRows] = TS_IN(f, ldg) ? f : 0;
     }
     __syncthreads();
     const int tx = tid & 31, ty = tid >> 5;
@@ -195,3 +200,5 @@ template cudaError_t launch_gather<double>(cudaStream_t, const double *, int64_t
                                            int64_t);
 
 }  // namespace tsnnls
+
+TSNNLS_CHECK_UNIT("dense")

@@ -17,9 +17,15 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
+#include "check.cuh"
 #include "engine.h"
 #include "sparse_chol.h"
 
@@ -61,7 +67,66 @@ static cudaEvent_t pool_event(Lane &l) {
     return l.ev_pool[l.ev_used++];
 }
 
+// ---- bounds-check records (filled only in the checked build) -------------
+
+namespace {
+struct CheckUnit {
+    const char *name;
+    CheckCollectFn fn;
+};
+std::vector<CheckUnit> &check_units() {
+    static std::vector<CheckUnit> units;
+    return units;
+}
+std::mutex g_check_mu;
+int64_t g_check_hits = 0;  // since the last tsnnls_check_report
+std::string g_check_first;
+}  // namespace
+
+CheckRegistrar::CheckRegistrar(const char *unit, CheckCollectFn fn) { check_units().push_back({unit, fn}); }
+
+int check_collect(char *what, size_t len) {
+    std::lock_guard<std::mutex> g(g_check_mu);
+    int total = 0;
+    for (const CheckUnit &u : check_units()) {
+        CheckRecord r{};
+        if (u.fn(&r) != 0 || r.hits <= 0) continue;
+        char line[256];
+        snprintf(line, sizeof line, "%s.cu:%d: index %lld outside [0, %lld)", u.name, r.line,
+                 (long long)r.index, (long long)r.bound);
+        if (total == 0 && what && len) snprintf(what, len, "%s", line);
+        if (g_check_hits == 0 && total == 0) g_check_first = line;
+        total += r.hits;
+    }
+    g_check_hits += total;
+    return total;
+}
+
+int check_report(char *buf, size_t len) {
+    std::lock_guard<std::mutex> g(g_check_mu);
+    const int64_t hits = g_check_hits;
+    if (buf && len) snprintf(buf, len, "%s", g_check_first.c_str());
+    g_check_hits = 0;
+    g_check_first.clear();
+    return (int)std::min<int64_t>(hits, INT32_MAX);
+}
+
+static const char *const kPhaseName[TSNNLS_NUM_PHASES] = {
+    "setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
+    "factor_diag", "factor_panel", "factor_update", "reuse"};
+
+NvtxSolve::NvtxSolve(Lane &lane, const char *what) : l(lane) { nvtxRangePushA(what); }
+
+NvtxSolve::~NvtxSolve() {
+    if (l.nvtx_open) nvtxRangePop();
+    l.nvtx_open = false;
+    nvtxRangePop();
+}
+
 void prof_begin(Lane &l, int phase) {
+    if (l.nvtx_open) nvtxRangePop();
+    nvtxRangePushA(phase >= 0 && phase < TSNNLS_NUM_PHASES ? kPhaseName[phase] : "phase");
+    l.nvtx_open = true;
     l.mark_launch0 = launches_so_far();
     if (!l.prof) return;
     PhaseMark mk{phase, pool_event(l), nullptr, 0.0, 0.0, 0};
@@ -70,6 +135,8 @@ void prof_begin(Lane &l, int phase) {
 }
 
 void prof_end(Lane &l, double bytes, double flops) {
+    if (l.nvtx_open) nvtxRangePop();
+    l.nvtx_open = false;
     if (!l.prof || l.marks.empty()) return;
     PhaseMark &mk = l.marks.back();
     mk.e1 = pool_event(l);
@@ -352,7 +419,7 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         prof_begin(lane, TSNNLS_PHASE_GRAM);
         if (sparse) {
             // c = A^T b, and A^T A on the analysed pattern (FP64)
-            TRY_CUDA(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, bd, 0.0, nullptr, c, avg_col));
+            TRY_CUDA(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, bd, m, 0.0, nullptr, c, avg_col));
             TRY_CUDA(sc.setup(*sym, sparse_mem, s, col_ptr, row_idx, cval));
             prof_end(lane, csc_bytes + 8.0 * (m + n) + 16.0 * (double)sym->grow.size(), 0.0);
         } else {
@@ -367,8 +434,8 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         // FP64 residual r = b - A_F x_F and s = A^T r (x_G = 0) for the current x
         auto residual = [&]() -> cudaError_t {
             prof_begin(lane, TSNNLS_PHASE_SPMV);
-            cudaError_t e = launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row);
-            if (e == cudaSuccess) e = launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col);
+            cudaError_t e = launch_spmv(s, m, row_ptr, col, val, -1.0, x, n, 1.0, bd, r, avg_row);
+            if (e == cudaSuccess) e = launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, m, 0.0, nullptr, sv, avg_col);
             prof_end(lane, 2.0 * 12.0 * nnz + 8.0 * (m + 1) + 8.0 * (n + 1) + 8.0 * (3.0 * m + 2.0 * n),
                      4.0 * nnz);
             return e;
@@ -401,13 +468,13 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 const double tri = sparse ? (double)sym->nnz_L * sizeof(T)
                                           : 0.5 * (double)kl * (double)(kl + 1) * sizeof(T);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                cudaError_t e = launch_gather_rhs<T>(s, sv, sol_list(), sol_len(), rhs);
+                cudaError_t e = launch_gather_rhs<T>(s, sv, n, sol_list(), sol_len(), rhs);
                 prof_end(lane, (12.0 + sizeof(T)) * sol_len(), 0.0);
                 prof_begin(lane, TSNNLS_PHASE_TRSV);
                 if (e == cudaSuccess) e = pivot_solve(rhs);
                 prof_end(lane, 2.0 * tri + 4.0 * sizeof(T) * kl, 2.0 * (double)kl * (double)kl);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                if (e == cudaSuccess) e = launch_update_x<T>(s, rhs, sol_list(), sol_len(), x, lane.st_dev);
+                if (e == cudaSuccess) e = launch_update_x<T>(s, rhs, sol_list(), sol_len(), x, n, lane.st_dev);
                 prof_end(lane, (20.0 + sizeof(T)) * sol_len(), 0.0);
                 if (e == cudaSuccess) e = sync.post();
                 if (e == cudaSuccess) e = residual();
@@ -537,13 +604,13 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 const int64_t kl = reuse ? kb : k;
                 const double tril = sparse ? tri : 0.5 * (double)kl * (double)(kl + 1) * sizeof(T);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                TRY_CUDA(launch_gather_rhs<T>(s, c, sol_list(), sol_len(), rhs));
+                TRY_CUDA(launch_gather_rhs<T>(s, c, n, sol_list(), sol_len(), rhs));
                 prof_end(lane, (12.0 + sizeof(T)) * sol_len(), 0.0);
                 prof_begin(lane, TSNNLS_PHASE_TRSV);
                 TRY_CUDA(pivot_solve(rhs));
                 prof_end(lane, 2.0 * tril + 4.0 * sizeof(T) * kl, 2.0 * (double)kl * (double)kl);
                 prof_begin(lane, TSNNLS_PHASE_VECTOR);
-                TRY_CUDA(launch_update_x<T>(s, rhs, sol_list(), sol_len(), x, lane.st_dev));
+                TRY_CUDA(launch_update_x<T>(s, rhs, sol_list(), sol_len(), x, n, lane.st_dev));
                 prof_end(lane, (20.0 + sizeof(T)) * sol_len(), 0.0);
                 TRY_CUDA(sync.post());
             }
@@ -752,8 +819,24 @@ size_t solve_footprint(const tsnnls_csr &A, const tsnnls_opts &o, size_t budget,
     return path == TSNNLS_PATH_LSQR ? lsqr_footprint(A, o) : factor_footprint(A, o);
 }
 
+static int solve_on_lane_unchecked(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
+                                   double *x_out, const tsnnls_opts &o, tsnnls_info *info,
+                                   const SolveExtras *extras);
+
 int solve_on_lane(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, double *x_out,
                   const tsnnls_opts &o, tsnnls_info *info, const SolveExtras *extras) {
+    int st = solve_on_lane_unchecked(ctx, lane, A, b, x_out, o, info, extras);
+    if (check_collect(nullptr, 0) > 0) {  // checked build: an index left its buffer
+        st = TSNNLS_EBOUNDS;
+        if (info) info->status = st;
+    }
+    return st;
+}
+
+static int solve_on_lane_unchecked(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
+                                   double *x_out, const tsnnls_opts &o, tsnnls_info *info,
+                                   const SolveExtras *extras) {
+    NvtxSolve range(lane, "tsnnls_solve");
     if (info) std::memset(info, 0, sizeof(*info));
     std::memset(lane.st_host, 0, sizeof(DevStatus));
     if (choose_path(A, o, ctx.budget) == TSNNLS_PATH_LSQR)

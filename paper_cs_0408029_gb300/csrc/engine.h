@@ -49,6 +49,15 @@ struct Lane {
     std::vector<PhaseMark> marks;
     int64_t mark_launch0 = 0;
     tsnnls_phase_stat stats[TSNNLS_NUM_PHASES] = {};
+    bool nvtx_open = false;  // a phase range is open on the NVTX stack
+};
+
+// NVTX ranges for timeline tools (Nsight Systems): one per solve and one per
+// phase that prof_begin opens; inert unless a tool is attached.
+struct NvtxSolve {
+    Lane &l;
+    NvtxSolve(Lane &lane, const char *what);
+    ~NvtxSolve();
 };
 
 // Bracket a phase with events on the lane's stream (no-ops unless prof).

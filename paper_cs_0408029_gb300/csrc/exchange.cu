@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "common.cuh"
 
 namespace tsnnls {
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kExThreads)
 
     // exchange between F and G
     if (d == 2) {
-        if (tid == 0) inF[big] ^= 1;
+        if (tid == 0 && TS_IN(big, n)) inF[big] ^= 1;
     } else {
         for (int64_t j = tid; j < n; j += kExThreads)
             if (infeasible(inF[j], x[j], y[j])) inF[j] ^= 1;
@@ -200,26 +201,28 @@ cudaError_t launch_exchange(cudaStream_t s, int64_t n, double *x, double *y, uin
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__global__ void gather_rhs_kernel(const double *__restrict__ v, const int32_t *__restrict__ F,
+__global__ void gather_rhs_kernel(const double *__restrict__ v, int64_t n, const int32_t *__restrict__ F,
                                   int64_t k, T *__restrict__ out) {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < k;
-         a += (int64_t)gridDim.x * blockDim.x)
-        out[a] = F[a] >= 0 ? (T)v[F[a]] : T(0);  // -1: a variable held at zero
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = F[a];  // -1: a variable held at zero
+        out[a] = j >= 0 && TS_IN(j, n) ? (T)v[j] : T(0);
+    }
 }
 
 template <typename T>
-cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, const int32_t *F, int64_t k,
+cudaError_t launch_gather_rhs(cudaStream_t s, const double *v, int64_t n, const int32_t *F, int64_t k,
                               T *out) {
     if (k <= 0) return cudaSuccess;
     const int g = (int)std::min<int64_t>(cdiv(k, 256), num_sms() * 8);
-    gather_rhs_kernel<T><<<g, 256, 0, s>>>(v, F, k, out);
+    gather_rhs_kernel<T><<<g, 256, 0, s>>>(v, n, F, k, out);
     note_launches(1);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_gather_rhs<float>(cudaStream_t, const double *, const int32_t *,
+template cudaError_t launch_gather_rhs<float>(cudaStream_t, const double *, int64_t, const int32_t *,
                                               int64_t, float *);
-template cudaError_t launch_gather_rhs<double>(cudaStream_t, const double *, const int32_t *,
+template cudaError_t launch_gather_rhs<double>(cudaStream_t, const double *, int64_t, const int32_t *,
                                                int64_t, double *);
 
 // x_F += delta (FP64), and ||delta||_inf, ||x_F||_inf into the status.
@@ -230,12 +233,12 @@ template cudaError_t launch_gather_rhs<double>(cudaStream_t, const double *, con
 template <typename T>
 __global__ void __launch_bounds__(256)
     update_x_kernel(const T *__restrict__ delta, const int32_t *__restrict__ F, int64_t k,
-                    double *__restrict__ x, DevStatus *st) {
+                    double *__restrict__ x, int64_t n, DevStatus *st) {
     __shared__ double shd[8], shx[8];
     double dm = 0.0, xm = 0.0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < k; a += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = F[a];
-        if (j < 0) continue;  // a variable held at zero
+        if (j < 0 || !TS_IN(j, n)) continue;  // -1: a variable held at zero
         const double d = (double)delta[a];
         const double xn = x[j] + d;
         x[j] = xn;
@@ -264,20 +267,20 @@ __global__ void __launch_bounds__(256)
 
 template <typename T>
 cudaError_t launch_update_x(cudaStream_t s, const T *delta, const int32_t *F, int64_t k,
-                            double *x, DevStatus *st) {
+                            double *x, int64_t n, DevStatus *st) {
     static_assert(offsetof(DevStatus, xnorm) == offsetof(DevStatus, dnorm) + sizeof(double), "adjacent norms");
     cudaError_t e = cudaMemsetAsync(&st->dnorm, 0, 2 * sizeof(double), s);
     if (e != cudaSuccess) return e;
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(k, 256), num_sms()));
-    update_x_kernel<T><<<g, 256, 0, s>>>(delta, F, k, x, st);
+    update_x_kernel<T><<<g, 256, 0, s>>>(delta, F, k, x, n, st);
     note_launches(1);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_update_x<float>(cudaStream_t, const float *, const int32_t *,
-                                            int64_t, double *, DevStatus *);
+                                            int64_t, double *, int64_t, DevStatus *);
 template cudaError_t launch_update_x<double>(cudaStream_t, const double *, const int32_t *,
-                                             int64_t, double *, DevStatus *);
+                                             int64_t, double *, int64_t, DevStatus *);
 
 // ---------------------------------------------------------------------------
 // Settled decisions.  Before the last pivot only the signs of x_F and y_G
@@ -483,3 +486,5 @@ cudaError_t launch_y_from_s(cudaStream_t s, int64_t n, const double *sv, const u
 }
 
 }  // namespace tsnnls
+
+TSNNLS_CHECK_UNIT("exchange")

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "check.cuh"
 #include "engine.h"
 
 namespace tsnnls {
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kLT)
 // one row per thread, its nonzeros loaded eight at a time)
 template <typename V, int TPR>
 __global__ void __launch_bounds__(kLT)
-    lsqr_av_kernel(int64_t m, const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+    lsqr_av_kernel(int64_t m, int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                    const V *__restrict__ val, const V *__restrict__ dv, V *__restrict__ u,
                    const LsqrScalars *__restrict__ cur, double *__restrict__ part_u) {
     __shared__ double sh[kLT / 32];
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kLT)
                     a[q] = in ? val[p + q] : V(0);
                 }
 #pragma unroll
-                for (int q = 0; q < 8; ++q) s += a[q] * dv[c[q]];
+                for (int q = 0; q < 8; ++q) s += TS_IN(c[q], n) ? a[q] * dv[c[q]] : V(0);
             }
             const V un = s - vscale * u[r];
             u[r] = un;
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kLT)
                         a[q] = in ? val[p + q * TPR] : V(0);
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) s += a[q] * dv[c[q]];
+                    for (int q = 0; q < 4; ++q) s += TS_IN(c[q], n) ? a[q] * dv[c[q]] : V(0);
                 }
             }
 #pragma unroll
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(kLT)
 // first != 0: v is zero (start of a run).  CTA 0 stores beta in nxt.
 template <typename V, int TPR>
 __global__ void __launch_bounds__(kLT)
-    lsqr_atu_kernel(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+    lsqr_atu_kernel(int64_t n, int64_t m, const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                     const V *__restrict__ val, const V *__restrict__ D,
                     const uint8_t *__restrict__ inF, const V *__restrict__ u, V *__restrict__ v,
                     const double *__restrict__ part_u, int n_part_u, LsqrScalars *nxt,
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kLT)
                     a[q] = in ? val[p + q * TPR] : V(0);
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) s += a[q] * u[c[q]];
+                for (int q = 0; q < 4; ++q) s += TS_IN(c[q], m) ? a[q] * u[c[q]] : V(0);
             }
         }
 #pragma unroll
@@ -385,12 +386,12 @@ struct LsqrLaunch {
 
     template <int TPR>
     void av(const LsqrScalars *cur) {
-        lsqr_av_kernel<V, TPR><<<grid_for(m, TPR), kLT, 0, s>>>(m, row_ptr, col, val, dv, u, cur, part_u);
+        lsqr_av_kernel<V, TPR><<<grid_for(m, TPR), kLT, 0, s>>>(m, n, row_ptr, col, val, dv, u, cur, part_u);
         note_launches(1);
     }
     template <int TPR>
     void atu(LsqrScalars *nxt) {
-        lsqr_atu_kernel<V, TPR><<<grid_for(n, TPR), kLT, 0, s>>>(n, col_ptr, row_idx, cval, D, inF, u, v,
+        lsqr_atu_kernel<V, TPR><<<grid_for(n, TPR), kLT, 0, s>>>(n, m, col_ptr, row_idx, cval, D, inF, u, v,
                                                                   part_u, grid_for(m, tpr_r), nxt, part_v);
         note_launches(1);
     }
@@ -569,7 +570,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         prof_end(lane, 2.0 * csr_bytes + 2.0 * csc_bytes + 2.0 * sizeof(V) * nnz, 0.0);
         // c = A^T b (FP64), then F = {}, x = 0, y = -c
         prof_begin(lane, TSNNLS_PHASE_SPMV);
-        TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, bd, 0.0, nullptr, c, avg_col));
+        TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, bd, m, 0.0, nullptr, c, avg_col));
         prof_end(lane, csc_bytes + 8.0 * (m + n), 2.0 * nnz);
         TRY_CUDA_L(launch_init_state(s, n, c, x, y, inF, o.p_max, lane.st_dev));
 
@@ -610,14 +611,14 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
             for (;;) {
                 // FP64 residual r = b - A x and, for y and the stop test, s = A^T r
                 prof_begin(lane, TSNNLS_PHASE_SPMV);
-                TRY_CUDA_L(launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row));
+                TRY_CUDA_L(launch_spmv(s, m, row_ptr, col, val, -1.0, x, n, 1.0, bd, r, avg_row));
                 prof_end(lane, csr_bytes + 8.0 * (3.0 * m + n), 2.0 * nnz);
                 if (conv) break;
                 // inner LSQR on (A_F D) z = r
                 prof_begin(lane, TSNNLS_PHASE_LSQR);
                 lsqr_start_kernel<V><<<grid_for(m, L.tpr_r), kLT, 0, s>>>(m, n, r, u, v, w, z, part_u);
                 note_launches(1);
-                TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col));
+                TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, m, 0.0, nullptr, sv, avg_col));
                 L.vstart(sv, &sc[0]);
                 L.upd(&sc[0], &sc[0], 1);
                 for (int it = 0; it < inner; ++it) {
@@ -655,7 +656,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 prev = d;
             }
             prof_begin(lane, TSNNLS_PHASE_SPMV);
-            TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col));
+            TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, m, 0.0, nullptr, sv, avg_col));
             prof_end(lane, csc_bytes + 8.0 * (m + n), 2.0 * nnz);
             TRY_CUDA_L(launch_y_from_s(s, n, sv, inF, y));
             last_steps = steps;
@@ -663,8 +664,8 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         }
         if (status == TSNNLS_OK) {
             if (trace_rows == 0) {  // no pivot ran: r and s of x = 0
-                TRY_CUDA_L(launch_spmv(s, m, row_ptr, col, val, -1.0, x, 1.0, bd, r, avg_row));
-                TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, 0.0, nullptr, sv, avg_col));
+                TRY_CUDA_L(launch_spmv(s, m, row_ptr, col, val, -1.0, x, n, 1.0, bd, r, avg_row));
+                TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, m, 0.0, nullptr, sv, avg_col));
             }
             // KKT violation and the residual change of the last correction D z
             prof_begin(lane, TSNNLS_PHASE_VECTOR);
@@ -720,3 +721,5 @@ int solve_lsqr(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b, d
 }
 
 }  // namespace tsnnls
+
+TSNNLS_CHECK_UNIT("lsqr")

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "check.cuh"
 #include "common.cuh"
 
 namespace tsnnls {
@@ -39,11 +40,11 @@ __device__ __forceinline__ double warp_max(double v) {
 
 template <typename T>
 __global__ void scatter_list_kernel(int64_t len, const T *__restrict__ vals, const int32_t *__restrict__ list,
-                                    double *__restrict__ d) {
+                                    double *__restrict__ d, int64_t n) {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < len;
          a += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = list[a];
-        if (j >= 0) d[j] = (double)vals[a];
+        if (j >= 0 && TS_IN(j, n)) d[j] = (double)vals[a];
     }
 }
 
@@ -141,9 +142,9 @@ cudaError_t launch_quality(cudaStream_t s, int64_t m, int64_t n, const int64_t *
         cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double) * n, s);
         if (e != cudaSuccess) return e;
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(len, 256), num_sms() * 8));
-        scatter_list_kernel<T><<<g, 256, 0, s>>>(len, delta, list, d);
+        scatter_list_kernel<T><<<g, 256, 0, s>>>(len, delta, list, d, n);
         note_launches(1);
-        e = launch_spmv(s, m, row_ptr, col, val, 1.0, d, 0.0, nullptr, q, avg_row);
+        e = launch_spmv(s, m, row_ptr, col, val, 1.0, d, n, 0.0, nullptr, q, avg_row);
         if (e != cudaSuccess) return e;
     }
     const int parts = quality_parts();
@@ -166,7 +167,7 @@ cudaError_t launch_quality_scaled(cudaStream_t s, int64_t m, int64_t n, const in
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), num_sms() * 8));
         scatter_scaled_kernel<V><<<g, 256, 0, s>>>(n, D, z, inF, d);
         note_launches(1);
-        cudaError_t e = launch_spmv(s, m, row_ptr, col, val, 1.0, d, 0.0, nullptr, q, avg_row);
+        cudaError_t e = launch_spmv(s, m, row_ptr, col, val, 1.0, d, n, 0.0, nullptr, q, avg_row);
         if (e != cudaSuccess) return e;
     }
     const int parts = quality_parts();
@@ -195,3 +196,5 @@ template cudaError_t launch_quality_scaled<double>(cudaStream_t, int64_t, int64_
                                                    void *, DevStatus *);
 
 }  // namespace tsnnls
+
+TSNNLS_CHECK_UNIT("quality")

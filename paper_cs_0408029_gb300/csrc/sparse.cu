@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "common.cuh"
 
 namespace tsnnls {
@@ -15,11 +16,13 @@ namespace tsnnls {
 // ---------------------------------------------------------------------------
 // CSR -> CSC
 
-__global__ void csc_count_kernel(int64_t nnz, const int32_t *__restrict__ col,
+__global__ void csc_count_kernel(int64_t nnz, int64_t n, const int32_t *__restrict__ col,
                                  int32_t *__restrict__ cnt) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
-         e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[col[e]], 1);
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = col[e];
+        if (TS_IN(j, n)) atomicAdd(&cnt[j], 1);
+    }
 }
 
 // Exclusive scan of cnt[0..n) into ptr[0..n] (ptr[n] = total) by one CTA of
@@ -66,14 +69,17 @@ __global__ void __launch_bounds__(1024) csc_scan_kernel(int64_t n, const int32_t
     }
 }
 
-__global__ void csc_fill_kernel(int64_t m, const int64_t *__restrict__ row_ptr,
+__global__ void csc_fill_kernel(int64_t m, int64_t n, int64_t nnz, const int64_t *__restrict__ row_ptr,
                                 const int32_t *__restrict__ col, const double *__restrict__ val,
                                 int64_t *__restrict__ next, int32_t *__restrict__ row_idx,
                                 double *__restrict__ cval) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
          r += (int64_t)gridDim.x * blockDim.x) {
         for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-            unsigned long long p = atomicAdd((unsigned long long *)&next[col[e]], 1ull);
+            const int32_t j = col[e];
+            if (!TS_IN(j, n)) continue;
+            unsigned long long p = atomicAdd((unsigned long long *)&next[j], 1ull);
+            if (!TS_IN(p, nnz)) continue;
             row_idx[p] = (int32_t)r;
             cval[p] = val[e];
         }
@@ -136,14 +142,14 @@ cudaError_t launch_csr_to_csc(cudaStream_t s, int64_t m, int64_t n, int64_t nnz,
     if (e != cudaSuccess) return e;
     if (nnz > 0) {
         int g = (int)std::min<int64_t>(cdiv(nnz, 256), num_sms() * 16);
-        csc_count_kernel<<<g, 256, 0, s>>>(nnz, col, work);
+        csc_count_kernel<<<g, 256, 0, s>>>(nnz, n, col, work);
         note_launches(1);
     }
     csc_scan_kernel<<<1, 1024, 0, s>>>(n, work, col_ptr, scan_work);
     note_launches(1);
     if (nnz > 0) {
         int g = (int)std::min<int64_t>(cdiv(m, 128), num_sms() * 16);
-        csc_fill_kernel<<<g, 128, 0, s>>>(m, row_ptr, col, val, scan_work, row_idx, cval);
+        csc_fill_kernel<<<g, 128, 0, s>>>(m, n, nnz, row_ptr, col, val, scan_work, row_idx, cval);
         note_launches(1);
         int gs = (int)std::min<int64_t>(n, num_sms() * 8);
         csc_sort_kernel<<<gs, 256, 0, s>>>(n, col_ptr, row_idx, cval);
@@ -248,7 +254,10 @@ __global__ void __launch_bounds__(kGramThreads)
                 for (; q < nq && q_off[q] < w0 + wn; ++q) {
                     const int64_t s0 = max(q_off[q], w0) - w0;
                     const int64_t s1 = min(q_off[q + 1], w0 + wn) - w0;
-                    for (int64_t p = s0 + tid; p < s1; p += 32) acc[pr_i[p]] += pr_v[p];
+                    for (int64_t p = s0 + tid; p < s1; p += 32) {
+                        const int32_t i = pr_i[p];
+                        if (TS_IN(i, kGramChunk)) acc[i] += pr_v[p];
+                    }
                     __syncwarp();
                 }
             }
@@ -290,7 +299,7 @@ template cudaError_t launch_gram<double>(cudaStream_t, int64_t, int64_t, const i
 template <int TPR>
 __global__ void __launch_bounds__(256)
     spmv_kernel(int64_t rows, const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                const double *__restrict__ val, double alpha, const double *__restrict__ x,
+                const double *__restrict__ val, double alpha, const double *__restrict__ x, int64_t xlen,
                 double beta, const double *__restrict__ z, double *__restrict__ out) {
     // Lanes of one warp own 32/TPR consecutive rows; the loop runs on the
     // warp's first row so that every lane takes part in the shuffles.
@@ -304,7 +313,10 @@ __global__ void __launch_bounds__(256)
         double sum = 0.0;
         if (r < rows) {
             const int64_t a = ptr[r], e = ptr[r + 1];
-            for (int64_t p = a + sub; p < e; p += TPR) sum += val[p] * x[idx[p]];
+            for (int64_t p = a + sub; p < e; p += TPR) {
+                const int32_t j = idx[p];
+                if (TS_IN(j, xlen)) sum += val[p] * x[j];
+            }
         }
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, TPR);
@@ -313,26 +325,26 @@ __global__ void __launch_bounds__(256)
 }
 
 cudaError_t launch_spmv(cudaStream_t s, int64_t rows, const int64_t *ptr, const int32_t *idx,
-                        const double *val, double alpha, const double *x, double beta,
+                        const double *val, double alpha, const double *x, int64_t xlen, double beta,
                         const double *z, double *out, double avg_nnz) {
     if (rows == 0) return cudaSuccess;
     auto grid_for = [&](int tpr) {
         return (int)std::min<int64_t>(cdiv(rows * tpr, 256), num_sms() * 32);
     };
     if (avg_nnz <= 3) {
-        spmv_kernel<2><<<grid_for(2), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, beta, z, out);
+        spmv_kernel<2><<<grid_for(2), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, xlen, beta, z, out);
         note_launches(1);
     } else if (avg_nnz <= 6) {
-        spmv_kernel<4><<<grid_for(4), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, beta, z, out);
+        spmv_kernel<4><<<grid_for(4), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, xlen, beta, z, out);
         note_launches(1);
     } else if (avg_nnz <= 12) {
-        spmv_kernel<8><<<grid_for(8), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, beta, z, out);
+        spmv_kernel<8><<<grid_for(8), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, xlen, beta, z, out);
         note_launches(1);
     } else if (avg_nnz <= 24) {
-        spmv_kernel<16><<<grid_for(16), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, beta, z, out);
+        spmv_kernel<16><<<grid_for(16), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, xlen, beta, z, out);
         note_launches(1);
     } else {
-        spmv_kernel<32><<<grid_for(32), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, beta, z, out);
+        spmv_kernel<32><<<grid_for(32), 256, 0, s>>>(rows, ptr, idx, val, alpha, x, xlen, beta, z, out);
         note_launches(1);
     }
     return cudaGetLastError();
@@ -375,3 +387,5 @@ cudaError_t launch_validate(cudaStream_t s, int64_t m, int64_t n, int64_t nnz,
 }
 
 }  // namespace tsnnls
+
+TSNNLS_CHECK_UNIT("sparse")

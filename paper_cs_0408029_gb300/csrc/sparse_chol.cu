@@ -30,6 +30,7 @@
 #include <cuda/atomic>
 #include <vector>
 
+#include "check.cuh"
 #include "common.cuh"
 #include "dense_block.cuh"
 #include "sparse_sym.h"
@@ -113,7 +114,7 @@ __global__ void sp_permF_kernel(int64_t n, const int32_t *__restrict__ perm, con
                                 int32_t *__restrict__ permF) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = perm[p];
-        permF[p] = inF[j] ? j : -1;
+        permF[p] = TS_IN(j, n) && inF[j] ? j : -1;
     }
 }
 
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(256, 1)
         // G' in this supernode's columns
         for (int64_t p = D.gptr[f] + tid; p < D.gptr[f + w]; p += 256) {
             const int32_t io = D.grow_orig[p], jo = D.gcol_orig[p];
+            if (!TS_IN(io, D.n) || !TS_IN(jo, D.n) || !TS_IN(D.gpos[p] - D.L_off[s], ld * w)) continue;
             const T v = (inF[io] && inF[jo]) ? (T)D.gval[p] : (io == jo ? T(1) : T(0));
             L[D.gpos[p]] = v;
         }
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(256, 1)
                 const int64_t i = e % hc, j = e / hc;
                 if (i < j) continue;
                 const int32_t li = rel[i], lj = rel[j];  // li >= lj: rows keep their order
+                if (!TS_IN(li, h) || !TS_IN(lj, li + 1)) continue;
                 const T v = Uc[j * lduc + i];
                 if (lj < w) P[(int64_t)lj * ld + li] += v;
                 else U[(int64_t)(lj - w) * ldu + (li - w)] += v;
@@ -294,7 +297,10 @@ __global__ void __launch_bounds__(kSpT)
             const int64_t hc = D.rows_off[c + 1] - D.rows_off[c] - wc;
             const T *uc = ua + D.u_off[c];
             const int32_t *rel = D.rel + D.u_off[c];
-            for (int64_t i = tid; i < hc; i += kSpT) a[rel[i]] -= __ldcg(uc + i);
+            for (int64_t i = tid; i < hc; i += kSpT) {
+                const int32_t r = rel[i];
+                if (TS_IN(r, h)) a[r] -= __ldcg(uc + i);
+            }
             __syncthreads();
         }
         const T *Ws = Wa + D.W_off[s];
@@ -344,7 +350,10 @@ __global__ void __launch_bounds__(kSpT)
         const int c = tid % w, g = tid / w;
         T acc = T(0);
         if (g < G)
-            for (int64_t p = w + g; p < h; p += G) acc += Ls[(int64_t)c * ld + p] * __ldcg(v + rows[p]);
+            for (int64_t p = w + g; p < h; p += G) {
+                const int32_t r = rows[p];
+                if (TS_IN(r, D.n)) acc += Ls[(int64_t)c * ld + p] * __ldcg(v + r);
+            }
         part[tid] = acc;
         __syncthreads();
         if (tid < w) {
@@ -534,3 +543,5 @@ template struct SparseChol<float>;
 template struct SparseChol<double>;
 
 }  // namespace tsnnls
+
+TSNNLS_CHECK_UNIT("sparse_chol")

@@ -99,6 +99,27 @@ def test_autotune_picks_candidate_widths(env):
     assert st == ts.OK
 
 
+def test_autotune_cache_hit_skips_timing(env, tmp_path):
+    """First call tunes and records the widths under this device's key; the
+    second finds them; a seeded entry is installed as it stands."""
+    ts, ctx, torch = env
+    path = str(tmp_path / "widths.json")
+    key = ctx.batch_tune_key(ts.MIXED, per_bucket=8)
+    assert "sm_10" in key and "mixed" in key
+    nb, hit = ctx.batch_autotune_cached(path, ts.MIXED, per_bucket=8)
+    assert not hit and list(ts.tune_cache_get(path, key)) == list(nb)
+    nb2, hit2 = ctx.batch_autotune_cached(path, ts.MIXED, per_bucket=8)
+    assert hit2 and list(nb2) == list(nb)
+    seeded = str(tmp_path / "seeded.json")
+    ts.tune_cache_put(seeded, key, [16, 16, 16, 16, 16])
+    nb3, hit3 = ctx.batch_autotune_cached(seeded, ts.MIXED, per_bucket=8)
+    assert hit3 and list(nb3) == [16] * 5
+    probs = _batch(104, 8, 32, 300)
+    st, stat, info, xs = _run(ts, ctx, torch, probs, "mixed")
+    assert st == ts.OK
+    ts.Context.batch_set_panel([32] * 5, ts.MIXED)  # the built-in table
+
+
 def test_batch_traces_match_oracle_and_full_refinement(env, oracle_mod):
     """Every problem's pivot trace equals the oracle's (A rounded to FP32 on
     both sides); refining intermediate pivots only until their signs are
