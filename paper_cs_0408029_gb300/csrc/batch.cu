@@ -560,7 +560,7 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
 // rhs <- (L L^T)^{-1} rhs inside one CTA: 32-row blocks, the diagonal block
 // solved by warp 0 with shuffles, the rest of the column updated by all threads.
 template <typename T>
-__device__ void cta_chol_solve(const T *L, int k, int lds, T *rhs) {
+__device__ __noinline__ void cta_chol_solve(const T *L, int k, int lds, T *rhs) {
     const int tid = threadIdx.x, lane = tid & 31;
     for (int B0 = 0; B0 < k; B0 += 32) {  // L z = rhs
         const int nb = min(32, k - B0);
@@ -615,15 +615,32 @@ __device__ void cta_chol_solve(const T *L, int k, int lds, T *rhs) {
             if (lane < nb) rhs[B0 + lane] = v;
         }
         __syncthreads();
-        // rows above: rhs[r] -= sum_c L(B0 + c, r) w_c for r < B0 (L^T row r)
-        for (int r = tid; r < B0; r += kBT) {
-            T lv[32];
+        // rows above: rhs[r] -= sum_c L(B0 + c, r) w_c for r < B0 (L^T row
+        // r).  A warp takes 32 rows r0 .. r0 + 31: lane c loads L(B0 + c, r)
+        // down the column r (one 128-byte line per load, 32 in flight) and
+        // scales it by w_c; five butterfly steps then leave in lane q the sum
+        // over c for row r0 + q (at each step a lane keeps the half of its
+        // partial sums selected by its own bit and adds its partner's).
+        {
+            const int lane = tid & 31;
+            const T wl = lane < nb ? rhs[B0 + lane] : T(0);
+            for (int t = tid >> 5; t < B0 / 32; t += kBWarps) {
+                const int r0 = 32 * t;
+                T v[32];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) lv[c] = c < nb ? L[(B0 + c) + (int64_t)r * lds] : T(0);
-            T s = T(0);
+                for (int q = 0; q < 32; ++q) v[q] = lane < nb ? L[(B0 + lane) + (int64_t)(r0 + q) * lds] * wl : T(0);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) s += lv[c] * rhs[B0 + c];
-            rhs[r] -= s;
+                for (int sft = 16; sft >= 1; sft >>= 1) {
+                    const bool upper = (lane & sft) != 0;
+#pragma unroll
+                    for (int q = 0; q < sft; ++q) {
+                        const T send = upper ? v[q] : v[q + sft];
+                        const T keep = upper ? v[q + sft] : v[q];
+                        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+                    }
+                }
+                rhs[r0 + lane] -= v[0];
+            }
         }
         __syncthreads();
     }
@@ -659,51 +676,106 @@ __device__ __forceinline__ float2 ff_split(double v) {
     return make_float2(h, (float)(v - (double)h));
 }
 
-// r = b - A_F x_F with the double-float products above; x_F (split) and F
-// are staged in shared memory (the factorisation's panel area, free here)
-// when they fit, and r is stored split into P.r.
-__device__ void cta_residual_ff(const BatchProb &P, int k, void *scr, int scr_bytes) {
+// r = b - A_F x_F with the double-float products above, stored split into
+// P.r.  One CTA streams all of A here, so what bounds it is the bytes it
+// keeps in flight: x is scattered over all n columns (0 outside F) as hi /
+// lo FP32 halves in shared memory, and a warp reads a whole row of A in
+// 16-byte chunks, eight per lane issued before the first is used.  A row's
+// chunks start at its first 16-byte boundary, h = 0..3 columns in; copy q of
+// x is shifted by q columns (xq[t] = x[t + q]) so that every chunk finds its
+// four x values in one aligned 16-byte shared load of copy h.  Columns
+// before the boundary and after the last whole chunk are taken one by one.
+// Without room for the four copies, lanes walk the F list instead.
+__device__ __noinline__ void cta_residual_ff(const BatchProb &P, int k, void *scr, int scr_bytes) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool staged = 12 * k <= scr_bytes;
-    float2 *xs = staged ? static_cast<float2 *>(scr) : reinterpret_cast<float2 *>(P.y);
-    const int32_t *F = P.F;
-    if (staged) {
-        int32_t *Fs = reinterpret_cast<int32_t *>(static_cast<float2 *>(scr) + k);
+    const int n = P.n;
+    const int np4 = (n + 7) & ~3;  // entries per copy: columns t + q < n for q <= 3
+    float2 *rs = reinterpret_cast<float2 *>(P.r);
+    if (32 * np4 <= scr_bytes) {
+        float *xc = static_cast<float *>(scr);  // copy q: hi at xc[2q np4], lo at xc[(2q + 1) np4]
+        for (int t = threadIdx.x; t < 8 * np4; t += kBT) xc[t] = 0.f;
+        __syncthreads();
         for (int a = threadIdx.x; a < k; a += kBT) {
             const int j = P.F[a];
-            Fs[a] = j;
-            xs[a] = ff_split(P.x[j]);
+            const float2 v = ff_split(P.x[j]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j >= q) {
+                    xc[2 * q * np4 + j - q] = v.x;
+                    xc[(2 * q + 1) * np4 + j - q] = v.y;
+                }
         }
-        F = Fs;
-    } else {
-        for (int a = threadIdx.x; a < k; a += kBT) xs[a] = ff_split(P.x[P.F[a]]);
+        __syncthreads();
+        constexpr int U = 8;
+        for (int i = warp; i < P.m; i += kBWarps) {
+            const float *row = P.A + (int64_t)i * n;
+            const int h = min(n, (int)((16u - ((uint32_t)reinterpret_cast<uintptr_t>(row) & 15u)) & 15u) >> 2);
+            const int nch = (n - h) >> 2;  // whole 16-byte chunks
+            const float4 *r4 = reinterpret_cast<const float4 *>(row + h);
+            const float4 *xh4 = reinterpret_cast<const float4 *>(xc + 2 * h * np4);
+            const float4 *xl4 = reinterpret_cast<const float4 *>(xc + (2 * h + 1) * np4);
+            float hs = 0.f, ls = 0.f;
+            // the columns before the first boundary and after the last chunk
+            const int tail0 = h + 4 * nch;
+            if (lane < h) ff_acc(hs, ls, row[lane], xc[lane], xc[np4 + lane]);
+            if (tail0 + lane < n) ff_acc(hs, ls, row[tail0 + lane], xc[tail0 + lane], xc[np4 + tail0 + lane]);
+            for (int c0 = 0; c0 < nch; c0 += 32 * U) {
+                float4 v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int c = c0 + lane + 32 * u;
+                    v[u] = c < nch ? __ldcg(r4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int c = c0 + lane + 32 * u;
+                    if (c < nch) {
+                        const float4 xh = xh4[c], xl = xl4[c];
+                        ff_acc(hs, ls, v[u].x, xh.x, xl.x);
+                        ff_acc(hs, ls, v[u].y, xh.y, xl.y);
+                        ff_acc(hs, ls, v[u].z, xh.z, xl.z);
+                        ff_acc(hs, ls, v[u].w, xh.w, xl.w);
+                    }
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float hh = __shfl_xor_sync(0xffffffffu, hs, o), ll = __shfl_xor_sync(0xffffffffu, ls, o);
+                ff_add(hs, ls, hh, ll);
+            }
+            if (lane == 0) rs[i] = ff_split(P.b[i] - ((double)hs + (double)ls));
+        }
+        __syncthreads();
+        return;
     }
+    float2 *xs = reinterpret_cast<float2 *>(P.y);
+    for (int a = threadIdx.x; a < k; a += kBT) xs[a] = ff_split(P.x[P.F[a]]);
     __syncthreads();
-    float2 *rs = reinterpret_cast<float2 *>(P.r);
     for (int i = warp; i < P.m; i += kBWarps) {
-        float h = 0.f, l = 0.f, h2 = 0.f, l2 = 0.f;
-        const float *row = P.A + (int64_t)i * P.n;
+        float hs = 0.f, ls = 0.f, h2 = 0.f, l2 = 0.f;
+        const float *row = P.A + (int64_t)i * n;
         int a = lane;
         for (; a + 32 < k; a += 64) {  // two gathers in flight per lane
             const float2 v0 = xs[a], v1 = xs[a + 32];
-            const float a0 = row[F[a]], a1 = row[F[a + 32]];
-            ff_acc(h, l, a0, v0.x, v0.y);
+            const float a0 = row[P.F[a]], a1 = row[P.F[a + 32]];
+            ff_acc(hs, ls, a0, v0.x, v0.y);
             ff_acc(h2, l2, a1, v1.x, v1.y);
         }
-        if (a < k) ff_acc(h, l, row[F[a]], xs[a].x, xs[a].y);
-        ff_add(h, l, h2, l2);
+        if (a < k) ff_acc(hs, ls, row[P.F[a]], xs[a].x, xs[a].y);
+        ff_add(hs, ls, h2, l2);
         for (int o = 16; o > 0; o >>= 1) {
-            const float hh = __shfl_xor_sync(0xffffffffu, h, o), ll = __shfl_xor_sync(0xffffffffu, l, o);
-            ff_add(h, l, hh, ll);
+            const float hh = __shfl_xor_sync(0xffffffffu, hs, o), ll = __shfl_xor_sync(0xffffffffu, ls, o);
+            ff_add(hs, ls, hh, ll);
         }
-        if (lane == 0) rs[i] = ff_split(P.b[i] - ((double)h + (double)l));
+        if (lane == 0) rs[i] = ff_split(P.b[i] - ((double)hs + (double)ls));
     }
     __syncthreads();
 }
 
 // s_j = (A^T r)_j with r split in P.r (staged in shared memory when it
-// fits); only the F columns unless all_cols.
-__device__ void cta_atr_ff(const BatchProb &P, bool all_cols, void *scr, int scr_bytes) {
+// fits); only the F columns unless all_cols.  Threads over columns (a
+// warp's loads of one row are one 128-byte line), rows in groups of 16
+// whose loads are all issued before the first product, in row order.
+__device__ __noinline__ void cta_atr_ff(const BatchProb &P, bool all_cols, void *scr, int scr_bytes) {
     const bool staged = 8 * P.m <= scr_bytes;
     const float2 *rs = reinterpret_cast<const float2 *>(P.r);
     if (staged) {
@@ -712,16 +784,25 @@ __device__ void cta_atr_ff(const BatchProb &P, bool all_cols, void *scr, int scr
         __syncthreads();
         rs = rsm;
     }
-    for (int j = threadIdx.x; j < P.n; j += kBT) {
+    const int n = P.n, m = P.m;
+    constexpr int R = 16;
+    for (int j = threadIdx.x; j < n; j += kBT) {
         if (!all_cols && !P.inF[j]) continue;
-        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;  // two chains for ILP
+        const float *col = P.A + j;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;  // two chains, even and odd rows
         int i = 0;
-        for (; i + 1 < P.m; i += 2) {
-            const float2 v0 = rs[i], v1 = rs[i + 1];
-            ff_acc(h0, l0, P.A[(int64_t)i * P.n + j], v0.x, v0.y);
-            ff_acc(h1, l1, P.A[(int64_t)(i + 1) * P.n + j], v1.x, v1.y);
+        for (; i + R <= m; i += R) {
+            float a[R];
+#pragma unroll
+            for (int u = 0; u < R; ++u) a[u] = __ldcg(col + (int64_t)(i + u) * n);
+#pragma unroll
+            for (int u = 0; u < R; u += 2) {
+                const float2 v0 = rs[i + u], v1 = rs[i + u + 1];
+                ff_acc(h0, l0, a[u], v0.x, v0.y);
+                ff_acc(h1, l1, a[u + 1], v1.x, v1.y);
+            }
         }
-        if (i < P.m) ff_acc(h0, l0, P.A[(int64_t)i * P.n + j], rs[i].x, rs[i].y);
+        for (; i < m; ++i) ff_acc(h0, l0, col[(int64_t)i * n], rs[i].x, rs[i].y);
         ff_add(h0, l0, h1, l1);
         P.s[j] = (double)h0 + (double)l0;
     }
@@ -966,12 +1047,33 @@ __global__ void __launch_bounds__(kBT, 1)
             k = sh_k;
             const int lds = P.ld;
             if (k > 0) {
-                // gather S = G_FF (lower)
-                for (int e = tid; e < k * k; e += kBT) {
-                    const int bcol = e / k, a = e % k;
-                    if (a >= bcol) S[a + (int64_t)bcol * lds] = Gsrc[P.F[a] + (int64_t)P.F[bcol] * P.ld];
+                // gather S = G_FF (lower): F staged in shared memory (the
+                // panel area, free until the factorisation), warps over
+                // columns, lanes over rows with four loads in flight
+                {
+                    int32_t *Fs = reinterpret_cast<int32_t *>(panel);
+                    for (int a = tid; a < k; a += kBT) Fs[a] = P.F[a];
+                    __syncthreads();
+                    const int lane = tid & 31;
+                    for (int bcol = tid >> 5; bcol < k; bcol += kBWarps) {
+                        const T *gc = Gsrc + (int64_t)Fs[bcol] * P.ld;
+                        T *sc = S + (int64_t)bcol * lds;
+                        for (int a0 = bcol; a0 < k; a0 += 128) {
+                            T v[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int a = a0 + lane + 32 * u;
+                                v[u] = a < k ? gc[Fs[a]] : T(0);
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int a = a0 + lane + 32 * u;
+                                if (a < k) sc[a] = v[u];
+                            }
+                        }
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
                 const int info = cta_cholesky<T>(S, k, lds, P.nb, panel, diag, shi);
                 if (info) { status = TSNNLS_ENOTPD; break; }
                 for (int a = tid; a < k; a += kBT) rhs[a] = (T)P.c[P.F[a]];

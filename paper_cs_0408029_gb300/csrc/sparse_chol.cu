@@ -75,16 +75,6 @@ __device__ bool sp_wait_all(const SpDev &D, const int32_t *flags, const int32_t 
     return *ok_sh != 0;
 }
 
-// first p in [lo, hi) with rows[p] >= v
-__device__ __forceinline__ int64_t sp_lower_bound(const int32_t *rows, int64_t lo, int64_t hi, int32_t v) {
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (rows[mid] < v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // G = A^T A on its pattern: one thread per stored entry, a merge of the two
 // sorted columns of A (rows ascending), summed in row order.
 __global__ void sp_gram_values_kernel(int64_t nnzg, const int32_t *__restrict__ orow, const int32_t *__restrict__ ocol,
