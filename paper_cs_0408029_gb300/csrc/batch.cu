@@ -176,13 +176,20 @@ __device__ __noinline__ void tc_trailing_update(float *S, int lds, int R0, int n
         while ((I + 1) * (I + 2) / 2 <= tb) ++I;
         const int J = tb - I * (I + 1) / 2;
         const int i0 = I * 32, j0 = J * 32;
+        // the accumulators start as the tile of C, all 32 loads issued
+        // before the MMAs so that their latency passes under them, and the
+        // MMAs add (-X) X^T (the A fragments with the sign bit flipped)
         float acc[2][4][4];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+                for (int q = 0; q < 4; ++q) {
+                    const int r = i0 + 16 * a + g + (q >= 2 ? 8 : 0);
+                    const int c = j0 + 8 * b + 2 * t + (q & 1);
+                    acc[a][b][q] = (r < nr && c < nr && r >= c) ? S[(R0 + r) + (int64_t)(R0 + c) * lds] : 0.f;
+                }
 #pragma unroll
         for (int k0 = 0; k0 < 32; k0 += 8) {
             uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
@@ -193,6 +200,11 @@ __device__ __noinline__ void tc_trailing_update(float *S, int lds, int R0, int n
                 split_tf32(X(ra + 8, k0 + t), ah[a][1], al[a][1]);
                 split_tf32(X(ra, k0 + t + 4), ah[a][2], al[a][2]);
                 split_tf32(X(ra + 8, k0 + t + 4), ah[a][3], al[a][3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    ah[a][q] ^= 0x80000000u;
+                    al[a][q] ^= 0x80000000u;
+                }
             }
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
@@ -209,10 +221,6 @@ __device__ __noinline__ void tc_trailing_update(float *S, int lds, int R0, int n
                     mma_tf32_16x8x8(acc[a][b], al[a], bh[b]);
                 }
         }
-        // all 32 loads of C before any store (a store could alias a later
-        // load as far as the compiler can tell, which would serialise every
-        // read-modify-write on its memory latency)
-        float cv[2][4][4];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -221,18 +229,7 @@ __device__ __noinline__ void tc_trailing_update(float *S, int lds, int R0, int n
                 for (int q = 0; q < 4; ++q) {
                     const int r = i0 + 16 * a + g + (q >= 2 ? 8 : 0);
                     const int c = j0 + 8 * b + 2 * t + (q & 1);
-                    cv[a][b][q] = (r < nr && c < nr && r >= c) ? S[(R0 + r) + (int64_t)(R0 + c) * lds] : 0.f;
-                }
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int r = i0 + 16 * a + g + (q >= 2 ? 8 : 0);
-                    const int c = j0 + 8 * b + 2 * t + (q & 1);
-                    if (r < nr && c < nr && r >= c)
-                        S[(R0 + r) + (int64_t)(R0 + c) * lds] = cv[a][b][q] - acc[a][b][q];
+                    if (r < nr && c < nr && r >= c) S[(R0 + r) + (int64_t)(R0 + c) * lds] = acc[a][b][q];
                 }
     }
 }
@@ -455,11 +452,20 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
                         xr[c] = s / diag[c * 65 + c];
                     }
                 }
+                if constexpr (sizeof(T) == 4) {
+                    // 16-byte stores (pitch 36: rows 144 bytes apart, no bank conflict)
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    panel[r * PP + c] = xr[c];
-                    if (c < kb) S[(R0 + r) + (int64_t)(K + c) * lds] = xr[c];
+                    for (int c4 = 0; c4 < 8; ++c4) {
+                        const T v4[4] = {xr[4 * c4], xr[4 * c4 + 1], xr[4 * c4 + 2], xr[4 * c4 + 3]};
+                        st4(&panel[r * PP + 4 * c4], v4);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) panel[r * PP + c] = xr[c];
                 }
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c < kb) S[(R0 + r) + (int64_t)(K + c) * lds] = xr[c];
             }
         } else {
         for (int r = tid; r < nr; r += kBT) {
@@ -557,90 +563,126 @@ __device__ int cta_cholesky(T *S, int k, int lds, int nb, T *panel, T *diag, int
     return info;
 }
 
-// rhs <- (L L^T)^{-1} rhs inside one CTA: 32-row blocks, the diagonal block
-// solved by warp 0 with shuffles, the rest of the column updated by all threads.
+// Warp 0's solves with one 32 x 32 diagonal block of L at B0 (nb rows):
+// lane = row (forward, L z = v) or column (backward, L^T w = v) of the block,
+// its entries loaded before the serial shuffle steps.
+template <typename T>
+__device__ __forceinline__ void warp_diag_fwd(const T *L, int lds, int B0, int nb, T *rhs) {
+    const int lane = threadIdx.x & 31;
+    T l[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) l[c] = (c < nb && lane < nb) ? L[(B0 + lane) + (int64_t)(B0 + c) * lds] : T(0);
+    const T inv = lane < nb ? T(1) / L[(B0 + lane) + (int64_t)(B0 + lane) * lds] : T(0);
+    T v = lane < nb ? rhs[B0 + lane] : T(0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        if (c < nb) {
+            const T zc = __shfl_sync(0xffffffffu, v * inv, c);
+            if (lane == c) v = zc;
+            if (lane > c) v -= l[c] * zc;
+        }
+    }
+    if (lane < nb) rhs[B0 + lane] = v;
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_diag_bwd(const T *L, int lds, int B0, int nb, T *rhs) {
+    const int lane = threadIdx.x & 31;
+    T lt[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) lt[c] = (c < nb && lane < nb) ? L[(B0 + c) + (int64_t)(B0 + lane) * lds] : T(0);
+    const T inv = lane < nb ? T(1) / L[(B0 + lane) + (int64_t)(B0 + lane) * lds] : T(0);
+    T v = lane < nb ? rhs[B0 + lane] : T(0);
+#pragma unroll
+    for (int c = 31; c >= 0; --c) {
+        if (c < nb) {
+            const T wc = __shfl_sync(0xffffffffu, v * inv, c);
+            if (lane == c) v = wc;
+            if (lane < c) v -= lt[c] * wc;
+        }
+    }
+    if (lane < nb) rhs[B0 + lane] = v;
+}
+
+// rhs[r0 + q] -= sum_c L(B0 + c, r0 + q) w_c for the 32 rows r0 .. r0 + 31
+// of L^T above the block at B0 (nb columns): lane c loads L(B0 + c, r) down
+// the column r (one 128-byte line per load, 32 in flight) scaled by w_c =
+// wl; five butterfly steps then leave in lane q the sum over c for row
+// r0 + q (at each step a lane keeps the half of its partial sums selected
+// by its own bit and adds its partner's).
+template <typename T>
+__device__ __forceinline__ void warp_bwd_tile(const T *L, int lds, int B0, int nb, int r0, T wl, T *rhs) {
+    const int lane = threadIdx.x & 31;
+    T v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = lane < nb ? L[(B0 + lane) + (int64_t)(r0 + q) * lds] * wl : T(0);
+#pragma unroll
+    for (int sft = 16; sft >= 1; sft >>= 1) {
+        const bool upper = (lane & sft) != 0;
+#pragma unroll
+        for (int q = 0; q < sft; ++q) {
+            const T send = upper ? v[q] : v[q + sft];
+            const T keep = upper ? v[q + sft] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+        }
+    }
+    rhs[r0 + lane] -= v[0];
+}
+
+// rhs <- (L L^T)^{-1} rhs inside one CTA, by 32-row blocks with a look-ahead
+// of one block: while warps 1.. apply block b's solution to the rows beyond
+// block b + 1, warp 0 applies it to the 32 rows of block b + 1 and solves
+// that block's diagonal system, so the serial shuffle chain of each diagonal
+// block runs beside the bulk update instead of between two barriers.
 template <typename T>
 __device__ __noinline__ void cta_chol_solve(const T *L, int k, int lds, T *rhs) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    for (int B0 = 0; B0 < k; B0 += 32) {  // L z = rhs
-        const int nb = min(32, k - B0);
-        if (tid < 32) {
-            // lane = row of the 32 x 32 diagonal block, loaded before the
-            // serial steps (l[c] = L(B0 + lane, B0 + c)); d = its diagonal entry
-            T l[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (k <= 0) return;
+    if (warp == 0) warp_diag_fwd<T>(L, lds, 0, min(32, k), rhs);  // L z = rhs
+    __syncthreads();
+    for (int B0 = 0; B0 + 32 < k; B0 += 32) {
+        const int N0 = B0 + 32, nn = min(32, k - N0);  // the next block
+        if (warp == 0) {
+            if (lane < nn) {
+                const int r = N0 + lane;
+                T lv[32];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) l[c] = (c < nb && lane < nb) ? L[(B0 + lane) + (int64_t)(B0 + c) * lds] : T(0);
-            const T inv = lane < nb ? T(1) / L[(B0 + lane) + (int64_t)(B0 + lane) * lds] : T(0);
-            T v = lane < nb ? rhs[B0 + lane] : T(0);
+                for (int c = 0; c < 32; ++c) lv[c] = L[r + (int64_t)(B0 + c) * lds];
+                T sum = T(0);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                if (c < nb) {
-                    const T zc = __shfl_sync(0xffffffffu, v * inv, c);
-                    if (lane == c) v = zc;
-                    if (lane > c) v -= l[c] * zc;
-                }
+                for (int c = 0; c < 32; ++c) sum += lv[c] * rhs[B0 + c];
+                rhs[r] -= sum;
             }
-            if (lane < nb) rhs[B0 + lane] = v;
-        }
-        __syncthreads();
-        for (int r = B0 + nb + tid; r < k; r += kBT) {
-            T lv[32];
+            __syncwarp();
+            warp_diag_fwd<T>(L, lds, N0, nn, rhs);
+        } else {
+            for (int r = N0 + 32 + (tid - 32); r < k; r += kBT - 32) {
+                T lv[32];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) lv[c] = c < nb ? L[r + (int64_t)(B0 + c) * lds] : T(0);
-            T s = T(0);
+                for (int c = 0; c < 32; ++c) lv[c] = L[r + (int64_t)(B0 + c) * lds];
+                T sum = T(0);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) s += lv[c] * rhs[B0 + c];
-            rhs[r] -= s;
+                for (int c = 0; c < 32; ++c) sum += lv[c] * rhs[B0 + c];
+                rhs[r] -= sum;
+            }
         }
         __syncthreads();
     }
     const int nblk = (k + 31) / 32;
-    for (int bi = nblk - 1; bi >= 0; --bi) {  // L^T w = z
+    {  // L^T w = z
+        const int B0 = (nblk - 1) * 32;
+        if (warp == 0) warp_diag_bwd<T>(L, lds, B0, k - B0, rhs);
+    }
+    __syncthreads();
+    for (int bi = nblk - 1; bi > 0; --bi) {
         const int B0 = bi * 32, nb = min(32, k - B0);
-        if (tid < 32) {
-            // lane = column of the block: lt[c] = L(B0 + c, B0 + lane)
-            T lt[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) lt[c] = (c < nb && lane < nb) ? L[(B0 + c) + (int64_t)(B0 + lane) * lds] : T(0);
-            const T inv = lane < nb ? T(1) / L[(B0 + lane) + (int64_t)(B0 + lane) * lds] : T(0);
-            T v = lane < nb ? rhs[B0 + lane] : T(0);
-#pragma unroll
-            for (int c = 31; c >= 0; --c) {
-                if (c < nb) {
-                    const T wc = __shfl_sync(0xffffffffu, v * inv, c);
-                    if (lane == c) v = wc;
-                    if (lane < c) v -= lt[c] * wc;
-                }
-            }
-            if (lane < nb) rhs[B0 + lane] = v;
-        }
-        __syncthreads();
-        // rows above: rhs[r] -= sum_c L(B0 + c, r) w_c for r < B0 (L^T row
-        // r).  A warp takes 32 rows r0 .. r0 + 31: lane c loads L(B0 + c, r)
-        // down the column r (one 128-byte line per load, 32 in flight) and
-        // scales it by w_c; five butterfly steps then leave in lane q the sum
-        // over c for row r0 + q (at each step a lane keeps the half of its
-        // partial sums selected by its own bit and adds its partner's).
-        {
-            const int lane = tid & 31;
-            const T wl = lane < nb ? rhs[B0 + lane] : T(0);
-            for (int t = tid >> 5; t < B0 / 32; t += kBWarps) {
-                const int r0 = 32 * t;
-                T v[32];
-#pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = lane < nb ? L[(B0 + lane) + (int64_t)(r0 + q) * lds] * wl : T(0);
-#pragma unroll
-                for (int sft = 16; sft >= 1; sft >>= 1) {
-                    const bool upper = (lane & sft) != 0;
-#pragma unroll
-                    for (int q = 0; q < sft; ++q) {
-                        const T send = upper ? v[q] : v[q + sft];
-                        const T keep = upper ? v[q + sft] : v[q];
-                        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
-                    }
-                }
-                rhs[r0 + lane] -= v[0];
-            }
+        const T wl = lane < nb ? rhs[B0 + lane] : T(0);
+        if (warp == 0) {
+            warp_bwd_tile<T>(L, lds, B0, nb, B0 - 32, wl, rhs);  // the rows of block bi - 1
+            __syncwarp();
+            warp_diag_bwd<T>(L, lds, B0 - 32, 32, rhs);
+        } else {
+            for (int t = warp - 1; t < bi - 1; t += kBWarps - 1) warp_bwd_tile<T>(L, lds, B0, nb, 32 * t, wl, rhs);
         }
         __syncthreads();
     }
