@@ -107,6 +107,13 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # nvidia-smi takes a moment to start: wait (at most 5 s) for its first
+        # sample so that a short timed region is sampled too
+        t0 = time.time()
+        while self.proc and self.proc.poll() is None and time.time() - t0 < 5.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *exc):

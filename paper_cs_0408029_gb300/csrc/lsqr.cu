@@ -37,7 +37,11 @@ struct LsqrScalars {
 };
 
 constexpr int kLT = 256;
-constexpr int kMaxPartials = 4096;  // cap of the per-CTA partial sums (>= 8 CTAs per SM)
+constexpr int kMaxPartials = 4096;  // capacity of the per-CTA partial sums
+
+// CTAs of a reduction kernel: eight per SM at most (every CTA of the next
+// kernel sums all the partials, so more CTAs than fit at once only add reads)
+inline int64_t partial_cap() { return std::min<int64_t>(kMaxPartials, (int64_t)num_sms() * 8); }
 
 // Sum of `count` partials in a fixed order, broadcast to the CTA.
 __device__ __forceinline__ double sum_partials(const double *__restrict__ part, int count,
@@ -154,12 +158,16 @@ __global__ void __launch_bounds__(kLT)
 }
 
 // av: u^ <- A dv - (alpha / beta) u^, dv = D v   (TPR lanes per row; TPR = 1:
-// one row per thread, its nonzeros loaded eight at a time)
+// one row per thread, its nonzeros loaded eight at a time; with vec (FP32
+// values, index and value arrays 16-byte aligned) the entries from the
+// row's first 16-byte boundary on come as int4 / float4 pairs, two of each
+// before the gathers, so that fewer, wider loads are in flight; the sum is
+// taken in the row's order either way)
 template <typename V, int TPR>
 __global__ void __launch_bounds__(kLT)
     lsqr_av_kernel(int64_t m, int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                    const V *__restrict__ val, const V *__restrict__ dv, V *__restrict__ u,
-                   const LsqrScalars *__restrict__ cur, double *__restrict__ part_u) {
+                   const LsqrScalars *__restrict__ cur, double *__restrict__ part_u, bool vec) {
     __shared__ double sh[kLT / 32];
     const double scale = cta_bcast(threadIdx.x == 0 ? safe_div(cur->alpha, cur->beta) : 0.0, sh);
     const V vscale = (V)scale;
@@ -170,7 +178,30 @@ __global__ void __launch_bounds__(kLT)
         for (int64_t r = gtid; r < m; r += stride) {
             const int64_t p0 = ptr[r], p1 = ptr[r + 1];
             V s = V(0);
-            for (int64_t p = p0; p < p1; p += 8) {
+            int64_t p = p0;
+            if constexpr (sizeof(V) == 4) {
+                if (vec) {
+                    const int64_t pa = min(p1, (p0 + 3) & ~(int64_t)3);
+                    for (; p < pa; ++p) {
+                        const int32_t c = idx[p];
+                        s += TS_IN(c, n) ? val[p] * dv[c] : V(0);
+                    }
+                    for (; p + 8 <= p1; p += 8) {
+                        const int4 c0 = __ldcs(reinterpret_cast<const int4 *>(idx + p));
+                        const int4 c1 = __ldcs(reinterpret_cast<const int4 *>(idx + p + 4));
+                        const float4 a0 = __ldcs(reinterpret_cast<const float4 *>(val + p));
+                        const float4 a1 = __ldcs(reinterpret_cast<const float4 *>(val + p + 4));
+                        const int c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                        float g[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) g[q] = TS_IN(c[q], n) ? (float)dv[c[q]] : 0.f;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) s += a[q] * g[q];
+                    }
+                }
+            }
+            for (; p < p1; p += 8) {
                 int32_t c[8];
                 V a[8];
 #pragma unroll
@@ -367,7 +398,7 @@ __global__ void keep_x_on_F_kernel(int64_t n, const uint8_t *__restrict__ inF,
 namespace {
 
 inline int grid_for(int64_t rows, int tpr) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(rows * tpr, kLT), kMaxPartials));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(rows * tpr, kLT), partial_cap()));
 }
 
 template <typename V>
@@ -386,7 +417,9 @@ struct LsqrLaunch {
 
     template <int TPR>
     void av(const LsqrScalars *cur) {
-        lsqr_av_kernel<V, TPR><<<grid_for(m, TPR), kLT, 0, s>>>(m, n, row_ptr, col, val, dv, u, cur, part_u);
+        const bool vec = sizeof(V) == 4 && (reinterpret_cast<uintptr_t>(col) & 15) == 0 &&
+                         (reinterpret_cast<uintptr_t>(val) & 15) == 0;
+        lsqr_av_kernel<V, TPR><<<grid_for(m, TPR), kLT, 0, s>>>(m, n, row_ptr, col, val, dv, u, cur, part_u, vec);
         note_launches(1);
     }
     template <int TPR>
@@ -413,14 +446,14 @@ struct LsqrLaunch {
         }
     }
     void vstart(const double *s_atr, LsqrScalars *nxt) {
-        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kLT), kMaxPartials));
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kLT), partial_cap()));
         lsqr_vstart_kernel<V><<<g, kLT, 0, s>>>(n, s_atr, D, inF, v, part_u, grid_for(m, tpr_r), nxt, part_v);
         note_launches(1);
         vstart_grid = g;
     }
     int vstart_grid = 0;
     void upd(const LsqrScalars *cur, LsqrScalars *nxt, int init) {
-        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kLT), kMaxPartials));
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kLT), partial_cap()));
         const int nparts = init ? vstart_grid : grid_for(n, tpr_c);
         lsqr_update_kernel<V><<<g, kLT, 0, s>>>(n, v, w, z, D, dv, part_v, nparts, cur, nxt, init);
         note_launches(1);
