@@ -79,10 +79,11 @@ def load_peaks():
     try:
         with open(PEAKS) as f:
             p = json.load(f)
+        p["kind"] = "measured"
         return p, "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
-                "sm_max_mhz": 2070.0}, "fallback"
+                "sm_max_mhz": 2070.0, "kind": "fallback"}, "fallback"
 
 
 class ClockSampler:
@@ -186,7 +187,7 @@ def kernel_rooflines(stats, peaks, sm_mhz, traffic, sms):
         if name == "factor_update":
             peak = tf32 / TC_SPLITS
             r.update(bound="tensor", unit="TFLOP/s", achieved=st["flops"] / sec / 1e12, peak=peak,
-                     peak_source=("bf16_tflops_sustained of measured x 1.1/2.25 (nominal TF32:BF16) "
+                     peak_source=(f"bf16_tflops_sustained ({peaks['kind']}) x 1.1/2.25 (nominal TF32:BF16) "
                                   "/ 3 (three TF32 products per FP32 product)"))
         elif name == "factor_diag":
             ach = st["flops"] / sec / 1e12
@@ -199,9 +200,12 @@ def kernel_rooflines(stats, peaks, sm_mhz, traffic, sms):
                      peak_source=chip_src)
         else:
             r.update(bound="hbm", unit="GB/s", achieved=st["bytes"] / sec / 1e9,
-                     peak=peaks["hbm_gbs"], peak_source="hbm_gbs of measured")
+                     peak=peaks["hbm_gbs"], peak_source=f"hbm_gbs ({peaks['kind']})")
         r["frac"] = r["achieved"] / r["peak"]
-        r["traffic"] = traffic.get(name)
+        t = traffic.get(name)
+        if isinstance(t, tuple):  # bytes per tile x the tiles of an average launch
+            t = int(t[1] * st["flops"] / st["launches"] / TC_TILE_FLOPS)
+        r["traffic"] = t
         out[name] = r
     return out
 
@@ -219,14 +223,17 @@ KERNEL_NAMES = {"factor_diag": "chol_diag_kernel", "factor_panel": "chol_panel_k
                 "gather": "gather_kernel", "spmv": "spmv_kernel", "gram": "gram_kernel"}
 
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
-# this workload (profiles/factor_kernels_*.md, profiles/solve_kernels_*.md):
-# the diagonal kernel's launches all have the same size; the others are the
-# captured launch of the first factorisation (k = 5987), so they are
-# representative, not averages.  Set an entry to None when its kernel changes.
+# this workload (profiles/chol_diag_kernel_*.md, tc_update_kernel_*.md,
+# solve_kernels_*.md): the diagonal kernel's launches all have the same size;
+# the update's bytes are per 128 x 128 tile (C read and written, the panel's
+# hi / lo rows), scaled to a launch by the tiles it updates; the others are the
+# captured launch of the first factorisation (k = 5987), representative, not
+# averages.  Set an entry to None when its kernel changes.
+TC_TILE_FLOPS = 2.0 * 128 ** 3
 NCU_TRAFFIC = {
     "factor_diag": 106_496,
     "factor_panel": None,  # only the 4-CTA head launch was captured for the current kernel
-    "factor_update": 66_581_504 + 6_302_208,
+    "factor_update": ("per_tile", (47_482_624 + 787_968) / 665),
     "trsv": (72_816_640 + 697_344 + 72_828_160 + 670_720) // 2,
     "gather": 96_223_744 + 33_048_064,
     "gram": 10_600_704 + 70_255_104,
@@ -513,7 +520,7 @@ def run_lsqr(args, ts, torch, ctx, dev, ws, rank, barrier, max_over_ranks, peaks
                   "rel_diff_mixed_vs_fp64": float(np.linalg.norm(xs - x64) / np.linalg.norm(x64))},
         roofline={"kernel": "lsqr_av + lsqr_atu + lsqr_update (inner iterations)", "bound": "hbm",
                   "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-                  "traffic": None, "peak_source": "hbm_gbs of measured"},
+                  "traffic": None, "peak_source": f"hbm_gbs ({peaks['kind']})"},
         pivots=int(info.iters), lsqr_phase_ms_per_step=lq["ms"] / args.steps,
         gpu_launches=int(info.kernel_launches), clocks=clk.summary())
 
