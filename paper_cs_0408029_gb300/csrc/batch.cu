@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <vector>
 
@@ -1171,6 +1172,39 @@ size_t batch_smem_bytes(bool mixed, int max_nb) {
     return t * 64 * 65 + t * (size_t)kMaxPanelRows * pitch;
 }
 
+// The last call's graph and arena on a lane.  The graph's kernels read
+// every per-problem pointer from the descriptor array in the arena, so a
+// call with the same shape (count, precision, parameters, sizes and panel
+// widths in queue order, trace capacity) only rewrites the descriptors and
+// replays the graph; any other shape rebuilds both.
+struct BatchGraphCache {
+    std::vector<int64_t> key;
+    char *arena = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    void release(cudaStream_t s) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (arena) {
+            cudaFreeAsync(arena, s);
+            cudaStreamSynchronize(s);
+        }
+        key.clear();
+        arena = nullptr;
+        graph = nullptr;
+        exec = nullptr;
+    }
+};
+
+void batch_cache_release(Lane &l) {
+    auto *c = static_cast<BatchGraphCache *>(l.batch_cache);
+    if (!c) return;
+    c->release(l.stream);
+    delete c;
+    l.batch_cache = nullptr;
+}
+
 int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const int32_t *n,
                     const float *const *a, const double *const *b, double *const *x,
                     const tsnnls_opts &o, int32_t *status_out, tsnnls_info *info,
@@ -1224,10 +1258,46 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
             for (int J = 0; J <= I; ++J) items.push_back({q, I, J});
     }
     const size_t item_bytes = up(sizeof(GramItem) * items.size());
-    char *arena = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&arena),
-                                    total + desc_bytes + out_bytes + item_bytes + 256, s);
-    if (e != cudaSuccess) return status_from_cuda(e);
+    BatchParams prm{o.zero_tol, o.rel_tol, o.p_max,
+                    o.max_iter > 0 ? o.max_iter : 0, o.max_refine, mixed ? 1 : 0,
+                    (int32_t)(batch_smem_bytes(mixed, max_nb) - (mixed ? sizeof(float) : sizeof(double)) * 64 * 65),
+                    mixed && o.full_refine == 0 ? 1 : 0};
+    if (prm.max_iter == 0) {
+        int nmax = 0;
+        for (int q = 0; q < count; ++q) nmax = std::max(nmax, hp[q].n);
+        prm.max_iter = 10 * nmax + 100;
+    }
+    // the shape the graph is built for (parameters are kernel arguments)
+    std::vector<int64_t> key = {mixed ? 1 : 0, count, trace ? trace_cap : 0, prm.p_max, prm.max_iter,
+                                prm.max_refine, prm.scratch_bytes, prm.settle};
+    int64_t tb[2];
+    std::memcpy(&tb[0], &prm.zero_tol, 8);
+    std::memcpy(&tb[1], &prm.rel_tol, 8);
+    key.push_back(tb[0]);
+    key.push_back(tb[1]);
+    for (int q = 0; q < count; ++q) {
+        key.push_back(hp[q].m);
+        key.push_back(hp[q].n);
+        key.push_back(hp[q].nb);
+    }
+    auto *cache = static_cast<BatchGraphCache *>(lane.batch_cache);
+    if (!cache) {
+        cache = new (std::nothrow) BatchGraphCache;
+        if (!cache) return TSNNLS_ENOMEM;
+        lane.batch_cache = cache;
+    }
+    const bool hit = cache->exec != nullptr && cache->arena != nullptr && cache->key == key;
+    cudaError_t e = cudaSuccess;
+    if (!hit) {
+        cache->release(s);
+        e = cudaMallocAsync(reinterpret_cast<void **>(&cache->arena),
+                            total + desc_bytes + out_bytes + item_bytes + 256, s);
+        if (e != cudaSuccess) {
+            cache->arena = nullptr;
+            return status_from_cuda(e);
+        }
+    }
+    char *arena = cache->arena;
     for (int q = 0; q < count; ++q) {
         char *pbase = arena + off[q];
         BatchProb &P = hp[q];
@@ -1251,19 +1321,13 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
     GramItem *d_items = reinterpret_cast<GramItem *>(arena + total + desc_bytes + out_bytes);
     int32_t *d_queue = reinterpret_cast<int32_t *>(arena + total + desc_bytes + out_bytes + item_bytes);
     std::vector<BatchOut> hout(count);
-    BatchParams prm{o.zero_tol, o.rel_tol, o.p_max,
-                    o.max_iter > 0 ? o.max_iter : 0, o.max_refine, mixed ? 1 : 0,
-                    (int32_t)(batch_smem_bytes(mixed, max_nb) - (mixed ? sizeof(float) : sizeof(double)) * 64 * 65),
-                    mixed && o.full_refine == 0 ? 1 : 0};
     int status = TSNNLS_OK;
     const size_t smem = batch_smem_bytes(mixed, max_nb);
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     const int64_t launch0 = launches_so_far();
     do {
         e = cudaMemcpyAsync(d_probs, hp.data(), sizeof(BatchProb) * count, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) break;
-        if (!items.empty())
+        if (!hit && !items.empty())
             e = cudaMemcpyAsync(d_items, items.data(), sizeof(GramItem) * items.size(),
                                 cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) break;
@@ -1271,42 +1335,39 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
             for (int q = 0; q < count && e == cudaSuccess; ++q)
                 e = cudaMemsetAsync(hp[q].trace, 0xFF, sizeof(int64_t) * 6 * (size_t)trace_cap, s);
         if (e != cudaSuccess) break;
-        if (prm.max_iter == 0) {
-            int nmax = 0;
-            for (int q = 0; q < count; ++q) nmax = std::max(nmax, hp[q].n);
-            prm.max_iter = 10 * nmax + 100;
-        }
         if (mixed)
             e = cudaFuncSetAttribute(batch_bpp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         else
             e = cudaFuncSetAttribute(batch_bpp_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) break;
-        // capture precompute + persistent kernel into one graph and replay it
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) break;
-        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) break;
-        cudaMemsetAsync(d_queue, 0, sizeof(int32_t), s);
-        const int gitems = (int)items.size();
-        const int ggrid = std::max(1, std::min(gitems, num_sms() * 8));
-        if (mixed) batch_gram_tc_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
-        else batch_gram64_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
-        note_launches(1);
-        batch_atb_kernel<<<std::min(count, num_sms() * 8), 256, 0, s>>>(d_probs, count);
-        note_launches(1);
-        const int pgrid = std::min(count, num_sms());
-        if (mixed)
-            batch_bpp_kernel<float><<<pgrid, kBT, smem, s>>>(d_probs, count, d_queue, prm, d_out);
-        else
-            batch_bpp_kernel<double><<<pgrid, kBT, smem, s>>>(d_probs, count, d_queue, prm, d_out);
-        note_launches(1);
-        e = cudaStreamEndCapture(s, &graph);
-        if (e != cudaSuccess) break;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        if (e != cudaSuccess) break;
+        // precompute + persistent kernel captured into one graph on the first
+        // call of this shape, replayed as it stands by the next ones
+        if (!hit) {
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) break;
+            e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) break;
+            cudaMemsetAsync(d_queue, 0, sizeof(int32_t), s);
+            const int gitems = (int)items.size();
+            const int ggrid = std::max(1, std::min(gitems, num_sms() * 8));
+            if (mixed) batch_gram_tc_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
+            else batch_gram64_kernel<<<ggrid, 256, 0, s>>>(d_probs, d_items, gitems);
+            batch_atb_kernel<<<std::min(count, num_sms() * 8), 256, 0, s>>>(d_probs, count);
+            const int pgrid = std::min(count, num_sms());
+            if (mixed)
+                batch_bpp_kernel<float><<<pgrid, kBT, smem, s>>>(d_probs, count, d_queue, prm, d_out);
+            else
+                batch_bpp_kernel<double><<<pgrid, kBT, smem, s>>>(d_probs, count, d_queue, prm, d_out);
+            e = cudaStreamEndCapture(s, &cache->graph);
+            if (e != cudaSuccess) break;
+            e = cudaGraphInstantiate(&cache->exec, cache->graph, 0);
+            if (e != cudaSuccess) break;
+            cache->key = key;
+        }
+        note_launches(3);  // the graph's three kernels
         e = cudaEventRecord(lane.ev0, s);
         if (e != cudaSuccess) break;
-        e = cudaGraphLaunch(exec, s);
+        e = cudaGraphLaunch(cache->exec, s);
         if (e != cudaSuccess) break;
         e = cudaEventRecord(lane.ev1, s);
         if (e != cudaSuccess) break;
@@ -1327,10 +1388,13 @@ int run_batch_dense(Context &ctx, Lane &lane, int count, const int32_t *m, const
     }
     float ms = 0.f;
     if (status == TSNNLS_OK) cudaEventElapsedTime(&ms, lane.ev0, lane.ev1);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    cudaFreeAsync(arena, s);
-    cudaStreamSynchronize(s);
+    if (status != TSNNLS_OK) {
+        // a failed capture or launch: nothing of this call is kept
+        cudaGraph_t open_capture = nullptr;  // a capture left open ends here (an error otherwise, ignored)
+        if (cudaStreamEndCapture(s, &open_capture) == cudaSuccess && open_capture) cudaGraphDestroy(open_capture);
+        cudaGetLastError();
+        cache->release(s);
+    }
     if (check_collect(nullptr, 0) > 0 && status == TSNNLS_OK) status = TSNNLS_EBOUNDS;
     int32_t iters = 0, refine = 0;
     double flops = 0.0, bytes = 0.0;

@@ -182,6 +182,7 @@ int lane_create(Lane &l) {
 void lane_destroy(Lane &l) {
     if (l.stream) cudaStreamSynchronize(l.stream);
     if (l.side) cudaStreamSynchronize(l.side);
+    batch_cache_release(l);
     if (l.fork) cudaEventDestroy(l.fork);
     if (l.head) cudaEventDestroy(l.head);
     if (l.ev_status) cudaEventDestroy(l.ev_status);

@@ -50,7 +50,13 @@ struct Lane {
     int64_t mark_launch0 = 0;
     tsnnls_phase_stat stats[TSNNLS_NUM_PHASES] = {};
     bool nvtx_open = false;  // a phase range is open on the NVTX stack
+    // the batched path's last graph and device arena, replayed by the next
+    // call of the same shape (batch.cu owns it; batch_cache_release frees it)
+    void *batch_cache = nullptr;
 };
+
+// Free a lane's cached batched graph and arena (the lane's stream idle).
+void batch_cache_release(Lane &l);
 
 // NVTX ranges for timeline tools (Nsight Systems): one per solve and one per
 // phase that prof_begin opens; inert unless a tool is attached.

@@ -63,6 +63,22 @@ def test_batch_equals_solve_alone(env):
         assert np.linalg.norm(x - alone) <= 1e-9 * np.linalg.norm(alone), p.name
 
 
+def test_replayed_graph_reads_the_new_problems(env, oracle_mod):
+    """A second call of the same shape replays the first call's graph: its
+    problems (new values, new buffers) must still be the ones solved."""
+    ts, ctx, torch = env
+    first = _batch(105, 10, 32, 400)
+    second = [workloads.DenseProblem(p.m, p.n, (-1.5 * p.a).astype(np.float32),
+                                     -1.5 * p.b + 0.25 * np.linspace(-1, 1, p.m), None, p.name + "_b")
+              for p in first]
+    for probs in (first, second, first):
+        st, stat, info, xs = _run(ts, ctx, torch, probs, "mixed")
+        assert st == ts.OK
+        for p, x in zip(probs, xs):
+            ref = oracle_mod.bpp_solve(workloads.dense_to_csr(p.a.astype(np.float64), p.b))
+            assert np.linalg.norm(x - ref.x) <= 1e-9 * max(np.linalg.norm(ref.x), 1e-300), p.name
+
+
 def test_batch_single_and_ragged_sizes(env, oracle_mod):
     ts, ctx, torch = env
     rng = np.random.default_rng(7)
