@@ -87,7 +87,11 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples during the timed region.
+
+    nvidia-smi runs on a pseudo-terminal, so each sample line reaches us as
+    it is printed (into a file or a pipe it would sit in nvidia-smi's output
+    buffer and be lost when the sampler is stopped)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -96,41 +100,67 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = None
+        self.lines = []
+        self._fd = None
+        self._thread = None
+
+    def _read(self, fd):
+        buf = b""
+        while True:
+            try:
+                chunk = os.read(fd, 4096)
+            except OSError:
+                break
+            if not chunk:
+                break
+            buf += chunk
+            *done, buf = buf.split(b"\n")
+            self.lines.extend(d.decode(errors="replace").strip() for d in done)
 
     def __enter__(self):
-        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
-        os.close(fd)
+        import pty
+        import threading
+
         try:
+            master, slave = pty.openpty()
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                stdout=slave, stderr=subprocess.DEVNULL, stdin=subprocess.DEVNULL, close_fds=True)
+            os.close(slave)
+            self._fd = master
+            self._thread = threading.Thread(target=self._read, args=(master,), daemon=True)
+            self._thread.start()
         except OSError:
             self.proc = None
         # nvidia-smi takes a moment to start: wait (at most 5 s) for its first
         # sample so that a short timed region is sampled too
         t0 = time.time()
-        while self.proc and self.proc.poll() is None and time.time() - t0 < 5.0:
-            if os.path.getsize(self.path) > 0:
-                break
+        while self.proc and self.proc.poll() is None and time.time() - t0 < 5.0 and not self.lines:
             time.sleep(0.02)
         return self
 
     def __exit__(self, *exc):
         if self.proc:
+            time.sleep(0.15)  # one more sample period
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self._thread:
+            self._thread.join(timeout=2)
+        if self._fd is not None:
+            try:
+                os.close(self._fd)
+            except OSError:
+                pass
+            self._fd = None
 
     def summary(self):
-        if not self.path or not os.path.exists(self.path):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in open(self.path):
+        for line in list(self.lines):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -142,7 +172,6 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        os.unlink(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),

@@ -108,6 +108,92 @@ __global__ void sp_permF_kernel(int64_t n, const int32_t *__restrict__ perm, con
     }
 }
 
+// Extend-add of a child's update matrix Uc (hc x hc lower, leading dimension
+// lduc) into this supernode's panel P (rows h, leading dimension ld, w
+// columns) and update matrix U (leading dimension ldu): child row i lands on
+// row rel[i] (increasing in i).  A warp takes a column j of Uc, its lanes the
+// rows i >= j, four at a time with every load issued before the stores (the
+// targets of distinct (i, j) are distinct, so the reordering is safe).
+template <typename T>
+__device__ __noinline__ void sp_extend_add(const T *__restrict__ Uc, int64_t lduc, int64_t hc,
+                                           const int32_t *__restrict__ rel, T *P, int64_t ld, T *U,
+                                           int64_t ldu, int w, int64_t h) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t j = warp; j < hc; j += 8) {
+        const int32_t lj = rel[j];
+        if (!TS_IN(lj, h)) continue;
+        // target column, indexed by li - roff
+        T *dst = lj < w ? P + (int64_t)lj * ld : U + (int64_t)(lj - w) * ldu;
+        const int roff = lj < w ? 0 : w;
+        const T *src = Uc + j * lduc;
+        for (int64_t i0 = j + lane; i0 < hc; i0 += 128) {
+            int32_t li[4];
+            T v[4], old[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + 32 * u;
+                li[u] = -1;
+                if (i < hc) {
+                    const int32_t r = rel[i];  // r >= lj: rows keep their order
+                    if (TS_IN(r, h) && TS_IN(r - lj, h - lj)) {
+                        li[u] = r;
+                        v[u] = __ldcg(src + i);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (li[u] >= 0) old[u] = dst[li[u] - roff];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (li[u] >= 0) dst[li[u] - roff] = old[u] + v[u];
+        }
+    }
+}
+
+// U -= X X^T on the lower triangle (X: hu rows x w columns, leading dimension
+// ld; U leading dimension ldu), one 4 x 4 tile per thread and turn; the
+// tile's 16 entries of U are loaded before the products so that their
+// latency passes under them.
+template <typename T>
+__device__ __noinline__ void sp_syrk(const T *X, int64_t ld, int64_t hu, int w, T *U, int64_t ldu) {
+    const int64_t nt = (hu + 3) / 4;
+    for (int64_t tile = threadIdx.x; tile < nt * nt; tile += 256) {
+        const int64_t tr = tile % nt, tc = tile / nt;
+        if (tr < tc) continue;
+        const int64_t i0 = 4 * tr, j0 = 4 * tc;
+        T cv[4][4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int64_t i = i0 + a, j = j0 + b;
+                cv[a][b] = (i < hu && j < hu && i >= j) ? U[j * ldu + i] : T(0);
+            }
+        T acc[4][4] = {};
+        for (int k = 0; k < w; ++k) {
+            const T *xk = X + (int64_t)k * ld;
+            T xi[4], xj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xi[u] = i0 + u < hu ? xk[i0 + u] : T(0);
+                xj[u] = j0 + u < hu ? xk[j0 + u] : T(0);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += xi[a] * xj[b];
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int64_t i = i0 + a, j = j0 + b;
+                if (i < hu && j < hu && i >= j) U[j * ldu + i] = cv[a][b] - acc[a][b];
+            }
+    }
+}
+
 template <typename T, int NB>
 struct SpSmem {
     static constexpr int P = NB + 4;
@@ -158,15 +244,7 @@ __global__ void __launch_bounds__(256, 1)
             const int64_t hc = D.rows_off[c + 1] - D.rows_off[c] - wc, lduc = (hc + 3) / 4 * 4;
             const T *Uc = Ua + D.U_off[c];
             const int32_t *rel = D.rel + D.u_off[c];
-            for (int64_t e = tid; e < hc * hc; e += 256) {
-                const int64_t i = e % hc, j = e / hc;
-                if (i < j) continue;
-                const int32_t li = rel[i], lj = rel[j];  // li >= lj: rows keep their order
-                if (!TS_IN(li, h) || !TS_IN(lj, li + 1)) continue;
-                const T v = Uc[j * lduc + i];
-                if (lj < w) P[(int64_t)lj * ld + li] += v;
-                else U[(int64_t)(lj - w) * ldu + (li - w)] += v;
-            }
+            sp_extend_add<T>(Uc, lduc, hc, rel, P, ld, U, ldu, w, h);
             __syncthreads();
         }
         // the diagonal block: factor and inverse in shared memory
@@ -221,37 +299,7 @@ __global__ void __launch_bounds__(256, 1)
         }
         __syncthreads();
         // update matrix: U -= X X^T on its lower triangle, X = rows below (hu x w)
-        const int64_t nt = (hu + 3) / 4;
-        const T *X = P + w;
-        for (int64_t tile = tid; tile < nt * nt; tile += 256) {
-            const int64_t tr = tile % nt, tc = tile / nt;
-            if (tr < tc) continue;
-            const int64_t i0 = 4 * tr, j0 = 4 * tc;
-            T acc[4][4] = {};
-            for (int k = 0; k < w; ++k) {
-                const T *xk = X + (int64_t)k * ld;
-                T xi[4], xj[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    xi[u] = i0 + u < hu ? xk[i0 + u] : T(0);
-                    xj[u] = j0 + u < hu ? xk[j0 + u] : T(0);
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] += xi[a] * xj[b];
-            }
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int64_t j = j0 + b;
-                if (j >= hu) break;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int64_t i = i0 + a;
-                    if (i < hu && i >= j) U[j * ldu + i] -= acc[a][b];
-                }
-            }
-        }
+        sp_syrk<T>(P + w, ld, hu, w, U, ldu);
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -306,6 +354,7 @@ __global__ void __launch_bounds__(kSpT)
         const T *Ls = L + D.L_off[s];
         for (int64_t i = tid; i < hu; i += kSpT) {
             T acc = -a[w + i];
+#pragma unroll 8
             for (int k = 0; k < w; ++k) acc += Ls[(int64_t)k * ld + w + i] * y_sh[k];
             ua[D.u_off[s] + i] = acc;
         }
@@ -320,10 +369,11 @@ __global__ void __launch_bounds__(kSpT)
 template <typename T>
 __global__ void __launch_bounds__(kSpT)
     sp_bwd_kernel(SpDev D, const T *__restrict__ L, const T *__restrict__ Wa, T *v, DevStatus *st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xb = reinterpret_cast<T *>(smem_raw);  // max_height entries: x at the rows below
     __shared__ T t_sh[128];
-    __shared__ T part[kSpT];
     __shared__ int sh_s, ok_sh;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (;;) {
         if (tid == 0) sh_s = atomicAdd(D.ticket, 1);
         __syncthreads();
@@ -332,30 +382,32 @@ __global__ void __launch_bounds__(kSpT)
         if (!sp_wait_all(D, D.flags, D.alist, D.a_off[s], D.a_off[s + 1], st, &ok_sh)) return;
         const int32_t f = D.sn_first[s], w = D.sn_first[s + 1] - f;
         const int32_t *rows = D.rows + D.rows_off[s];
-        const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4;
+        const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4, hu = h - w;
         const T *Ls = L + D.L_off[s];
-        // t_c = y_c - sum_{p >= w} L(p, c) x(rows[p]): G groups of threads per
-        // column share the rows below, partial sums added in group order
-        const int G = max(1, kSpT / w);
-        const int c = tid % w, g = tid / w;
-        T acc = T(0);
-        if (g < G)
-            for (int64_t p = w + g; p < h; p += G) {
-                const int32_t r = rows[p];
-                if (TS_IN(r, D.n)) acc += Ls[(int64_t)c * ld + p] * __ldcg(v + r);
-            }
-        part[tid] = acc;
+        // x at the rows below, gathered once (independent loads)
+        for (int64_t p = tid; p < hu; p += kSpT) {
+            const int32_t r = rows[w + p];
+            xb[p] = TS_IN(r, D.n) ? __ldcg(v + r) : T(0);
+        }
         __syncthreads();
-        if (tid < w) {
-            T t = __ldcg(v + f + tid);
-            for (int q = 0; q < G; ++q) t -= part[q * w + tid];
-            t_sh[tid] = t;
+        // t_c = y_c - sum_{p >= w} L(p, c) x(rows[p]): a warp per column, its
+        // lanes down the column (coalesced), summed in a fixed order
+        for (int c = warp; c < w; c += kSpT / 32) {
+            const T *lc = Ls + (int64_t)c * ld + w;
+            T acc = T(0);
+#pragma unroll 4
+            for (int64_t p = lane; p < hu; p += 32) acc += lc[p] * xb[p];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) t_sh[c] = __ldcg(v + f + c) - acc;
         }
         __syncthreads();
         const T *Ws = Wa + D.W_off[s];
         T x = T(0);
-        if (tid < w)
+        if (tid < w) {
+#pragma unroll 8
             for (int cc = tid; cc < w; ++cc) x += Ws[(int64_t)tid * w + cc] * t_sh[cc];  // W(cc, r), cc >= r
+        }
         if (tid < w) v[f + tid] = x;
         __syncthreads();
         if (tid == 0) {
@@ -519,12 +571,14 @@ cudaError_t SparseChol<T>::solve(cudaStream_t s, T *v, DevStatus *st) {
     const int g = std::max(1, num_sms() * 4);
     const size_t smem = sizeof(T) * (size_t)std::max<int64_t>(max_height, 1);
     cudaError_t e = cudaFuncSetAttribute(sp_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sp_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = reset(s);
     if (e != cudaSuccess) return e;
     sp_fwd_kernel<T><<<g, kSpT, smem, s>>>(D, Lmem, Wmem, umem, v, st);
     e = reset(s);
     if (e != cudaSuccess) return e;
-    sp_bwd_kernel<T><<<g, kSpT, 0, s>>>(D, Lmem, Wmem, v, st);
+    sp_bwd_kernel<T><<<g, kSpT, smem, s>>>(D, Lmem, Wmem, v, st);
     note_launches(2);
     return cudaGetLastError();
 }
