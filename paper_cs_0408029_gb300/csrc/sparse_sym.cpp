@@ -138,17 +138,20 @@ class Dissection {
             return;
         }
         // pseudo-peripheral root: repeat from the farthest vertex while the depth grows
-        int32_t root = comp.back(), depth = last;
+        int32_t root = comp.back(), depth = last, maxl = -1;
         for (int it = 0; it < 4; ++it) {
             int32_t d2 = 0;
             std::vector<int32_t> q = bfs(root, id, &d2);
-            if (d2 <= depth && it > 0) break;
+            if (d2 <= depth && it > 0) {  // q is the level structure from root itself: keep it
+                comp.swap(q);
+                maxl = d2;
+                break;
+            }
             depth = d2;
             comp.swap(q);
             root = comp.back();
         }
-        int32_t maxl = 0;
-        comp = bfs(root, id, &maxl);
+        if (maxl < 0) comp = bfs(root, id, &maxl);
         if (maxl < 2) {  // (nearly) complete subgraph: nothing to dissect
             order_.insert(order_.end(), verts.begin(), verts.end());
             for (int32_t v : verts) sub_[v] = -1;
@@ -288,24 +291,33 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
                 first_child[parent[j]] = (int32_t)j;
                 nchild[parent[j]] += 1;
             }
-        std::vector<int32_t> mark(n, -1);
+        // the column's own rows (sorted), then each child's rows after j
+        // merged in (both sorted, duplicates dropped): linear in the sizes,
+        // no sort of the merged structure
+        std::vector<int32_t> tmp;
         for (int64_t j = 0; j < n; ++j) {
             std::vector<int32_t> &v = cs[j];
-            mark[j] = (int32_t)j;
-            for (int64_t p = S.gptr[j] + 1; p < S.gptr[j + 1]; ++p) {
-                const int32_t i = S.grow[p];
-                if (mark[i] != (int32_t)j) {
-                    mark[i] = (int32_t)j;
-                    v.push_back(i);
-                }
-            }
-            for (int32_t c = first_child[j]; c >= 0; c = sib[c])
-                for (int32_t i : cs[c])
-                    if (i > j && mark[i] != (int32_t)j) {
-                        mark[i] = (int32_t)j;
-                        v.push_back(i);
-                    }
+            for (int64_t p = S.gptr[j] + 1; p < S.gptr[j + 1]; ++p) v.push_back(S.grow[p]);
             std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+            for (int32_t c = first_child[j]; c >= 0; c = sib[c]) {
+                const std::vector<int32_t> &w = cs[c];
+                auto b = std::upper_bound(w.begin(), w.end(), (int32_t)j);  // rows below j only
+                tmp.clear();
+                tmp.reserve(v.size() + (size_t)(w.end() - b));
+                auto a = v.begin();
+                while (a != v.end() && b != w.end()) {
+                    if (*a < *b) tmp.push_back(*a++);
+                    else if (*b < *a) tmp.push_back(*b++);
+                    else {
+                        tmp.push_back(*a++);
+                        ++b;
+                    }
+                }
+                tmp.insert(tmp.end(), a, v.end());
+                tmp.insert(tmp.end(), b, w.end());
+                v.swap(tmp);
+            }
         }
     }
 
