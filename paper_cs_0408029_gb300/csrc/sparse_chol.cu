@@ -112,7 +112,7 @@ __global__ void sp_permF_kernel(int64_t n, const int32_t *__restrict__ perm, con
 // lduc) into this supernode's panel P (rows h, leading dimension ld, w
 // columns) and update matrix U (leading dimension ldu): child row i lands on
 // row rel[i] (increasing in i).  A warp takes a column j of Uc, its lanes the
-// rows i >= j, four at a time with every load issued before the stores (the
+// rows i >= j, eight at a time with every load issued before the stores (the
 // targets of distinct (i, j) are distinct, so the reordering is safe).
 template <typename T>
 __device__ __noinline__ void sp_extend_add(const T *__restrict__ Uc, int64_t lduc, int64_t hc,
@@ -126,11 +126,11 @@ __device__ __noinline__ void sp_extend_add(const T *__restrict__ Uc, int64_t ldu
         T *dst = lj < w ? P + (int64_t)lj * ld : U + (int64_t)(lj - w) * ldu;
         const int roff = lj < w ? 0 : w;
         const T *src = Uc + j * lduc;
-        for (int64_t i0 = j + lane; i0 < hc; i0 += 128) {
-            int32_t li[4];
-            T v[4], old[4];
+        for (int64_t i0 = j + lane; i0 < hc; i0 += 256) {
+            int32_t li[8];
+            T v[8], old[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const int64_t i = i0 + 32 * u;
                 li[u] = -1;
                 if (i < hc) {
@@ -142,11 +142,118 @@ __device__ __noinline__ void sp_extend_add(const T *__restrict__ Uc, int64_t ldu
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
                 if (li[u] >= 0) old[u] = dst[li[u] - roff];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
                 if (li[u] >= 0) dst[li[u] - roff] = old[u] + v[u];
+        }
+    }
+}
+
+// FP32: U -= X X^T on the lower triangle (X: hu rows x w <= 64 columns,
+// leading dimension ld; U leading dimension ldu) by 128 x 128 blocks of U
+// (only those on or below the diagonal): the block's row and column panels
+// of X are staged in shared memory (sm: two 64 x 132 panels, k-major) and
+// each thread accumulates an 8 x 8 register tile over all w columns, then
+// loads its 64 entries of U before storing any.  A block of a 723-row
+// update then costs 128 x 128 x w FMAs from shared memory instead of
+// 8 global loads per 16 FMAs.
+__device__ __noinline__ void sp_syrk_tiled(const float *X, int64_t ld, int64_t hu, int w, float *U, int64_t ldu,
+                                           float *sm) {
+    constexpr int BM = 128, P = BM + 4;
+    float(*Xa)[P] = reinterpret_cast<float(*)[P]>(sm);            // Xa[k][i] = X(I0 + i, k)
+    float(*Xb)[P] = reinterpret_cast<float(*)[P]>(sm + 64 * P);   // Xb[k][j] = X(J0 + j, k)
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t nb = (hu + BM - 1) / BM;
+    for (int64_t I = 0; I < nb; ++I) {
+        for (int64_t J = 0; J <= I; ++J) {
+            const int64_t I0 = I * BM, J0 = J * BM;
+            __syncthreads();
+            // eight elements of each panel per thread in flight
+            for (int e0 = tid; e0 < w * BM; e0 += 256 * 8) {
+                float va[8], vb[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + 256 * u, k = e / BM, i = e % BM;
+                    va[u] = (e < w * BM && I0 + i < hu) ? X[(int64_t)k * ld + I0 + i] : 0.f;
+                    vb[u] = (e < w * BM && J0 + i < hu) ? X[(int64_t)k * ld + J0 + i] : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + 256 * u, k = e / BM, i = e % BM;
+                    if (e < w * BM) {
+                        Xa[k][i] = va[u];
+                        Xb[k][i] = vb[u];
+                    }
+                }
+            }
+            __syncthreads();
+            // thread (tx, ty): rows I0 + 4 tx .. + 3 and I0 + 64 + 4 tx .. + 3 (16
+            // lanes run down a column of U: 16-byte accesses), columns likewise
+            // from ty
+            float acc[8][8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+            for (int k = 0; k < w; ++k) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&Xa[k][tx * 4]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&Xa[k][64 + tx * 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Xb[k][ty * 4]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Xb[k][64 + ty * 4]);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) acc[a][b] += av[a] * bv[b];
+            }
+            // U's entries: a whole 4-row group with one 16-byte load when it
+            // lies inside the lower triangle (ldu, the offsets and the row
+            // start are multiples of 4), entry by entry otherwise; every load
+            // before the first store
+            float cv[8][8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int64_t j = J0 + (b < 4 ? ty * 4 + b : 64 + ty * 4 + b - 4);
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int64_t i4 = I0 + 64 * hh + tx * 4;
+                    if (j < hu && i4 + 3 < hu && i4 >= j) {
+                        const float4 u4 = *reinterpret_cast<const float4 *>(&U[j * ldu + i4]);
+                        cv[4 * hh][b] = u4.x;
+                        cv[4 * hh + 1][b] = u4.y;
+                        cv[4 * hh + 2][b] = u4.z;
+                        cv[4 * hh + 3][b] = u4.w;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int64_t i = i4 + q;
+                            cv[4 * hh + q][b] = (i < hu && j < hu && i >= j) ? U[j * ldu + i] : 0.f;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int64_t j = J0 + (b < 4 ? ty * 4 + b : 64 + ty * 4 + b - 4);
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int64_t i4 = I0 + 64 * hh + tx * 4;
+                    if (j < hu && i4 + 3 < hu && i4 >= j) {
+                        *reinterpret_cast<float4 *>(&U[j * ldu + i4]) =
+                            make_float4(cv[4 * hh][b] - acc[4 * hh][b], cv[4 * hh + 1][b] - acc[4 * hh + 1][b],
+                                        cv[4 * hh + 2][b] - acc[4 * hh + 2][b], cv[4 * hh + 3][b] - acc[4 * hh + 3][b]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int64_t i = i4 + q;
+                            if (i < hu && j < hu && i >= j) U[j * ldu + i] = cv[4 * hh + q][b] - acc[4 * hh + q][b];
+                        }
+                    }
+                }
+            }
         }
     }
 }
@@ -197,7 +304,10 @@ __device__ __noinline__ void sp_syrk(const T *X, int64_t ld, int64_t hu, int w, 
 template <typename T, int NB>
 struct SpSmem {
     static constexpr int P = NB + 4;
-    static constexpr size_t bytes = sizeof(T) * (2 * (size_t)NB * P + (size_t)NB * 36);
+    static constexpr size_t core = sizeof(T) * (2 * (size_t)NB * P + (size_t)NB * 36);
+    // the FP32 update matrix's two staged operand panels (sp_syrk_tiled)
+    static constexpr size_t tiled = sizeof(T) == 4 ? sizeof(float) * 2 * 64 * 132 : 0;
+    static constexpr size_t bytes = core > tiled ? core : tiled;
 };
 
 template <typename T, int NB>
@@ -285,9 +395,18 @@ __global__ void __launch_bounds__(256, 1)
         // (Bs lies after both views of A and W)
         for (int64_t r0 = w; r0 < h; r0 += 32) {
             __syncthreads();
-            for (int e = tid; e < w * 32; e += 256) {
-                const int t = e / 32, rr = e % 32;
-                Bs[t][rr] = r0 + rr < h ? P[(int64_t)t * ld + r0 + rr] : T(0);
+            {  // all of this thread's loads (at most eight) before the stores
+                T bv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = tid + 256 * u, t = e / 32, rr = e % 32;
+                    bv[u] = (e < w * 32 && r0 + rr < h) ? P[(int64_t)t * ld + r0 + rr] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = tid + 256 * u;
+                    if (e < w * 32) Bs[e / 32][e % 32] = bv[u];
+                }
             }
             __syncthreads();
             for (int e = tid; e < w * 32; e += 256) {
@@ -299,7 +418,10 @@ __global__ void __launch_bounds__(256, 1)
         }
         __syncthreads();
         // update matrix: U -= X X^T on its lower triangle, X = rows below (hu x w)
-        sp_syrk<T>(P + w, ld, hu, w, U, ldu);
+        if constexpr (sizeof(T) == 4)
+            sp_syrk_tiled(P + w, ld, hu, w, U, ldu, reinterpret_cast<float *>(smem_raw));
+        else
+            sp_syrk<T>(P + w, ld, hu, w, U, ldu);
         __syncthreads();
         if (tid == 0) {
             __threadfence();

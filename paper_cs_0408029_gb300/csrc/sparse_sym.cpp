@@ -21,12 +21,18 @@
 //      supernodes that hold its rows below, the offsets of its panel of L,
 //      of its update matrix and of its diagonal block's inverse, and where
 //      every entry of the lower triangle of P G P^T lands in the panels.
-// Plain C++; deterministic (no hashing, no threads).
+// Plain C++; deterministic: no hashing, and the dissection's top splits hand
+// one half to a thread of its own (the halves touch disjoint vertices, and
+// their orders are joined in a fixed order), so the result does not depend
+// on the threads' timing.
 #include "sparse_sym.h"
 
 #include <algorithm>
 #include <cstring>
 #include <functional>
+#include <atomic>
+#include <system_error>
+#include <thread>
 
 namespace tsnnls {
 
@@ -53,24 +59,47 @@ void gram_graph(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col
     g.n = n;
     g.ptr.assign(n + 1, 0);
     g.adj.clear();
-    std::vector<int32_t> mark(n, -1);
-    std::vector<int32_t> nb;
-    for (int64_t j = 0; j < n; ++j) {
-        nb.clear();
-        mark[j] = (int32_t)j;
-        for (int64_t p = cptr[j]; p < cptr[j + 1]; ++p) {
-            const int32_t r = crow[p];
-            for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-                const int32_t c = col[e];
-                if (mark[c] != (int32_t)j) {
-                    mark[c] = (int32_t)j;
-                    nb.push_back(c);
+    // columns in contiguous ranges, one per thread (each with its own marks
+    // and output), joined in column order
+    unsigned nt = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
+    if (n < 4096) nt = 1;
+    std::vector<std::vector<int32_t>> adj(nt);
+    std::vector<std::vector<int64_t>> cnt(nt);
+    auto work = [&](unsigned t) {
+        const int64_t j0 = n * t / nt, j1 = n * (t + 1) / nt;
+        std::vector<int32_t> mark(n, -1);
+        std::vector<int32_t> nb;
+        cnt[t].assign(j1 - j0, 0);
+        for (int64_t j = j0; j < j1; ++j) {
+            nb.clear();
+            mark[j] = (int32_t)j;
+            for (int64_t p = cptr[j]; p < cptr[j + 1]; ++p) {
+                const int32_t r = crow[p];
+                for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                    const int32_t c = col[e];
+                    if (mark[c] != (int32_t)j) {
+                        mark[c] = (int32_t)j;
+                        nb.push_back(c);
+                    }
                 }
             }
+            std::sort(nb.begin(), nb.end());
+            adj[t].insert(adj[t].end(), nb.begin(), nb.end());
+            cnt[t][j - j0] = (int64_t)nb.size();
         }
-        std::sort(nb.begin(), nb.end());
-        g.adj.insert(g.adj.end(), nb.begin(), nb.end());
-        g.ptr[j + 1] = (int64_t)g.adj.size();
+    };
+    std::vector<std::thread> th;
+    try {
+        for (unsigned t = 1; t < nt; ++t) th.emplace_back(work, t);
+    } catch (const std::system_error &) {  // fewer threads to be had: the rest in line
+    }
+    work(0);
+    for (unsigned t = 1 + (unsigned)th.size(); t < nt; ++t) work(t);
+    for (auto &x : th) x.join();
+    for (unsigned t = 0; t < nt; ++t) {
+        const int64_t j0 = n * t / nt;
+        for (size_t q = 0; q < cnt[t].size(); ++q) g.ptr[j0 + (int64_t)q + 1] = g.ptr[j0 + (int64_t)q] + cnt[t][q];
+        g.adj.insert(g.adj.end(), adj[t].begin(), adj[t].end());
     }
 }
 
@@ -82,13 +111,18 @@ class Dissection {
     std::vector<int32_t> run() {
         std::vector<int32_t> all(g_.n);
         for (int64_t v = 0; v < g_.n; ++v) all[v] = (int32_t)v;
-        order_.reserve(g_.n);
-        split(all);
-        return order_;
+        std::vector<int32_t> order;
+        order.reserve(g_.n);
+        split(all, order, 0);
+        return order;
     }
 
   private:
     static constexpr size_t kLeaf = 48;
+    // splits this shallow whose halves both hold this many vertices run the
+    // first half on a thread of its own (at most 2^kThreadDepth at once)
+    static constexpr int kThreadDepth = 3;
+    static constexpr size_t kThreadMin = 4096;
 
     // breadth-first levels inside the current subset (sub_ == id) from root;
     // returns the vertices in visiting order, level_ set for them
@@ -113,13 +147,13 @@ class Dissection {
         return q;
     }
 
-    void split(std::vector<int32_t> &verts) {
+    // appends the order of verts (its halves', then its separator) to out
+    void split(std::vector<int32_t> &verts, std::vector<int32_t> &out, int tdepth) {
         if (verts.size() <= kLeaf) {
-            order_.insert(order_.end(), verts.begin(), verts.end());
+            out.insert(out.end(), verts.begin(), verts.end());
             return;
         }
-        const int32_t id = next_id_;
-        next_id_ += 2;
+        const int32_t id = next_id_.fetch_add(2);
         for (int32_t v : verts) sub_[v] = id;
         // connected components of the subset, each dissected on its own
         int32_t last = 0;
@@ -134,7 +168,7 @@ class Dissection {
                 for (int32_t u : c) sub_[u] = -2;
                 comps.push_back(std::move(c));
             }
-            for (auto &c : comps) split(c);
+            for (auto &c : comps) split(c, out, tdepth);
             return;
         }
         // pseudo-peripheral root: repeat from the farthest vertex while the depth grows
@@ -153,7 +187,7 @@ class Dissection {
         }
         if (maxl < 0) comp = bfs(root, id, &maxl);
         if (maxl < 2) {  // (nearly) complete subgraph: nothing to dissect
-            order_.insert(order_.end(), verts.begin(), verts.end());
+            out.insert(out.end(), verts.begin(), verts.end());
             for (int32_t v : verts) sub_[v] = -1;
             return;
         }
@@ -179,15 +213,31 @@ class Dissection {
             else if (level_[v] > best) b.push_back(v);
             else s.push_back(v);
         }
-        split(a);
-        split(b);
-        order_.insert(order_.end(), s.begin(), s.end());
+        bool done = false;
+        if (tdepth < kThreadDepth && a.size() >= kThreadMin && b.size() >= kThreadMin) {
+            // a and b are not adjacent (their levels differ by two or more), so
+            // the two searches read and write disjoint vertices
+            std::vector<int32_t> oa, ob;
+            try {
+                std::thread t([&] { split(a, oa, tdepth + 1); });
+                split(b, ob, tdepth + 1);
+                t.join();
+                out.insert(out.end(), oa.begin(), oa.end());
+                out.insert(out.end(), ob.begin(), ob.end());
+                done = true;
+            } catch (const std::system_error &) {  // no thread to be had: in line
+            }
+        }
+        if (!done) {
+            split(a, out, tdepth + 1);
+            split(b, out, tdepth + 1);
+        }
+        out.insert(out.end(), s.begin(), s.end());
     }
 
     const Graph &g_;
     std::vector<int32_t> sub_, level_;
-    std::vector<int32_t> order_;
-    int32_t next_id_ = 0;
+    std::atomic<int32_t> next_id_{0};
 };
 
 }  // namespace
