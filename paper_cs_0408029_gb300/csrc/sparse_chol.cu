@@ -457,6 +457,7 @@ __global__ void __launch_bounds__(kSpT)
             const int64_t hc = D.rows_off[c + 1] - D.rows_off[c] - wc;
             const T *uc = ua + D.u_off[c];
             const int32_t *rel = D.rel + D.u_off[c];
+#pragma unroll 4
             for (int64_t i = tid; i < hc; i += kSpT) {
                 const int32_t r = rel[i];
                 if (TS_IN(r, h)) a[r] -= __ldcg(uc + i);
@@ -466,6 +467,7 @@ __global__ void __launch_bounds__(kSpT)
         const T *Ws = Wa + D.W_off[s];
         if (tid < w) {
             T y = T(0);
+#pragma unroll 8
             for (int c = 0; c <= tid; ++c) y += Ws[(int64_t)c * w + tid] * a[c];  // W(r, c), c <= r
             y_sh[tid] = y;
             v[f + tid] = y;
@@ -512,16 +514,25 @@ __global__ void __launch_bounds__(kSpT)
             xb[p] = TS_IN(r, D.n) ? __ldcg(v + r) : T(0);
         }
         __syncthreads();
-        // t_c = y_c - sum_{p >= w} L(p, c) x(rows[p]): a warp per column, its
-        // lanes down the column (coalesced), summed in a fixed order
-        for (int c = warp; c < w; c += kSpT / 32) {
-            const T *lc = Ls + (int64_t)c * ld + w;
-            T acc = T(0);
-#pragma unroll 4
-            for (int64_t p = lane; p < hu; p += 32) acc += lc[p] * xb[p];
+        // t_c = y_c - sum_{p >= w} L(p, c) x(rows[p]): a warp takes four
+        // columns at a time (c0, c0 + 4, c0 + 8, c0 + 12), its lanes down them
+        // (coalesced, four independent sums), each summed in a fixed order
+        for (int c0 = warp; c0 < w; c0 += 16) {
+            T acc[4] = {T(0), T(0), T(0), T(0)};
+            const T *lc = Ls + (int64_t)c0 * ld + w;
+#pragma unroll 2
+            for (int64_t p = lane; p < hu; p += 32) {
+                const T xp = xb[p];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) t_sh[c] = __ldcg(v + f + c) - acc;
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + 4 * q < w) acc[q] += lc[(int64_t)4 * q * ld + p] * xp;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+                if (lane == 0 && c0 + 4 * q < w) t_sh[c0 + 4 * q] = __ldcg(v + f + c0 + 4 * q) - acc[q];
+            }
         }
         __syncthreads();
         const T *Ws = Wa + D.W_off[s];
