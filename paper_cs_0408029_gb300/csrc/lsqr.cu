@@ -273,45 +273,30 @@ __global__ void __launch_bounds__(kLT)
     const int64_t warp_row0 = ((gtid >> 5) << 5) / TPR;
     const int64_t my_off = (gtid / TPR) - warp_row0;
     double acc = 0.0;
-    // two columns per pass (j and j + stride_rows), their loads interleaved,
-    // so that twice the gathers are in flight; each column's sum in its own
-    // order as before
-    for (int64_t j0 = warp_row0; j0 < n; j0 += 2 * stride_rows) {
-        const int64_t jA = j0 + my_off, jB = jA + stride_rows;
-        const bool actA = jA < n && inF[jA], actB = jB < n && inF[jB];
-        const int64_t pA = actA ? ptr[jA] : 0, eA = actA ? ptr[jA + 1] : 0;
-        const int64_t pB = actB ? ptr[jB] : 0, eB = actB ? ptr[jB + 1] : 0;
-        V sA = V(0), sB = V(0);
-        for (int64_t t = sub; pA + t < eA || pB + t < eB; t += 4 * TPR) {
-            int32_t cA[4], cB[4];
-            V aA[4], aB[4];
+    for (int64_t j0 = warp_row0; j0 < n; j0 += stride_rows) {
+        const int64_t j = j0 + my_off;
+        const bool active = j < n && inF[j];
+        V s = V(0);
+        if (active) {
+            const int64_t p1 = ptr[j + 1];
+            for (int64_t p = ptr[j] + sub; p < p1; p += 4 * TPR) {
+                int32_t c[4];
+                V a[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const bool inA = pA + t + q * TPR < eA, inB = pB + t + q * TPR < eB;
-                cA[q] = inA ? idx[pA + t + q * TPR] : 0;
-                aA[q] = inA ? val[pA + t + q * TPR] : V(0);
-                cB[q] = inB ? idx[pB + t + q * TPR] : 0;
-                aB[q] = inB ? val[pB + t + q * TPR] : V(0);
-            }
+                for (int q = 0; q < 4; ++q) {
+                    const bool in = p + q * TPR < p1;
+                    c[q] = in ? idx[p + q * TPR] : 0;
+                    a[q] = in ? val[p + q * TPR] : V(0);
+                }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                sA += TS_IN(cA[q], m) ? aA[q] * u[cA[q]] : V(0);
-                sB += TS_IN(cB[q], m) ? aB[q] * u[cB[q]] : V(0);
+                for (int q = 0; q < 4; ++q) s += TS_IN(c[q], m) ? a[q] * u[c[q]] : V(0);
             }
         }
 #pragma unroll
-        for (int o = TPR / 2; o > 0; o >>= 1) {
-            sA += __shfl_xor_sync(0xffffffffu, sA, o, TPR);
-            sB += __shfl_xor_sync(0xffffffffu, sB, o, TPR);
-        }
-        if (sub == 0 && jA < n) {
-            const V vn = actA ? D[jA] * (sA * inv_beta) - vbeta * v[jA] : V(0);
-            v[jA] = vn;
-            acc += (double)vn * (double)vn;
-        }
-        if (sub == 0 && jB < n) {
-            const V vn = actB ? D[jB] * (sB * inv_beta) - vbeta * v[jB] : V(0);
-            v[jB] = vn;
+        for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+        if (sub == 0 && j < n) {
+            const V vn = active ? D[j] * (s * inv_beta) - vbeta * v[j] : V(0);
+            v[j] = vn;
             acc += (double)vn * (double)vn;
         }
     }
