@@ -119,8 +119,19 @@ NvtxSolve::NvtxSolve(Lane &lane, const char *what) : l(lane) { nvtxRangePushA(wh
 
 NvtxSolve::~NvtxSolve() {
     if (l.nvtx_open) nvtxRangePop();
-    l.nvtx_open = false;
+    if (l.nvtx_pivot_open) nvtxRangePop();
+    l.nvtx_open = l.nvtx_pivot_open = false;
     nvtxRangePop();
+}
+
+void nvtx_pivot(Lane &l, int iter) {
+    if (l.nvtx_open) nvtxRangePop();
+    if (l.nvtx_pivot_open) nvtxRangePop();
+    char name[32];
+    snprintf(name, sizeof name, "pivot %d", iter);
+    nvtxRangePushA(name);
+    l.nvtx_open = false;
+    l.nvtx_pivot_open = true;
 }
 
 void prof_begin(Lane &l, int phase) {
@@ -514,7 +525,8 @@ int solve_factor(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         int open_steps = 0;
         double open_prev = 0.0;
 
-        for (;;) {
+        for (int pivot_range = 1;; ++pivot_range) {
+            nvtx_pivot(lane, pivot_range);
             prof_begin(lane, TSNNLS_PHASE_EXCHANGE);
             TRY_CUDA(launch_exchange(s, n, x, y, inF, F, o.zero_tol, o.p_max, max_iter,
                                      lane.st_host->iters > 0 ? 1 : 0, lane.st_dev));

@@ -49,7 +49,8 @@ struct Lane {
     std::vector<PhaseMark> marks;
     int64_t mark_launch0 = 0;
     tsnnls_phase_stat stats[TSNNLS_NUM_PHASES] = {};
-    bool nvtx_open = false;  // a phase range is open on the NVTX stack
+    bool nvtx_open = false;        // a phase range is open on the NVTX stack
+    bool nvtx_pivot_open = false;  // and under it a pivot's range
     // the batched path's last graph and device arena, replayed by the next
     // call of the same shape (batch.cu owns it; batch_cache_release frees it)
     void *batch_cache = nullptr;
@@ -65,6 +66,9 @@ struct NvtxSolve {
     NvtxSolve(Lane &lane, const char *what);
     ~NvtxSolve();
 };
+
+// Start pivot `iter`'s range (ends the previous pivot's and any open phase).
+void nvtx_pivot(Lane &l, int iter);
 
 // Bracket a phase with events on the lane's stream (no-ops unless prof).
 void prof_begin(Lane &l, int phase);

@@ -607,7 +607,8 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
         prof_end(lane, csc_bytes + 8.0 * (m + n), 2.0 * nnz);
         TRY_CUDA_L(launch_init_state(s, n, c, x, y, inF, o.p_max, lane.st_dev));
 
-        for (;;) {
+        for (int pivot_range = 1;; ++pivot_range) {
+            nvtx_pivot(lane, pivot_range);
             // keep the current x as the warm start of the next LSQR run
             TRY_CUDA_L(cudaMemcpyAsync(xprev, x, 8 * n, cudaMemcpyDeviceToDevice, s));
             prof_begin(lane, TSNNLS_PHASE_EXCHANGE);

@@ -185,3 +185,29 @@ def test_batch_single_exchange_fallback(env, oracle_mod):
         xv = xt.cpu().numpy()
         assert np.linalg.norm(xv - ref.x) <= 1e-9 * np.linalg.norm(ref.x), p.name
     assert singles >= 3
+
+
+def test_batched_full_size_sampled(env, oracle_mod):
+    """The bench's configuration: all 512 problems of the batched workload in
+    one call (MIXED).  Every result passes the KKT test of Eq. 3; the three
+    largest problems and five others drawn with a fixed seed are compared
+    with the oracle one by one."""
+    ts, ctx, torch = env
+    probs = workloads.batched_uneven()
+    assert len(probs) == 512
+    st, stat, info, xs = _run(ts, ctx, torch, probs, "mixed")
+    assert st == ts.OK and (stat == ts.OK).all(), stat
+    for p, x in zip(probs, xs):  # dense KKT in numpy, on the FP64 copy of the FP32 values
+        a = p.a.astype(np.float64)
+        y = a.T @ (a @ x - p.b)
+        scale = np.linalg.norm(a.T @ p.b)
+        assert x.min() >= 0.0, p.name
+        assert -y.min() <= 1e-10 * scale, p.name
+        assert np.max(np.abs(x * y) / np.maximum(1.0, np.abs(x))) <= 1e-10 * scale, p.name
+    ns = np.array([p.n for p in probs])
+    pick = list(np.argsort(-ns, kind="stable")[:3]) + list(np.random.default_rng(7).choice(512, 5, replace=False))
+    for i in pick:
+        p = probs[int(i)]
+        ref = oracle_mod.bpp_solve(workloads.dense_to_csr(p.a.astype(np.float64), p.b))
+        err = np.linalg.norm(xs[int(i)] - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-9, (p.name, err)
