@@ -151,111 +151,114 @@ __device__ __noinline__ void sp_extend_add(const T *__restrict__ Uc, int64_t ldu
     }
 }
 
-// FP32: U -= X X^T on the lower triangle (X: hu rows x w <= 64 columns,
-// leading dimension ld; U leading dimension ldu) by 128 x 128 blocks of U
-// (only those on or below the diagonal): the block's row and column panels
-// of X are staged in shared memory (sm: two 64 x 132 panels, k-major) and
-// each thread accumulates an 8 x 8 register tile over all w columns, then
-// loads its 64 entries of U before storing any.  A block of a 723-row
-// update then costs 128 x 128 x w FMAs from shared memory instead of
-// 8 global loads per 16 FMAs.
-__device__ __noinline__ void sp_syrk_tiled(const float *X, int64_t ld, int64_t hu, int w, float *U, int64_t ldu,
-                                           float *sm) {
+// FP32: block (I, J) (I >= J) of U -= X X^T on the lower triangle (X: hu
+// rows x w <= 64 columns, leading dimension ld; U leading dimension ldu;
+// blocks of 128 x 128): the block's row and column panels of X are staged
+// in shared memory (sm: two 64 x 132 panels, k-major) and each thread
+// accumulates an 8 x 8 register tile over all w columns, then loads its 64
+// entries of U before storing any.  A block then costs 128 x 128 x w FMAs
+// from shared memory instead of 8 global loads per 16 FMAs.  Called by all
+// 256 threads.
+__device__ __noinline__ void sp_syrk_block(const float *X, int64_t ld, int64_t hu, int w, float *U, int64_t ldu,
+                                           float *sm, int64_t I, int64_t J) {
     constexpr int BM = 128, P = BM + 4;
     float(*Xa)[P] = reinterpret_cast<float(*)[P]>(sm);            // Xa[k][i] = X(I0 + i, k)
     float(*Xb)[P] = reinterpret_cast<float(*)[P]>(sm + 64 * P);   // Xb[k][j] = X(J0 + j, k)
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t nb = (hu + BM - 1) / BM;
-    for (int64_t I = 0; I < nb; ++I) {
-        for (int64_t J = 0; J <= I; ++J) {
-            const int64_t I0 = I * BM, J0 = J * BM;
-            __syncthreads();
-            // eight elements of each panel per thread in flight
-            for (int e0 = tid; e0 < w * BM; e0 += 256 * 8) {
-                float va[8], vb[8];
+    const int64_t I0 = I * BM, J0 = J * BM;
+    __syncthreads();
+    // eight elements of each panel per thread in flight
+    for (int e0 = tid; e0 < w * BM; e0 += 256 * 8) {
+        float va[8], vb[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = e0 + 256 * u, k = e / BM, i = e % BM;
-                    va[u] = (e < w * BM && I0 + i < hu) ? X[(int64_t)k * ld + I0 + i] : 0.f;
-                    vb[u] = (e < w * BM && J0 + i < hu) ? X[(int64_t)k * ld + J0 + i] : 0.f;
-                }
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + 256 * u, k = e / BM, i = e % BM;
+            va[u] = (e < w * BM && I0 + i < hu) ? X[(int64_t)k * ld + I0 + i] : 0.f;
+            vb[u] = (e < w * BM && J0 + i < hu) ? X[(int64_t)k * ld + J0 + i] : 0.f;
+        }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = e0 + 256 * u, k = e / BM, i = e % BM;
-                    if (e < w * BM) {
-                        Xa[k][i] = va[u];
-                        Xb[k][i] = vb[u];
-                    }
-                }
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + 256 * u, k = e / BM, i = e % BM;
+            if (e < w * BM) {
+                Xa[k][i] = va[u];
+                Xb[k][i] = vb[u];
             }
-            __syncthreads();
-            // thread (tx, ty): rows I0 + 4 tx .. + 3 and I0 + 64 + 4 tx .. + 3 (16
-            // lanes run down a column of U: 16-byte accesses), columns likewise
-            // from ty
-            float acc[8][8];
+        }
+    }
+    __syncthreads();
+    // thread (tx, ty): rows I0 + 4 tx .. + 3 and I0 + 64 + 4 tx .. + 3 (16
+    // lanes run down a column of U: 16-byte accesses), columns likewise
+    // from ty
+    float acc[8][8];
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-            for (int k = 0; k < w; ++k) {
-                const float4 a0 = *reinterpret_cast<const float4 *>(&Xa[k][tx * 4]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&Xa[k][64 + tx * 4]);
-                const float4 b0 = *reinterpret_cast<const float4 *>(&Xb[k][ty * 4]);
-                const float4 b1 = *reinterpret_cast<const float4 *>(&Xb[k][64 + ty * 4]);
-                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    for (int k = 0; k < w; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(&Xa[k][tx * 4]);
+        const float4 a1 = *reinterpret_cast<const float4 *>(&Xa[k][64 + tx * 4]);
+        const float4 b0 = *reinterpret_cast<const float4 *>(&Xb[k][ty * 4]);
+        const float4 b1 = *reinterpret_cast<const float4 *>(&Xb[k][64 + ty * 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-                for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < 8; ++a)
 #pragma unroll
-                    for (int b = 0; b < 8; ++b) acc[a][b] += av[a] * bv[b];
-            }
-            // U's entries: a whole 4-row group with one 16-byte load when it
-            // lies inside the lower triangle (ldu, the offsets and the row
-            // start are multiples of 4), entry by entry otherwise; every load
-            // before the first store
-            float cv[8][8];
+            for (int b = 0; b < 8; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    // U's entries: a whole 4-row group with one 16-byte load when it
+    // lies inside the lower triangle (ldu, the offsets and the row
+    // start are multiples of 4), entry by entry otherwise; every load
+    // before the first store
+    float cv[8][8];
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const int64_t j = J0 + (b < 4 ? ty * 4 + b : 64 + ty * 4 + b - 4);
+    for (int b = 0; b < 8; ++b) {
+        const int64_t j = J0 + (b < 4 ? ty * 4 + b : 64 + ty * 4 + b - 4);
 #pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int64_t i4 = I0 + 64 * hh + tx * 4;
-                    if (j < hu && i4 + 3 < hu && i4 >= j) {
-                        const float4 u4 = *reinterpret_cast<const float4 *>(&U[j * ldu + i4]);
-                        cv[4 * hh][b] = u4.x;
-                        cv[4 * hh + 1][b] = u4.y;
-                        cv[4 * hh + 2][b] = u4.z;
-                        cv[4 * hh + 3][b] = u4.w;
-                    } else {
+        for (int hh = 0; hh < 2; ++hh) {
+            const int64_t i4 = I0 + 64 * hh + tx * 4;
+            if (j < hu && i4 + 3 < hu && i4 >= j) {
+                const float4 u4 = *reinterpret_cast<const float4 *>(&U[j * ldu + i4]);
+                cv[4 * hh][b] = u4.x;
+                cv[4 * hh + 1][b] = u4.y;
+                cv[4 * hh + 2][b] = u4.z;
+                cv[4 * hh + 3][b] = u4.w;
+            } else {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int64_t i = i4 + q;
-                            cv[4 * hh + q][b] = (i < hu && j < hu && i >= j) ? U[j * ldu + i] : 0.f;
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const int64_t j = J0 + (b < 4 ? ty * 4 + b : 64 + ty * 4 + b - 4);
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int64_t i4 = I0 + 64 * hh + tx * 4;
-                    if (j < hu && i4 + 3 < hu && i4 >= j) {
-                        *reinterpret_cast<float4 *>(&U[j * ldu + i4]) =
-                            make_float4(cv[4 * hh][b] - acc[4 * hh][b], cv[4 * hh + 1][b] - acc[4 * hh + 1][b],
-                                        cv[4 * hh + 2][b] - acc[4 * hh + 2][b], cv[4 * hh + 3][b] - acc[4 * hh + 3][b]);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int64_t i = i4 + q;
-                            if (i < hu && j < hu && i >= j) U[j * ldu + i] = cv[4 * hh + q][b] - acc[4 * hh + q][b];
-                        }
-                    }
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t i = i4 + q;
+                    cv[4 * hh + q][b] = (i < hu && j < hu && i >= j) ? U[j * ldu + i] : 0.f;
                 }
             }
         }
     }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int64_t j = J0 + (b < 4 ? ty * 4 + b : 64 + ty * 4 + b - 4);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int64_t i4 = I0 + 64 * hh + tx * 4;
+            if (j < hu && i4 + 3 < hu && i4 >= j) {
+                *reinterpret_cast<float4 *>(&U[j * ldu + i4]) =
+                    make_float4(cv[4 * hh][b] - acc[4 * hh][b], cv[4 * hh + 1][b] - acc[4 * hh + 1][b],
+                                cv[4 * hh + 2][b] - acc[4 * hh + 2][b], cv[4 * hh + 3][b] - acc[4 * hh + 3][b]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t i = i4 + q;
+                    if (i < hu && j < hu && i >= j) U[j * ldu + i] = cv[4 * hh + q][b] - acc[4 * hh + q][b];
+                }
+            }
+        }
+    }
+}
+
+// All blocks of one update matrix by this CTA alone.
+__device__ __noinline__ void sp_syrk_tiled(const float *X, int64_t ld, int64_t hu, int w, float *U, int64_t ldu,
+                                           float *sm) {
+    const int64_t nb = (hu + 127) / 128;
+    for (int64_t I = 0; I < nb; ++I)
+        for (int64_t J = 0; J <= I; ++J) sp_syrk_block(X, ld, hu, w, U, ldu, sm, I, J);
 }
 
 // U -= X X^T on the lower triangle (X: hu rows x w columns, leading dimension
@@ -301,6 +304,154 @@ __device__ __noinline__ void sp_syrk(const T *X, int64_t ld, int64_t hu, int w, 
     }
 }
 
+// ---- shared update-matrix jobs (FP32 factor) ---------------------------------
+// The update matrix of a tall supernode near the root is most of the work on
+// the factor's critical path, while most CTAs wait for children there.  Its
+// owner posts it as a job of 128 x 128 blocks in its CTA's slot; CTAs that
+// wait for children take blocks meanwhile (a compare-and-swap on the slot's
+// word, which carries the supernode and the block count, so a stale read
+// never claims a block of a job that is not posted); the owner takes blocks
+// too, waits (bounded) until every block is done, frees the slot and only
+// then publishes its flag.  A block waits on nothing once claimed, so every
+// claimed block completes.
+
+constexpr int64_t kSpJobMinBlocks = 3;  // update matrices of at least 3 blocks (more than 128 rows)
+
+__device__ __forceinline__ unsigned long long sp_word_load(unsigned long long *p) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+    return a.load(cuda::memory_order_acquire);
+}
+__device__ __forceinline__ void sp_word_store(unsigned long long *p, unsigned long long v) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+    a.store(v, cuda::memory_order_release);
+}
+__device__ __forceinline__ bool sp_word_open(unsigned long long w) {
+    return (w >> 40) != 0 && (w & 0xFFFFFull) < ((w >> 20) & 0xFFFFFull);
+}
+
+// One thread: claim the next block of the job in slot sl, starting from the
+// word value w.  Returns the supernode (>= 0) and the block, or -1 once the
+// job has no block left.  A failed swap means that another CTA claimed a
+// block (or the job is gone), so the loop ends after at most as many turns
+// as the job has blocks.
+__device__ __forceinline__ int64_t sp_claim_slot(const SpDev &D, int sl, unsigned long long w, int64_t *blk) {
+    while (sp_word_open(w)) {
+        const unsigned long long prev = atomicCAS(D.job_word + sl, w, w + 1);
+        if (prev == w) {
+            *blk = (int64_t)(w & 0xFFFFFull);
+            __threadfence();  // the owner's panel, published before its word, is visible from here on
+            return (int64_t)(w >> 40) - 1;
+        }
+        w = prev;
+    }
+    return -1;
+}
+
+// Warp 0: claim one block of any open job, the slots scanned by the lanes
+// from `first` round robin.  Returns the supernode (>= 0), its block and
+// slot, or -1.  Uniform across the warp.
+__device__ int64_t sp_claim_any(const SpDev &D, int first, int64_t *blk, int *slot) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < D.njobs; base += 32) {
+        const int sl = (first + base + lane) % D.njobs;
+        unsigned long long w = 0;
+        if (base + lane < D.njobs) w = sp_word_load(D.job_word + sl);
+        unsigned m = __ballot_sync(0xffffffffu, sp_word_open(w));
+        while (m) {
+            const int src = __ffs(m) - 1;
+            const int slw = __shfl_sync(0xffffffffu, sl, src);
+            const unsigned long long ww = __shfl_sync(0xffffffffu, w, src);
+            long long got = -1, gb = 0;
+            if (lane == 0) {
+                int64_t b = 0;
+                got = sp_claim_slot(D, slw, ww, &b);
+                gb = b;
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            gb = __shfl_sync(0xffffffffu, gb, 0);
+            if (got >= 0) {
+                *blk = gb;
+                *slot = slw;
+                return got;
+            }
+            m &= m - 1;
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void sp_block_ij(int64_t b, int64_t &I, int64_t &J) {
+    int64_t i = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > b) --i;
+    while ((i + 1) * (i + 2) / 2 <= b) ++i;
+    I = i;
+    J = b - i * (i + 1) / 2;
+}
+
+// Block b of supernode s's update matrix (all 256 threads).
+__device__ void sp_job_block(const SpDev &D, const float *L, float *Ua, float *sm, int64_t s, int64_t b) {
+    const int32_t w = D.sn_first[s + 1] - D.sn_first[s];
+    const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4;
+    const int64_t hu = h - w, ldu = (hu + 3) / 4 * 4;
+    int64_t I, J;
+    sp_block_ij(b, I, J);
+    sp_syrk_block(L + D.L_off[s] + w, ld, hu, w, Ua + D.U_off[s], ldu, sm, I, J);
+}
+
+// The factor's wait for flags[list[b..e)]: bounded, and taking blocks of
+// open jobs meanwhile.  Uniform across the CTA; false on abort or timeout.
+__device__ bool sp_wait_help(const SpDev &D, const int32_t *list, int64_t b, int64_t e, const float *L, float *Ua,
+                             float *sm, DevStatus *st, long long *sh) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int idle = 0;
+    for (;;) {
+        if (warp == 0) {
+            bool notready = false;
+            for (int64_t i = b + lane; i < e; i += 32) notready |= sp_flag_load(D.flags + list[i]) == 0;
+            long long cmd = -1;  // -1: ready, -2: nothing to take, -3: abort, else a claimed supernode
+            int64_t blk = 0;
+            int slot = 0;
+            if (__any_sync(0xffffffffu, notready)) {
+                if (sp_flag_load(D.abort) != 0) {
+                    cmd = -3;
+                } else {
+                    const int64_t j = sp_claim_any(D, (int)((blockIdx.x + 1) % max(D.njobs, 1)), &blk, &slot);
+                    cmd = j >= 0 ? j : -2;
+                }
+            }
+            if (lane == 0) {
+                sh[0] = cmd;
+                sh[1] = blk;
+                sh[2] = slot;
+            }
+        }
+        __syncthreads();
+        const long long cmd = sh[0], blk = sh[1];
+        const int slot = (int)sh[2];
+        __syncthreads();
+        if (cmd == -1) return true;
+        if (cmd == -3) return false;
+        if (cmd == -2) {
+            if (++idle > kSpinLimit) {
+                if (tid == 0) {
+                    sp_flag_store(D.abort, 1);
+                    st->timeout = 1;
+                }
+                return false;
+            }
+            if (tid == 0 && idle > 8) __nanosleep(32);
+            continue;
+        }
+        idle = 0;
+        sp_job_block(D, L, Ua, sm, cmd, blk);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(D.job_done + slot, 1);
+        }
+    }
+}
+
 template <typename T, int NB>
 struct SpSmem {
     static constexpr int P = NB + 4;
@@ -323,6 +474,7 @@ __global__ void __launch_bounds__(256, 1)
     T(*W32)[36] = reinterpret_cast<T(*)[36]>(smem_raw + sizeof(T) * NB * SM::P);
     T(*Bs)[36] = reinterpret_cast<T(*)[36]>(smem_raw + 2 * sizeof(T) * NB * SM::P);  // Bs[t][r]
     __shared__ int sh_s, ok_sh, bad_sh;
+    __shared__ long long job_sh[3];
     __shared__ __align__(16) T col[2][32];
     const int tid = threadIdx.x;
     for (;;) {
@@ -330,7 +482,13 @@ __global__ void __launch_bounds__(256, 1)
         __syncthreads();
         const int64_t s = sh_s;
         if (s >= D.ns) return;
-        if (!sp_wait_all(D, D.flags, D.clist, D.c_off[s], D.c_off[s + 1], st, &ok_sh)) return;
+        if constexpr (sizeof(T) == 4) {
+            if (!sp_wait_help(D, D.clist, D.c_off[s], D.c_off[s + 1], reinterpret_cast<const float *>(L),
+                              reinterpret_cast<float *>(Ua), reinterpret_cast<float *>(smem_raw), st, job_sh))
+                return;
+        } else {
+            if (!sp_wait_all(D, D.flags, D.clist, D.c_off[s], D.c_off[s + 1], st, &ok_sh)) return;
+        }
         const int32_t f = D.sn_first[s], w = D.sn_first[s + 1] - f;
         const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4;
         const int64_t hu = h - w, ldu = (hu + 3) / 4 * 4;
@@ -418,10 +576,63 @@ __global__ void __launch_bounds__(256, 1)
         }
         __syncthreads();
         // update matrix: U -= X X^T on its lower triangle, X = rows below (hu x w)
-        if constexpr (sizeof(T) == 4)
-            sp_syrk_tiled(P + w, ld, hu, w, U, ldu, reinterpret_cast<float *>(smem_raw));
-        else
+        if constexpr (sizeof(T) == 4) {
+            const int64_t nbu = (hu + 127) / 128, nblk = nbu * (nbu + 1) / 2;
+            const int slot = (int)blockIdx.x;
+            if (nblk >= kSpJobMinBlocks && slot < D.njobs && nblk < (1 << 20)) {
+                // post the job: the panel and U (zeroed, children added) are
+                // complete; the count of finished blocks is reset first
+                if (tid == 0) {
+                    D.job_done[slot] = 0;
+                    __threadfence();
+                    sp_word_store(D.job_word + slot,
+                                  ((unsigned long long)(s + 1) << 40) | ((unsigned long long)nblk << 20));
+                }
+                __syncthreads();
+                // take blocks of it until none is left
+                for (;;) {
+                    if (tid == 0) {
+                        int64_t b = 0;
+                        const int64_t got = sp_claim_slot(D, slot, sp_word_load(D.job_word + slot), &b);
+                        job_sh[0] = got >= 0 ? b : -1;
+                    }
+                    __syncthreads();
+                    const long long b = job_sh[0];
+                    __syncthreads();
+                    if (b < 0) break;
+                    sp_job_block(D, reinterpret_cast<const float *>(L), reinterpret_cast<float *>(Ua),
+                                 reinterpret_cast<float *>(smem_raw), s, b);
+                    __syncthreads();
+                    if (tid == 0) {
+                        __threadfence();
+                        atomicAdd(D.job_done + slot, 1);
+                    }
+                }
+                // wait (bounded) for the blocks other CTAs took, then free the slot
+                if (tid == 0) {
+                    int ok = 1, spins = 0;
+                    cuda::atomic_ref<int32_t, cuda::thread_scope_device> dn(D.job_done[slot]);
+                    while (dn.load(cuda::memory_order_acquire) < (int32_t)nblk) {
+                        if (sp_flag_load(D.abort) != 0) { ok = 0; break; }
+                        if (++spins > kSpinLimit) {
+                            sp_flag_store(D.abort, 1);
+                            st->timeout = 1;
+                            ok = 0;
+                            break;
+                        }
+                        if (spins > 8) __nanosleep(32);
+                    }
+                    if (ok) sp_word_store(D.job_word + slot, 0ull);
+                    ok_sh = ok;
+                }
+                __syncthreads();
+                if (!ok_sh) return;
+            } else {
+                sp_syrk_tiled(P + w, ld, hu, w, U, ldu, reinterpret_cast<float *>(smem_raw));
+            }
+        } else {
             sp_syrk<T>(P + w, ld, hu, w, U, ldu);
+        }
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -572,6 +783,7 @@ size_t SparseChol<T>::device_bytes(const SparseSym &S, int /*ctas*/) {
     b += up(sizeof(T) * (size_t)S.L_off[ns]) + up(sizeof(T) * (size_t)S.W_off[ns]);
     b += up(sizeof(T) * (size_t)S.U_off[ns]) + up(sizeof(T) * nu + 4);   // update matrices and vectors
     b += up(4 * ns) + up(16) + up(4 * n);                                // flags, ticket / abort, permF
+    b += up(8 * (size_t)kSpJobSlots) + up(4 * (size_t)kSpJobSlots);      // job words and counts
     return b + 256;
 }
 
@@ -615,6 +827,9 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     int32_t *flags = (int32_t *)take(4 * ns);
     int32_t *ctl = (int32_t *)take(16);
     permF = (int32_t *)take(4 * n);
+    D.job_word = (unsigned long long *)take(8 * (size_t)kSpJobSlots);
+    D.job_done = (int32_t *)take(4 * (size_t)kSpJobSlots);
+    D.njobs = ctas <= kSpJobSlots ? ctas : 0;
     // per-entry original column of the lower pattern
     std::vector<int32_t> gcol(ng);
     for (int64_t j = 0; j < S.n; ++j)
@@ -685,6 +900,8 @@ cudaError_t SparseChol<T>::factor(cudaStream_t s, const uint8_t *inF, DevStatus 
     cudaError_t e = cudaFuncSetAttribute(sp_factor_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess) e = reset(s);
+    if (e == cudaSuccess && sizeof(T) == 4)  // no job is open (an aborted factor may have left one)
+        e = cudaMemsetAsync(D.job_word, 0, sizeof(unsigned long long) * kSpJobSlots, s);
     if (e != cudaSuccess) return e;
     sp_factor_kernel<T, NB><<<ctas, 256, smem, s>>>(D, inF, Lmem, Wmem, Umem, st);
     note_launches(1);
