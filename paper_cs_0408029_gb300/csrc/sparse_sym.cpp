@@ -21,10 +21,13 @@
 //      supernodes that hold its rows below, the offsets of its panel of L,
 //      of its update matrix and of its diagonal block's inverse, and where
 //      every entry of the lower triangle of P G P^T lands in the panels.
-// Plain C++; deterministic: no hashing, and the dissection's top splits hand
-// one half to a thread of its own (the halves touch disjoint vertices, and
-// their orders are joined in a fixed order), so the result does not depend
-// on the threads' timing.
+// Plain C++ on up to 16 threads, deterministic: no hashing; the
+// dissection's top splits hand one half to a thread of its own (the halves
+// touch disjoint vertices, and their orders are joined in a fixed order);
+// the per-column and per-supernode stages run on ranges of columns or
+// supernodes, and the column structures on disjoint subtrees of the
+// elimination tree, each writing only its own outputs.  The result does
+// not depend on the threads' timing.
 #include "sparse_sym.h"
 
 #include <algorithm>
@@ -44,6 +47,28 @@ struct Graph {
     std::vector<int32_t> adj;  // neighbours, no self loops, ascending
 };
 
+// Threads for one stage: up to 16, one per 4096 units of work.
+unsigned stage_threads(int64_t work) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t want = std::max<int64_t>(1, work / 4096);
+    return (unsigned)std::min<int64_t>(std::min<int64_t>(16, (int64_t)hw), want);
+}
+
+// fn(t) for t = 0 .. nt - 1, each on a thread of its own where one can be
+// had (the calling thread takes t = 0 and whatever no thread could).  The
+// parts write disjoint outputs, so the result does not depend on timing.
+template <typename Fn>
+void run_parts(unsigned nt, Fn &&fn) {
+    std::vector<std::thread> th;
+    try {
+        for (unsigned t = 1; t < nt; ++t) th.emplace_back(fn, t);
+    } catch (const std::system_error &) {  // fewer threads to be had: the rest in line
+    }
+    fn(0u);
+    for (unsigned t = 1 + (unsigned)th.size(); t < nt; ++t) fn(t);
+    for (auto &x : th) x.join();
+}
+
 // Pattern of A^T A without the diagonal, as adjacency lists.
 void gram_graph(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col, Graph &g) {
     const int64_t nnz = row_ptr[m];
@@ -61,8 +86,7 @@ void gram_graph(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col
     g.adj.clear();
     // columns in contiguous ranges, one per thread (each with its own marks
     // and output), joined in column order
-    unsigned nt = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
-    if (n < 4096) nt = 1;
+    const unsigned nt = stage_threads(n);
     std::vector<std::vector<int32_t>> adj(nt);
     std::vector<std::vector<int64_t>> cnt(nt);
     auto work = [&](unsigned t) {
@@ -88,14 +112,7 @@ void gram_graph(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col
             cnt[t][j - j0] = (int64_t)nb.size();
         }
     };
-    std::vector<std::thread> th;
-    try {
-        for (unsigned t = 1; t < nt; ++t) th.emplace_back(work, t);
-    } catch (const std::system_error &) {  // fewer threads to be had: the rest in line
-    }
-    work(0);
-    for (unsigned t = 1 + (unsigned)th.size(); t < nt; ++t) work(t);
-    for (auto &x : th) x.join();
+    run_parts(nt, work);
     for (unsigned t = 0; t < nt; ++t) {
         const int64_t j0 = n * t / nt;
         for (size_t q = 0; q < cnt[t].size(); ++q) g.ptr[j0 + (int64_t)q + 1] = g.ptr[j0 + (int64_t)q] + cnt[t][q];
@@ -300,11 +317,17 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
                 }
             }
         }
-        std::vector<int32_t> p2(n);
-        for (int64_t k = 0; k < n; ++k) p2[k] = perm[post[k]];
+        // a postorder is a topological order of the tree, so the tree of
+        // the reordered matrix is the same tree relabelled
+        std::vector<int32_t> p2(n), ipost(n), par2(n);
+        for (int64_t k = 0; k < n; ++k) ipost[post[k]] = (int32_t)k;
+        for (int64_t k = 0; k < n; ++k) {
+            p2[k] = perm[post[k]];
+            par2[k] = parent[post[k]] < 0 ? -1 : ipost[parent[post[k]]];
+        }
         perm.swap(p2);
+        parent.swap(par2);
         for (int64_t k = 0; k < n; ++k) iperm[perm[k]] = (int32_t)k;
-        etree_of(perm, iperm, parent);
     }
 
     // lower pattern of P G P^T by column (new indices), diagonal first
@@ -312,22 +335,34 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
     S.gptr.assign(n + 1, 0);
     S.grow.clear();
     S.gpair_orig_row.clear();
+    const unsigned nt = stage_threads(n);
     {
-        std::vector<int32_t> rows;
-        for (int64_t j = 0; j < n; ++j) {
-            rows.clear();
-            const int32_t vj = perm[j];
-            for (int64_t p = g.ptr[vj]; p < g.ptr[vj + 1]; ++p) {
-                const int32_t i = iperm[g.adj[p]];
-                if (i > j) rows.push_back(i);
+        // counts, then each column range fills its own part
+        run_parts(nt, [&](unsigned t) {
+            for (int64_t j = n * t / nt; j < n * (t + 1) / nt; ++j) {
+                const int32_t vj = perm[j];
+                int64_t c = 1;
+                for (int64_t p = g.ptr[vj]; p < g.ptr[vj + 1]; ++p) c += iperm[g.adj[p]] > j;
+                S.gptr[j + 1] = c;
             }
-            std::sort(rows.begin(), rows.end());
-            S.grow.push_back((int32_t)j);
-            S.grow.insert(S.grow.end(), rows.begin(), rows.end());
-            S.gptr[j + 1] = (int64_t)S.grow.size();
-        }
-        S.gpair_orig_row.resize(S.grow.size());
-        for (size_t e = 0; e < S.grow.size(); ++e) S.gpair_orig_row[e] = perm[S.grow[e]];
+        });
+        for (int64_t j = 0; j < n; ++j) S.gptr[j + 1] += S.gptr[j];
+        S.grow.resize(S.gptr[n]);
+        S.gpair_orig_row.resize(S.gptr[n]);
+        run_parts(nt, [&](unsigned t) {
+            for (int64_t j = n * t / nt; j < n * (t + 1) / nt; ++j) {
+                int32_t *o = S.grow.data() + S.gptr[j];
+                int64_t c = 0;
+                o[c++] = (int32_t)j;
+                const int32_t vj = perm[j];
+                for (int64_t p = g.ptr[vj]; p < g.ptr[vj + 1]; ++p) {
+                    const int32_t i = iperm[g.adj[p]];
+                    if (i > j) o[c++] = i;
+                }
+                std::sort(o + 1, o + c);
+                for (int64_t q = 0; q < c; ++q) S.gpair_orig_row[S.gptr[j] + q] = perm[o[q]];
+            }
+        });
     }
 
     // 4. column structures (rows below the diagonal), children merged
@@ -344,12 +379,9 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
         // the column's own rows (sorted), then each child's rows after j
         // merged in (both sorted, duplicates dropped): linear in the sizes,
         // no sort of the merged structure
-        std::vector<int32_t> tmp;
-        for (int64_t j = 0; j < n; ++j) {
+        auto column = [&](int64_t j, std::vector<int32_t> &tmp) {
             std::vector<int32_t> &v = cs[j];
-            for (int64_t p = S.gptr[j] + 1; p < S.gptr[j + 1]; ++p) v.push_back(S.grow[p]);
-            std::sort(v.begin(), v.end());
-            v.erase(std::unique(v.begin(), v.end()), v.end());
+            v.assign(S.grow.begin() + S.gptr[j] + 1, S.grow.begin() + S.gptr[j + 1]);  // sorted, distinct
             for (int32_t c = first_child[j]; c >= 0; c = sib[c]) {
                 const std::vector<int32_t> &w = cs[c];
                 auto b = std::upper_bound(w.begin(), w.end(), (int32_t)j);  // rows below j only
@@ -368,7 +400,28 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
                 tmp.insert(tmp.end(), b, w.end());
                 v.swap(tmp);
             }
-        }
+        };
+        // In the postorder a subtree is the range of columns that ends at
+        // its root.  The subtrees of at most `thr` columns whose parent's
+        // is larger are independent: threads take them largest first; the
+        // columns above them follow in order.
+        std::vector<int64_t> desc(n, 1);
+        for (int64_t j = 0; j < n; ++j)
+            if (parent[j] >= 0) desc[parent[j]] += desc[j];
+        const int64_t thr = std::max<int64_t>(256, n / (8 * (int64_t)nt));
+        std::vector<int32_t> task;
+        for (int64_t j = 0; j < n; ++j)
+            if (desc[j] <= thr && (parent[j] < 0 || desc[parent[j]] > thr)) task.push_back((int32_t)j);
+        std::stable_sort(task.begin(), task.end(), [&](int32_t a, int32_t b) { return desc[a] > desc[b]; });
+        std::atomic<size_t> next_task{0};
+        run_parts(nt, [&](unsigned) {
+            std::vector<int32_t> tmp;
+            for (size_t q; (q = next_task.fetch_add(1)) < task.size();)
+                for (int64_t j = task[q] - desc[task[q]] + 1; j <= task[q]; ++j) column(j, tmp);
+        });
+        std::vector<int32_t> tmp;
+        for (int64_t j = 0; j < n; ++j)
+            if (desc[j] > thr) column(j, tmp);
     }
 
     // 5. fundamental supernodes, at most max_width wide ...
@@ -478,15 +531,17 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
             if (S.sparent[sn] >= 0) S.clist[fill[S.sparent[sn]]++] = (int32_t)sn;
     }
     S.rel.assign(S.u_off[ns], 0);
-    for (int64_t sn = 0; sn < ns; ++sn) {
-        const int32_t pa = S.sparent[sn];
-        if (pa < 0) continue;
-        const int32_t w = S.sn_first[sn + 1] - S.sn_first[sn];
-        const int32_t *pb = S.rows.data() + S.rows_off[pa], *pe = S.rows.data() + S.rows_off[pa + 1];
-        int64_t k = S.u_off[sn];
-        for (int64_t q = S.rows_off[sn] + w; q < S.rows_off[sn + 1]; ++q)
-            S.rel[k++] = (int32_t)(std::lower_bound(pb, pe, S.rows[q]) - pb);
-    }
+    run_parts(nt, [&](unsigned t) {
+        for (int64_t sn = ns * t / nt; sn < ns * (t + 1) / nt; ++sn) {
+            const int32_t pa = S.sparent[sn];
+            if (pa < 0) continue;
+            const int32_t w = S.sn_first[sn + 1] - S.sn_first[sn];
+            const int32_t *pb = S.rows.data() + S.rows_off[pa], *pe = S.rows.data() + S.rows_off[pa + 1];
+            int64_t k = S.u_off[sn];
+            for (int64_t q = S.rows_off[sn] + w; q < S.rows_off[sn + 1]; ++q)
+                S.rel[k++] = (int32_t)(std::lower_bound(pb, pe, S.rows[q]) - pb);
+        }
+    });
     // A(s): the supernodes holding s's rows below (ascending), for the backward solve
     S.a_off.assign(ns + 1, 0);
     S.alist.clear();
@@ -505,15 +560,17 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
     // where each lower entry of P G P^T lands: panel of its column's
     // supernode, column j - f, local row = position of i among the rows
     S.gpos.resize(S.grow.size());
-    for (int64_t j = 0; j < n; ++j) {
-        const int32_t s = S.col_sn[j], f = S.sn_first[s];
-        const int64_t h = S.rows_off[s + 1] - S.rows_off[s], ld = (h + 3) / 4 * 4;
-        const int32_t *rb = S.rows.data() + S.rows_off[s], *re = S.rows.data() + S.rows_off[s + 1];
-        for (int64_t p = S.gptr[j]; p < S.gptr[j + 1]; ++p) {
-            const int64_t loc = std::lower_bound(rb, re, S.grow[p]) - rb;
-            S.gpos[p] = S.L_off[s] + (j - f) * ld + loc;
+    run_parts(nt, [&](unsigned t) {
+        for (int64_t j = n * t / nt; j < n * (t + 1) / nt; ++j) {
+            const int32_t s = S.col_sn[j], f = S.sn_first[s];
+            const int64_t h = S.rows_off[s + 1] - S.rows_off[s], ld = (h + 3) / 4 * 4;
+            const int32_t *rb = S.rows.data() + S.rows_off[s], *re = S.rows.data() + S.rows_off[s + 1];
+            for (int64_t p = S.gptr[j]; p < S.gptr[j + 1]; ++p) {
+                const int64_t loc = std::lower_bound(rb, re, S.grow[p]) - rb;
+                S.gpos[p] = S.L_off[s] + (j - f) * ld + loc;
+            }
         }
-    }
+    });
     S.perm.swap(perm);
     S.iperm.swap(iperm);
     S.parent.swap(parent);
