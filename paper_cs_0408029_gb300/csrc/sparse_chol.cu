@@ -7,9 +7,9 @@
 // and its entry of every solve is 0.
 //
 // Factor (multifrontal): one persistent kernel, one CTA per SM.  CTAs take
-// supernodes in postorder by ticket; a supernode waits (bounded) until its
-// children in the supernodal tree are done -- CTAs holding smaller tickets,
-// so running or finished.  It then
+// supernodes by ticket in order of height in the supernodal tree (leaves
+// first); a supernode waits (bounded) until its children are done -- CTAs
+// holding smaller tickets, so running or finished.  It then
 //   - clears its panel (rows x width) and its update matrix (rows below
 //     squared), assembles the entries of G' in its columns, and adds its
 //     children's update matrices, child by child in ascending order, through
@@ -18,10 +18,10 @@
 //     block code of the blocked factorisation (dense_block.cuh) and forms
 //     the rows below as X = B W^T, 32 rows at a time;
 //   - subtracts X X^T from its update matrix and publishes a done flag.
-// Solves: forward in postorder (a supernode adds its children's update
-// vectors, applies W, and leaves the update vector of its rows below for its
-// parent), backward in reverse postorder (it gathers the solved entries of
-// its rows below from the supernodes above, then applies W^T).  Every sum
+// Solves: forward in the factor's order (a supernode adds its children's
+// update vectors, applies W, and leaves the update vector of its rows below
+// for its parent), backward by depth, roots first (it gathers the solved
+// entries of its rows below from the supernodes above, then applies W^T).  Every sum
 // runs in a fixed order, so results are reproducible.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -480,8 +480,8 @@ __global__ void __launch_bounds__(256, 1)
     for (;;) {
         if (tid == 0) sh_s = atomicAdd(D.ticket, 1);
         __syncthreads();
-        const int64_t s = sh_s;
-        if (s >= D.ns) return;
+        if (sh_s >= D.ns) return;
+        const int64_t s = D.order_up[sh_s];
         if constexpr (sizeof(T) == 4) {
             if (!sp_wait_help(D, D.clist, D.c_off[s], D.c_off[s + 1], reinterpret_cast<const float *>(L),
                               reinterpret_cast<float *>(Ua), reinterpret_cast<float *>(smem_raw), st, job_sh))
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-constexpr int kSpT = 128;  // threads of a solve CTA
+constexpr int kSpT = 256;  // threads of a solve CTA
 
 template <typename T>
 __global__ void __launch_bounds__(kSpT)
@@ -655,11 +655,11 @@ __global__ void __launch_bounds__(kSpT)
     for (;;) {
         if (tid == 0) sh_s = atomicAdd(D.ticket, 1);
         __syncthreads();
-        const int64_t s = sh_s;
-        if (s >= D.ns) return;
+        if (sh_s >= D.ns) return;
+        const int64_t s = D.order_up[sh_s];
         if (!sp_wait_all(D, D.flags, D.clist, D.c_off[s], D.c_off[s + 1], st, &ok_sh)) return;
         const int32_t f = D.sn_first[s], w = D.sn_first[s + 1] - f;
-        const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4, hu = h - w;
+        const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4;
         for (int64_t i = tid; i < h; i += kSpT) a[i] = i < w ? v[f + i] : T(0);
         __syncthreads();
         for (int64_t ci = D.c_off[s]; ci < D.c_off[s + 1]; ++ci) {
@@ -685,13 +685,31 @@ __global__ void __launch_bounds__(kSpT)
         }
         __syncthreads();
         // update vector of the rows below, what the parent subtracts: L_below y
-        // plus the children's updates passed through (a_below holds minus those)
+        // plus the children's updates passed through (a_below holds minus
+        // those).  A thread takes four rows at a time with 16-byte loads down
+        // the panel's columns (a column starts 16-byte aligned: ld and the
+        // panel offsets are multiples of 4), from the group holding row w.
         const T *Ls = L + D.L_off[s];
-        for (int64_t i = tid; i < hu; i += kSpT) {
-            T acc = -a[w + i];
-#pragma unroll 8
-            for (int k = 0; k < w; ++k) acc += Ls[(int64_t)k * ld + w + i] * y_sh[k];
-            ua[D.u_off[s] + i] = acc;
+        for (int64_t q = w / 4 + tid; q < (h + 3) / 4; q += kSpT) {
+            T acc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t r = 4 * q + j;
+                acc[j] = (r >= w && r < h) ? -a[r] : T(0);
+            }
+#pragma unroll 16
+            for (int k = 0; k < w; ++k) {
+                T l4[4];
+                ld4(Ls + (int64_t)k * ld + 4 * q, l4);
+                const T yk = y_sh[k];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] += l4[j] * yk;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t r = 4 * q + j;
+                if (r >= w && r < h) ua[D.u_off[s] + r - w] = acc[j];
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -713,7 +731,7 @@ __global__ void __launch_bounds__(kSpT)
         if (tid == 0) sh_s = atomicAdd(D.ticket, 1);
         __syncthreads();
         if (sh_s >= D.ns) return;
-        const int64_t s = D.ns - 1 - sh_s;  // reverse postorder
+        const int64_t s = D.order_down[sh_s];
         if (!sp_wait_all(D, D.flags, D.alist, D.a_off[s], D.a_off[s + 1], st, &ok_sh)) return;
         const int32_t f = D.sn_first[s], w = D.sn_first[s + 1] - f;
         const int32_t *rows = D.rows + D.rows_off[s];
@@ -726,23 +744,35 @@ __global__ void __launch_bounds__(kSpT)
         }
         __syncthreads();
         // t_c = y_c - sum_{p >= w} L(p, c) x(rows[p]): a warp takes four
-        // columns at a time (c0, c0 + 4, c0 + 8, c0 + 12), its lanes down them
-        // (coalesced, four independent sums), each summed in a fixed order
-        for (int c0 = warp; c0 < w; c0 += 16) {
+        // adjacent columns at a time, its lanes down them by groups of four
+        // rows with 16-byte loads (from the group holding row w; rows outside
+        // [w, h) count zero), four independent sums, each in a fixed order
+        constexpr int kWarps = kSpT / 32;
+        for (int c0 = 4 * warp; c0 < w; c0 += 4 * kWarps) {
             T acc[4] = {T(0), T(0), T(0), T(0)};
-            const T *lc = Ls + (int64_t)c0 * ld + w;
 #pragma unroll 2
-            for (int64_t p = lane; p < hu; p += 32) {
-                const T xp = xb[p];
+            for (int64_t q = w / 4 + lane; q < (h + 3) / 4; q += 32) {
+                T xv[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c0 + 4 * q < w) acc[q] += lc[(int64_t)4 * q * ld + p] * xp;
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t r = 4 * q + j;
+                    xv[j] = (r >= w && r < h) ? xb[r - w] : T(0);
+                }
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    if (c0 + cc < w) {
+                        T l4[4];
+                        ld4(Ls + (int64_t)(c0 + cc) * ld + 4 * q, l4);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[cc] += l4[j] * xv[j];
+                    }
+                }
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int cc = 0; cc < 4; ++cc) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-                if (lane == 0 && c0 + 4 * q < w) t_sh[c0 + 4 * q] = __ldcg(v + f + c0 + 4 * q) - acc[q];
+                for (int o = 16; o > 0; o >>= 1) acc[cc] += __shfl_xor_sync(0xffffffffu, acc[cc], o);
+                if (lane == 0 && c0 + cc < w) t_sh[c0 + cc] = __ldcg(v + f + c0 + cc) - acc[cc];
             }
         }
         __syncthreads();
@@ -783,6 +813,7 @@ size_t SparseChol<T>::device_bytes(const SparseSym &S, int /*ctas*/) {
     b += up(sizeof(T) * (size_t)S.L_off[ns]) + up(sizeof(T) * (size_t)S.W_off[ns]);
     b += up(sizeof(T) * (size_t)S.U_off[ns]) + up(sizeof(T) * nu + 4);   // update matrices and vectors
     b += up(4 * ns) + up(16) + up(4 * n);                                // flags, ticket / abort, permF
+    b += 2 * up(4 * ns);                                                 // ticket orders
     b += up(8 * (size_t)kSpJobSlots) + up(4 * (size_t)kSpJobSlots);      // job words and counts
     return b + 256;
 }
@@ -827,6 +858,8 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     int32_t *flags = (int32_t *)take(4 * ns);
     int32_t *ctl = (int32_t *)take(16);
     permF = (int32_t *)take(4 * n);
+    int32_t *order_up = (int32_t *)take(4 * ns);
+    int32_t *order_down = (int32_t *)take(4 * ns);
     D.job_word = (unsigned long long *)take(8 * (size_t)kSpJobSlots);
     D.job_done = (int32_t *)take(4 * (size_t)kSpJobSlots);
     D.njobs = ctas <= kSpJobSlots ? ctas : 0;
@@ -855,6 +888,8 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     up(grow_orig, S.gpair_orig_row.data(), 4 * ng);
     up(gcol_orig, gcol.data(), 4 * ng);
     up(gpos, S.gpos.data(), 8 * ng);
+    up(order_up, S.order_up.data(), 4 * ns);
+    up(order_down, S.order_down.data(), 4 * ns);
     if (e != cudaSuccess) return e;
     // the host vectors must outlive the copies: wait for them here (setup runs once per problem)
     e = cudaStreamSynchronize(s);
@@ -877,6 +912,8 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     D.gcol_orig = gcol_orig;
     D.gpos = gpos;
     D.gval = gval;
+    D.order_up = order_up;
+    D.order_down = order_down;
     D.flags = flags;
     D.ticket = ctl;
     D.abort = ctl + 1;

@@ -23,6 +23,7 @@ struct SpDev {
     const int32_t *grow_orig, *gcol_orig;
     const int64_t *gpos;
     double *gval;        // A^T A on its lower pattern (FP64)
+    const int32_t *order_up, *order_down;  // ticket -> supernode (factor and forward; backward)
     int32_t *flags;      // per supernode: done
     int32_t *ticket;     // ticket counter, then the abort flag
     int32_t *abort;

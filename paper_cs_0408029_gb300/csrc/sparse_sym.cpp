@@ -24,10 +24,10 @@
 // Plain C++ on up to 16 threads, deterministic: no hashing; the
 // dissection's top splits hand one half to a thread of its own (the halves
 // touch disjoint vertices, and their orders are joined in a fixed order);
-// the per-column and per-supernode stages run on ranges of columns or
-// supernodes, and the column structures on disjoint subtrees of the
-// elimination tree, each writing only its own outputs.  The result does
-// not depend on the threads' timing.
+// the per-column and per-supernode stages run on chunks of columns or
+// supernodes taken in turn by the threads, and the column structures on
+// disjoint subtrees of the elimination tree, each writing only its own
+// outputs.  The result does not depend on the threads' timing.
 #include "sparse_sym.h"
 
 #include <algorithm>
@@ -47,25 +47,31 @@ struct Graph {
     std::vector<int32_t> adj;  // neighbours, no self loops, ascending
 };
 
-// Threads for one stage: up to 16, one per 4096 units of work.
+// Threads for one stage: up to 16, one per 4096 units of work, a core left
+// to the rest of the process.
 unsigned stage_threads(int64_t work) {
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
     const int64_t want = std::max<int64_t>(1, work / 4096);
-    return (unsigned)std::min<int64_t>(std::min<int64_t>(16, (int64_t)hw), want);
+    return (unsigned)std::min<int64_t>(std::min<int64_t>(16, std::max<int64_t>(1, hw - 1)), want);
 }
 
-// fn(t) for t = 0 .. nt - 1, each on a thread of its own where one can be
-// had (the calling thread takes t = 0 and whatever no thread could).  The
-// parts write disjoint outputs, so the result does not depend on timing.
+// fn(t, c) for the chunks c = 0 .. nchunks - 1, taken in turn by nt workers
+// (t = 0 .. nt - 1, each on a thread of its own where one can be had, the
+// calling thread as t = 0): a worker that the system delays leaves its
+// remaining chunks to the others.  The chunks write disjoint outputs, so the
+// result does not depend on timing.
 template <typename Fn>
-void run_parts(unsigned nt, Fn &&fn) {
+void run_chunks(int64_t nchunks, unsigned nt, Fn &&fn) {
+    std::atomic<int64_t> next{0};
+    auto worker = [&](unsigned t) {
+        for (int64_t c; (c = next.fetch_add(1)) < nchunks;) fn(t, c);
+    };
     std::vector<std::thread> th;
     try {
-        for (unsigned t = 1; t < nt; ++t) th.emplace_back(fn, t);
-    } catch (const std::system_error &) {  // fewer threads to be had: the rest in line
+        for (unsigned t = 1; t < nt; ++t) th.emplace_back(worker, t);
+    } catch (const std::system_error &) {  // fewer threads to be had: the others take their chunks
     }
-    fn(0u);
-    for (unsigned t = 1 + (unsigned)th.size(); t < nt; ++t) fn(t);
+    worker(0u);
     for (auto &x : th) x.join();
 }
 
@@ -84,16 +90,18 @@ void gram_graph(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col
     g.n = n;
     g.ptr.assign(n + 1, 0);
     g.adj.clear();
-    // columns in contiguous ranges, one per thread (each with its own marks
-    // and output), joined in column order
+    // columns in contiguous chunks (each with its own output; a worker's
+    // marks are its own), joined in column order
     const unsigned nt = stage_threads(n);
-    std::vector<std::vector<int32_t>> adj(nt);
-    std::vector<std::vector<int64_t>> cnt(nt);
-    auto work = [&](unsigned t) {
-        const int64_t j0 = n * t / nt, j1 = n * (t + 1) / nt;
-        std::vector<int32_t> mark(n, -1);
+    const int64_t nch = nt > 1 ? 8 * (int64_t)nt : 1;
+    std::vector<std::vector<int32_t>> adj(nch), marks(nt);
+    std::vector<std::vector<int64_t>> cnt(nch);
+    run_chunks(nch, nt, [&](unsigned t, int64_t ch) {
+        const int64_t j0 = n * ch / nch, j1 = n * (ch + 1) / nch;
+        std::vector<int32_t> &mark = marks[t];
+        if (mark.empty()) mark.assign(n, -1);
         std::vector<int32_t> nb;
-        cnt[t].assign(j1 - j0, 0);
+        cnt[ch].assign(j1 - j0, 0);
         for (int64_t j = j0; j < j1; ++j) {
             nb.clear();
             mark[j] = (int32_t)j;
@@ -108,15 +116,15 @@ void gram_graph(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col
                 }
             }
             std::sort(nb.begin(), nb.end());
-            adj[t].insert(adj[t].end(), nb.begin(), nb.end());
-            cnt[t][j - j0] = (int64_t)nb.size();
+            adj[ch].insert(adj[ch].end(), nb.begin(), nb.end());
+            cnt[ch][j - j0] = (int64_t)nb.size();
         }
-    };
-    run_parts(nt, work);
-    for (unsigned t = 0; t < nt; ++t) {
-        const int64_t j0 = n * t / nt;
-        for (size_t q = 0; q < cnt[t].size(); ++q) g.ptr[j0 + (int64_t)q + 1] = g.ptr[j0 + (int64_t)q] + cnt[t][q];
-        g.adj.insert(g.adj.end(), adj[t].begin(), adj[t].end());
+    });
+    for (int64_t ch = 0; ch < nch; ++ch) {
+        const int64_t j0 = n * ch / nch;
+        for (size_t q = 0; q < cnt[ch].size(); ++q)
+            g.ptr[j0 + (int64_t)q + 1] = g.ptr[j0 + (int64_t)q] + cnt[ch][q];
+        g.adj.insert(g.adj.end(), adj[ch].begin(), adj[ch].end());
     }
 }
 
@@ -336,10 +344,11 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
     S.grow.clear();
     S.gpair_orig_row.clear();
     const unsigned nt = stage_threads(n);
+    const int64_t ncc = nt > 1 ? 8 * (int64_t)nt : 1;  // column chunks
     {
-        // counts, then each column range fills its own part
-        run_parts(nt, [&](unsigned t) {
-            for (int64_t j = n * t / nt; j < n * (t + 1) / nt; ++j) {
+        // counts, then each column chunk fills its own part
+        run_chunks(ncc, nt, [&](unsigned, int64_t ch) {
+            for (int64_t j = n * ch / ncc; j < n * (ch + 1) / ncc; ++j) {
                 const int32_t vj = perm[j];
                 int64_t c = 1;
                 for (int64_t p = g.ptr[vj]; p < g.ptr[vj + 1]; ++p) c += iperm[g.adj[p]] > j;
@@ -349,8 +358,8 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
         for (int64_t j = 0; j < n; ++j) S.gptr[j + 1] += S.gptr[j];
         S.grow.resize(S.gptr[n]);
         S.gpair_orig_row.resize(S.gptr[n]);
-        run_parts(nt, [&](unsigned t) {
-            for (int64_t j = n * t / nt; j < n * (t + 1) / nt; ++j) {
+        run_chunks(ncc, nt, [&](unsigned, int64_t ch) {
+            for (int64_t j = n * ch / ncc; j < n * (ch + 1) / ncc; ++j) {
                 int32_t *o = S.grow.data() + S.gptr[j];
                 int64_t c = 0;
                 o[c++] = (int32_t)j;
@@ -413,15 +422,12 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
         for (int64_t j = 0; j < n; ++j)
             if (desc[j] <= thr && (parent[j] < 0 || desc[parent[j]] > thr)) task.push_back((int32_t)j);
         std::stable_sort(task.begin(), task.end(), [&](int32_t a, int32_t b) { return desc[a] > desc[b]; });
-        std::atomic<size_t> next_task{0};
-        run_parts(nt, [&](unsigned) {
-            std::vector<int32_t> tmp;
-            for (size_t q; (q = next_task.fetch_add(1)) < task.size();)
-                for (int64_t j = task[q] - desc[task[q]] + 1; j <= task[q]; ++j) column(j, tmp);
+        std::vector<std::vector<int32_t>> tmps(nt);
+        run_chunks((int64_t)task.size(), nt, [&](unsigned t, int64_t q) {
+            for (int64_t j = task[q] - desc[task[q]] + 1; j <= task[q]; ++j) column(j, tmps[t]);
         });
-        std::vector<int32_t> tmp;
         for (int64_t j = 0; j < n; ++j)
-            if (desc[j] > thr) column(j, tmp);
+            if (desc[j] > thr) column(j, tmps[0]);
     }
 
     // 5. fundamental supernodes, at most max_width wide ...
@@ -531,8 +537,8 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
             if (S.sparent[sn] >= 0) S.clist[fill[S.sparent[sn]]++] = (int32_t)sn;
     }
     S.rel.assign(S.u_off[ns], 0);
-    run_parts(nt, [&](unsigned t) {
-        for (int64_t sn = ns * t / nt; sn < ns * (t + 1) / nt; ++sn) {
+    run_chunks(ncc, nt, [&](unsigned, int64_t ch) {
+        for (int64_t sn = ns * ch / ncc; sn < ns * (ch + 1) / ncc; ++sn) {
             const int32_t pa = S.sparent[sn];
             if (pa < 0) continue;
             const int32_t w = S.sn_first[sn + 1] - S.sn_first[sn];
@@ -542,6 +548,30 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
                 S.rel[k++] = (int32_t)(std::lower_bound(pb, pe, S.rows[q]) - pb);
         }
     });
+    // Ticket orders.  A CTA waits only on supernodes of earlier tickets, so
+    // any order with children before parents serves the factor and the
+    // forward solve, and any with parents before children the backward
+    // solve.  Levels keep the CTAs on supernodes that become ready together:
+    // by height for the first two (every leaf before any parent), by depth
+    // for the third (every supernode of one level below the root before the
+    // next), where a postorder would send them down one subtree at a time.
+    {
+        std::vector<int32_t> height(ns, 0), depth(ns, 0);
+        for (int64_t sn = 0; sn < ns; ++sn)  // children before parents
+            if (S.sparent[sn] >= 0) height[S.sparent[sn]] = std::max(height[S.sparent[sn]], height[sn] + 1);
+        for (int64_t sn = ns - 1; sn >= 0; --sn)  // parents before children
+            depth[sn] = S.sparent[sn] >= 0 ? depth[S.sparent[sn]] + 1 : 0;
+        S.order_up.resize(ns);
+        S.order_down.resize(ns);
+        for (int64_t sn = 0; sn < ns; ++sn) {
+            S.order_up[sn] = (int32_t)sn;
+            S.order_down[sn] = (int32_t)(ns - 1 - sn);
+        }
+        std::stable_sort(S.order_up.begin(), S.order_up.end(),
+                         [&](int32_t a, int32_t b) { return height[a] < height[b]; });
+        std::stable_sort(S.order_down.begin(), S.order_down.end(),
+                         [&](int32_t a, int32_t b) { return depth[a] < depth[b]; });
+    }
     // A(s): the supernodes holding s's rows below (ascending), for the backward solve
     S.a_off.assign(ns + 1, 0);
     S.alist.clear();
@@ -560,8 +590,8 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
     // where each lower entry of P G P^T lands: panel of its column's
     // supernode, column j - f, local row = position of i among the rows
     S.gpos.resize(S.grow.size());
-    run_parts(nt, [&](unsigned t) {
-        for (int64_t j = n * t / nt; j < n * (t + 1) / nt; ++j) {
+    run_chunks(ncc, nt, [&](unsigned, int64_t ch) {
+        for (int64_t j = n * ch / ncc; j < n * (ch + 1) / ncc; ++j) {
             const int32_t s = S.col_sn[j], f = S.sn_first[s];
             const int64_t h = S.rows_off[s + 1] - S.rows_off[s], ld = (h + 3) / 4 * 4;
             const int32_t *rb = S.rows.data() + S.rows_off[s], *re = S.rows.data() + S.rows_off[s + 1];

@@ -29,6 +29,10 @@ struct SparseSym {
                                      //   vectors of the forward solve, and rel)
     std::vector<int32_t> rel;        // position of each row below among the parent's rows
     std::vector<int32_t> sparent;    // supernodal tree, -1 at a root
+    std::vector<int32_t> order_up;   // ns: the order in which CTAs take supernodes for the factor and
+                                     //   the forward solve: by height (leaves first), ties in postorder
+    std::vector<int32_t> order_down; // ns: the same for the backward solve: by depth (roots first),
+                                     //   ties in reverse postorder
     std::vector<int64_t> c_off;      // ns + 1: clist[c_off[s] ..] = children of s, ascending
     std::vector<int32_t> clist;
     std::vector<int64_t> a_off;      // ns + 1: alist[a_off[s] ..] = supernodes holding s's rows below
