@@ -100,3 +100,50 @@ def test_sparse_full_size_grid(env):
     assert kkt.violation(p, x64) <= 1e-10 * atb
     assert np.linalg.norm(xm - x64) <= 1e-9 * np.linalg.norm(x64)
     assert im.iters == i64.iters and im.path_used == ts.PATH_SPARSE
+
+
+def _block_diagonal(p1, p2):
+    """A = diag(A1, A2) with b = (b1, b2): two independent problems, so the
+    Gram pattern has two components and the supernodal tree two roots."""
+    return workloads.CSRProblem(
+        m=p1.m + p2.m, n=p1.n + p2.n,
+        row_ptr=np.concatenate([p1.row_ptr, p1.row_ptr[-1] + p2.row_ptr[1:]]).astype(np.int64),
+        col_idx=np.concatenate([p1.col_idx, p2.col_idx + p1.n]).astype(np.int32),
+        val=np.concatenate([p1.val, p2.val]), b=np.concatenate([p1.b, p2.b]),
+        x_planted=np.concatenate([p1.x_planted, p2.x_planted]), name="block_diagonal")
+
+
+def test_sparse_disconnected_gram(env, oracle_mod):
+    """Two components: a forest of supernodal trees, each root taken by depth
+    0 in the backward solve's order; against the oracle, trace included."""
+    ts, ctx, _ = env
+    p = _block_diagonal(workloads.grid_sparse(12, seed=21), workloads.grid_sparse(10, seed=22))
+    _, parent, _ = ts.sparse_analyze(p.m, p.n, p.row_ptr, p.col_idx)
+    assert (parent < 0).sum() >= 2  # the elimination forest has a root per component
+    ref = oracle_mod.bpp_solve(p)
+    for precision in ("mixed", "fp64"):
+        x, y, inF, trace, info = ctx.solve_ex(ts.HostCSR.from_problem(p), p.b, precision=precision,
+                                              path="sparse")
+        _check(p, ref, x, inF)
+        assert np.array_equal(trace, ref.trace)
+
+
+def test_sparse_shared_update_matrices_match_dense_path(env):
+    """A 96 x 96 grid, whose tallest supernodes have update matrices of three
+    and more 128 x 128 blocks (shared out to waiting CTAs in the FP32
+    factor): the same trace and F as the dense path, x within 1e-12, and
+    bitwise repeatable."""
+    ts, ctx, _ = env
+    p = workloads.grid_sparse(96, seed=23)
+    _, _, st = ts.sparse_analyze(p.m, p.n, p.row_ptr, p.col_idx)
+    # the tallest supernode (at most 64 columns) has more than 128 rows below:
+    # its update matrix spans 2 x 2 block rows, three 128 x 128 blocks or more
+    assert st["max_height"] > 128 + 64
+    A = ts.HostCSR.from_problem(p)
+    xs, _, fs, trs, _ = ctx.solve_ex(A, p.b, path="sparse")
+    xd, _, fd, trd, _ = ctx.solve_ex(A, p.b, path="factor")
+    assert np.array_equal(trs, trd) and np.array_equal(fs, fd)
+    assert np.linalg.norm(xs - xd) <= 1e-12 * np.linalg.norm(xd)
+    xs2, _ = ctx.solve(A, p.b, path="sparse")
+    assert np.array_equal(xs, xs2)
+    assert kkt.violation(p, xs) <= 1e-10 * kkt.atb_norm(p)
