@@ -111,15 +111,16 @@ __global__ void sp_permF_kernel(int64_t n, const int32_t *__restrict__ perm, con
 // Extend-add of a child's update matrix Uc (hc x hc lower, leading dimension
 // lduc) into this supernode's panel P (rows h, leading dimension ld, w
 // columns) and update matrix U (leading dimension ldu): child row i lands on
-// row rel[i] (increasing in i).  A warp takes a column j of Uc, its lanes the
-// rows i >= j, eight at a time with every load issued before the stores (the
-// targets of distinct (i, j) are distinct, so the reordering is safe).
+// row rel[i] (increasing in i).  Child columns j0 .. j1 - 1: a warp takes a
+// column j of Uc, its lanes the rows i >= j, eight at a time with every load
+// issued before the stores (the targets of distinct (i, j) are distinct, so
+// the reordering is safe).
 template <typename T>
 __device__ __noinline__ void sp_extend_add(const T *__restrict__ Uc, int64_t lduc, int64_t hc,
                                            const int32_t *__restrict__ rel, T *P, int64_t ld, T *U,
-                                           int64_t ldu, int w, int64_t h) {
+                                           int64_t ldu, int w, int64_t h, int64_t j0, int64_t j1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t j = warp; j < hc; j += 8) {
+    for (int64_t j = j0 + warp; j < j1; j += 8) {
         const int32_t lj = rel[j];
         if (!TS_IN(lj, h)) continue;
         // target column, indexed by li - roff
@@ -304,18 +305,26 @@ __device__ __noinline__ void sp_syrk(const T *X, int64_t ld, int64_t hu, int w, 
     }
 }
 
-// ---- shared update-matrix jobs (FP32 factor) ---------------------------------
-// The update matrix of a tall supernode near the root is most of the work on
-// the factor's critical path, while most CTAs wait for children there.  Its
-// owner posts it as a job of 128 x 128 blocks in its CTA's slot; CTAs that
-// wait for children take blocks meanwhile (a compare-and-swap on the slot's
-// word, which carries the supernode and the block count, so a stale read
-// never claims a block of a job that is not posted); the owner takes blocks
-// too, waits (bounded) until every block is done, frees the slot and only
-// then publishes its flag.  A block waits on nothing once claimed, so every
-// claimed block completes.
+// ---- shared jobs (FP32 factor) -----------------------------------------------
+// Near the root the factor's critical path is a chain of tall supernodes,
+// while most CTAs wait for children.  The owner of a tall supernode posts
+// three of its steps as jobs in its CTA's slot, one after the other: the
+// extend-add of its children by 64-column blocks of its own rows (a block
+// gathers, child by child in ascending order, every child column that lands
+// in it, so each entry receives its additions in the sequential order), the
+// rows below X = B W^T by 128-row blocks, and the update matrix by
+// 128 x 128 blocks.  CTAs that wait for children take blocks meanwhile (a
+// compare-and-swap on the slot's word, which carries the kind, the
+// supernode and the block count, so a stale read never claims a block of a
+// job that is not posted); the owner takes blocks too, waits (bounded) until
+// every block is done and frees the slot.  A block waits on nothing once
+// claimed, so every claimed block completes.
+//
+// Word: kind << 62 | (supernode + 1) << 40 | blocks << 20 | next block.
 
-constexpr int64_t kSpJobMinBlocks = 3;  // update matrices of at least 3 blocks (more than 128 rows)
+constexpr int kSpJobSyrk = 0, kSpJobTrsm = 1, kSpJobExtend = 2;
+constexpr int64_t kSpJobMinBlocks = 3;  // share a step of at least three blocks
+constexpr int64_t kSpMaxJobSupernodes = (1ll << 22) - 1;
 
 __device__ __forceinline__ unsigned long long sp_word_load(unsigned long long *p) {
     cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
@@ -328,29 +337,31 @@ __device__ __forceinline__ void sp_word_store(unsigned long long *p, unsigned lo
 __device__ __forceinline__ bool sp_word_open(unsigned long long w) {
     return (w >> 40) != 0 && (w & 0xFFFFFull) < ((w >> 20) & 0xFFFFFull);
 }
+__device__ __forceinline__ unsigned long long sp_word(int kind, int64_t s, int64_t nblk) {
+    return ((unsigned long long)kind << 62) | ((unsigned long long)(s + 1) << 40) | ((unsigned long long)nblk << 20);
+}
 
 // One thread: claim the next block of the job in slot sl, starting from the
-// word value w.  Returns the supernode (>= 0) and the block, or -1 once the
-// job has no block left.  A failed swap means that another CTA claimed a
-// block (or the job is gone), so the loop ends after at most as many turns
-// as the job has blocks.
-__device__ __forceinline__ int64_t sp_claim_slot(const SpDev &D, int sl, unsigned long long w, int64_t *blk) {
+// word value w.  Returns the claimed word (its low field is the block), or
+// 0 once the job has no block left.  A failed swap means that another CTA
+// claimed a block (or the job is gone), so the loop ends after at most as
+// many turns as the job has blocks.
+__device__ __forceinline__ unsigned long long sp_claim_slot(const SpDev &D, int sl, unsigned long long w) {
     while (sp_word_open(w)) {
         const unsigned long long prev = atomicCAS(D.job_word + sl, w, w + 1);
         if (prev == w) {
-            *blk = (int64_t)(w & 0xFFFFFull);
-            __threadfence();  // the owner's panel, published before its word, is visible from here on
-            return (int64_t)(w >> 40) - 1;
+            __threadfence();  // the owner's data, published before its word, is visible from here on
+            return w;
         }
         w = prev;
     }
-    return -1;
+    return 0ull;
 }
 
 // Warp 0: claim one block of any open job, the slots scanned by the lanes
-// from `first` round robin.  Returns the supernode (>= 0), its block and
-// slot, or -1.  Uniform across the warp.
-__device__ int64_t sp_claim_any(const SpDev &D, int first, int64_t *blk, int *slot) {
+// from `first` round robin.  Returns the claimed word and its slot, or 0.
+// Uniform across the warp.
+__device__ unsigned long long sp_claim_any(const SpDev &D, int first, int *slot) {
     const int lane = threadIdx.x & 31;
     for (int base = 0; base < D.njobs; base += 32) {
         const int sl = (first + base + lane) % D.njobs;
@@ -361,23 +372,17 @@ __device__ int64_t sp_claim_any(const SpDev &D, int first, int64_t *blk, int *sl
             const int src = __ffs(m) - 1;
             const int slw = __shfl_sync(0xffffffffu, sl, src);
             const unsigned long long ww = __shfl_sync(0xffffffffu, w, src);
-            long long got = -1, gb = 0;
-            if (lane == 0) {
-                int64_t b = 0;
-                got = sp_claim_slot(D, slw, ww, &b);
-                gb = b;
-            }
+            unsigned long long got = 0;
+            if (lane == 0) got = sp_claim_slot(D, slw, ww);
             got = __shfl_sync(0xffffffffu, got, 0);
-            gb = __shfl_sync(0xffffffffu, gb, 0);
-            if (got >= 0) {
-                *blk = gb;
+            if (got != 0) {
                 *slot = slw;
                 return got;
             }
             m &= m - 1;
         }
     }
-    return -1;
+    return 0ull;
 }
 
 __device__ __forceinline__ void sp_block_ij(int64_t b, int64_t &I, int64_t &J) {
@@ -388,50 +393,145 @@ __device__ __forceinline__ void sp_block_ij(int64_t b, int64_t &I, int64_t &J) {
     J = b - i * (i + 1) / 2;
 }
 
-// Block b of supernode s's update matrix (all 256 threads).
-__device__ void sp_job_block(const SpDev &D, const float *L, float *Ua, float *sm, int64_t s, int64_t b) {
+// Rows r_begin .. r_end - 1 (>= w) of X = B W^T in place over the panel P of
+// a supernode of w columns and h rows (leading dimension ld), W = the
+// inverse of its diagonal block from Ws (W(r, c) at Ws[c w + r]), 32 rows at
+// a time through shared memory (sm: W as Wt[t][c] = W(c, t), then the rows).
+// All 256 threads.
+__device__ void sp_trsm_rows(float *P, int64_t ld, int64_t h, int w, const float *Ws, float *sm,
+                             int64_t r_begin, int64_t r_end) {
+    const int tid = threadIdx.x;
+    float *Wt = sm;                                                 // [t][c], w x w
+    float(*Bs)[36] = reinterpret_cast<float(*)[36]>(sm + 64 * 64);  // Bs[t][r]
+    __syncthreads();
+    for (int e = tid; e < w * w; e += 256) Wt[e] = Ws[e];  // Ws[t w + c] = W(c, t)
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += 32) {
+        __syncthreads();
+        {  // all of this thread's loads (at most eight) before the stores
+            float bv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = tid + 256 * u, t = e / 32, rr = e % 32;
+                bv[u] = (e < w * 32 && r0 + rr < r_end) ? P[(int64_t)t * ld + r0 + rr] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = tid + 256 * u;
+                if (e < w * 32) Bs[e / 32][e % 32] = bv[u];
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < w * 32; e += 256) {
+            const int c = e / 32, rr = e % 32;
+            float acc = 0.f;
+            for (int t = 0; t <= c; ++t) acc += Bs[t][rr] * Wt[t * w + c];  // W(c, t), zero for t > c
+            if (r0 + rr < r_end) P[(int64_t)c * ld + r0 + rr] = acc;
+        }
+    }
+    __syncthreads();
+}
+
+// Number of entries of rel[0 .. n) (increasing) below lo and below hi, for
+// all 256 threads (red: 16 ints of shared scratch).
+__device__ void sp_count_below(const int32_t *rel, int64_t n, int32_t lo, int32_t hi, int *red, int64_t *c_lo,
+                               int64_t *c_hi) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int a = 0, b = 0;
+    for (int64_t j = tid; j < n; j += 256) {
+        const int32_t r = rel[j];
+        a += r < lo;
+        b += r < hi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        red[warp] = a;
+        red[8 + warp] = b;
+    }
+    __syncthreads();
+    int64_t sa = 0, sb = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        sa += red[q];
+        sb += red[8 + q];
+    }
+    *c_lo = sa;
+    *c_hi = sb;
+}
+
+// Block b of a posted job (all 256 threads).
+__device__ void sp_job_block(const SpDev &D, float *L, const float *Wa, float *Ua, float *sm, int *red,
+                             unsigned long long word) {
+    const int kind = (int)(word >> 62);
+    const int64_t s = (int64_t)((word >> 40) & 0x3FFFFFull) - 1, b = (int64_t)(word & 0xFFFFFull);
     const int32_t w = D.sn_first[s + 1] - D.sn_first[s];
     const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4;
     const int64_t hu = h - w, ldu = (hu + 3) / 4 * 4;
-    int64_t I, J;
-    sp_block_ij(b, I, J);
-    sp_syrk_block(L + D.L_off[s] + w, ld, hu, w, Ua + D.U_off[s], ldu, sm, I, J);
+    float *P = L + D.L_off[s];
+    if (kind == kSpJobSyrk) {
+        int64_t I, J;
+        sp_block_ij(b, I, J);
+        sp_syrk_block(P + w, ld, hu, w, Ua + D.U_off[s], ldu, sm, I, J);
+    } else if (kind == kSpJobTrsm) {
+        const int64_t r0 = w + 128 * b;
+        sp_trsm_rows(P, ld, h, w, Wa + D.W_off[s], sm, r0, min(h, r0 + 128));
+    } else {
+        // this supernode's rows [64 b, 64 b + 64) as columns: every child
+        // column landing there, child by child in ascending order
+        const int32_t lo = (int32_t)(64 * b), hi = (int32_t)min(h, 64 * b + 64);
+        for (int64_t ci = D.c_off[s]; ci < D.c_off[s + 1]; ++ci) {
+            const int32_t c = D.clist[ci];
+            const int32_t wc = D.sn_first[c + 1] - D.sn_first[c];
+            const int64_t hc = D.rows_off[c + 1] - D.rows_off[c] - wc, lduc = (hc + 3) / 4 * 4;
+            const int32_t *rel = D.rel + D.u_off[c];
+            int64_t j0, j1;
+            sp_count_below(rel, hc, lo, hi, red, &j0, &j1);
+            if (j1 > j0)
+                sp_extend_add<float>(Ua + D.U_off[c], lduc, hc, rel, P, ld, Ua + D.U_off[s], ldu, w, h, j0, j1);
+            __syncthreads();
+        }
+    }
 }
 
 // The factor's wait for flags[list[b..e)]: bounded, and taking blocks of
 // open jobs meanwhile.  Uniform across the CTA; false on abort or timeout.
-__device__ bool sp_wait_help(const SpDev &D, const int32_t *list, int64_t b, int64_t e, const float *L, float *Ua,
-                             float *sm, DevStatus *st, long long *sh) {
+__device__ bool sp_wait_help(const SpDev &D, const int32_t *list, int64_t b, int64_t e, float *L, const float *Wa,
+                             float *Ua, float *sm, int *red, DevStatus *st, long long *sh) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int idle = 0;
     for (;;) {
         if (warp == 0) {
             bool notready = false;
             for (int64_t i = b + lane; i < e; i += 32) notready |= sp_flag_load(D.flags + list[i]) == 0;
-            long long cmd = -1;  // -1: ready, -2: nothing to take, -3: abort, else a claimed supernode
-            int64_t blk = 0;
+            long long cmd = 0;  // 0: ready, 1: a claimed block, 2: nothing to take, 3: abort
+            unsigned long long got = 0;
             int slot = 0;
             if (__any_sync(0xffffffffu, notready)) {
                 if (sp_flag_load(D.abort) != 0) {
-                    cmd = -3;
+                    cmd = 3;
                 } else {
-                    const int64_t j = sp_claim_any(D, (int)((blockIdx.x + 1) % max(D.njobs, 1)), &blk, &slot);
-                    cmd = j >= 0 ? j : -2;
+                    got = sp_claim_any(D, (int)((blockIdx.x + 1) % max(D.njobs, 1)), &slot);
+                    cmd = got != 0 ? 1 : 2;
                 }
             }
             if (lane == 0) {
                 sh[0] = cmd;
-                sh[1] = blk;
+                sh[1] = (long long)got;
                 sh[2] = slot;
             }
         }
         __syncthreads();
-        const long long cmd = sh[0], blk = sh[1];
+        const long long cmd = sh[0];
+        const unsigned long long word = (unsigned long long)sh[1];
         const int slot = (int)sh[2];
         __syncthreads();
-        if (cmd == -1) return true;
-        if (cmd == -3) return false;
-        if (cmd == -2) {
+        if (cmd == 0) return true;
+        if (cmd == 3) return false;
+        if (cmd == 2) {
             if (++idle > kSpinLimit) {
                 if (tid == 0) {
                     sp_flag_store(D.abort, 1);
@@ -443,13 +543,64 @@ __device__ bool sp_wait_help(const SpDev &D, const int32_t *list, int64_t b, int
             continue;
         }
         idle = 0;
-        sp_job_block(D, L, Ua, sm, cmd, blk);
+        sp_job_block(D, L, Wa, Ua, sm, red, word);
         __syncthreads();
         if (tid == 0) {
             __threadfence();
             atomicAdd(D.job_done + slot, 1);
         }
     }
+}
+
+// The owner's side of a job: post it in this CTA's slot (everything the
+// blocks read is written and fenced before the word), take blocks until
+// none is left, wait (bounded) until the blocks other CTAs took are done,
+// free the slot.  Uniform across the CTA; false on abort or timeout.
+__device__ bool sp_run_job(const SpDev &D, int kind, int64_t s, int64_t nblk, float *L, const float *Wa, float *Ua,
+                           float *sm, int *red, DevStatus *st, long long *sh) {
+    const int tid = threadIdx.x, slot = (int)blockIdx.x;
+    __syncthreads();
+    if (tid == 0) {
+        D.job_done[slot] = 0;
+        __threadfence();
+        sp_word_store(D.job_word + slot, sp_word(kind, s, nblk));
+    }
+    __syncthreads();
+    for (;;) {
+        if (tid == 0) sh[0] = (long long)sp_claim_slot(D, slot, sp_word_load(D.job_word + slot));
+        __syncthreads();
+        const unsigned long long got = (unsigned long long)sh[0];
+        __syncthreads();
+        if (got == 0) break;
+        sp_job_block(D, L, Wa, Ua, sm, red, got);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(D.job_done + slot, 1);
+        }
+    }
+    if (tid == 0) {
+        int ok = 1, spins = 0;
+        cuda::atomic_ref<int32_t, cuda::thread_scope_device> dn(D.job_done[slot]);
+        while (dn.load(cuda::memory_order_acquire) < (int32_t)nblk) {
+            if (sp_flag_load(D.abort) != 0) { ok = 0; break; }
+            if (++spins > kSpinLimit) {
+                sp_flag_store(D.abort, 1);
+                st->timeout = 1;
+                ok = 0;
+                break;
+            }
+            if (spins > 8) __nanosleep(32);
+        }
+        if (ok) sp_word_store(D.job_word + slot, 0ull);
+        sh[1] = ok;
+    }
+    __syncthreads();
+    return sh[1] != 0;
+}
+
+__device__ __forceinline__ bool sp_share(const SpDev &D, int64_t nblk) {
+    return nblk >= kSpJobMinBlocks && (int)blockIdx.x < D.njobs && nblk < (1 << 20);
 }
 
 template <typename T, int NB>
@@ -475,28 +626,34 @@ __global__ void __launch_bounds__(256, 1)
     T(*Bs)[36] = reinterpret_cast<T(*)[36]>(smem_raw + 2 * sizeof(T) * NB * SM::P);  // Bs[t][r]
     __shared__ int sh_s, ok_sh, bad_sh;
     __shared__ long long job_sh[3];
+    __shared__ int red_sh[16];
     __shared__ __align__(16) T col[2][32];
     const int tid = threadIdx.x;
+    constexpr bool kF32 = sizeof(T) == 4;
+    float *Lf = reinterpret_cast<float *>(L);
+    float *Uf = reinterpret_cast<float *>(Ua);
+    const float *Wf = reinterpret_cast<const float *>(Wa);
+    float *smf = reinterpret_cast<float *>(smem_raw);
     for (;;) {
         if (tid == 0) sh_s = atomicAdd(D.ticket, 1);
         __syncthreads();
         if (sh_s >= D.ns) return;
         const int64_t s = D.order_up[sh_s];
-        if constexpr (sizeof(T) == 4) {
-            if (!sp_wait_help(D, D.clist, D.c_off[s], D.c_off[s + 1], reinterpret_cast<const float *>(L),
-                              reinterpret_cast<float *>(Ua), reinterpret_cast<float *>(smem_raw), st, job_sh))
-                return;
-        } else {
-            if (!sp_wait_all(D, D.flags, D.clist, D.c_off[s], D.c_off[s + 1], st, &ok_sh)) return;
-        }
         const int32_t f = D.sn_first[s], w = D.sn_first[s + 1] - f;
         const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4;
         const int64_t hu = h - w, ldu = (hu + 3) / 4 * 4;
         T *P = L + D.L_off[s];
         T *U = Ua + D.U_off[s];
+        // clear the panel and the update matrix before waiting: nothing else
+        // touches them until this supernode's children are done
         for (int64_t e = tid; e < ld * w; e += 256) P[e] = T(0);
         for (int64_t e = tid; e < ldu * hu; e += 256) U[e] = T(0);
-        __syncthreads();
+        if constexpr (kF32) {
+            if (!sp_wait_help(D, D.clist, D.c_off[s], D.c_off[s + 1], Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
+        } else {
+            __syncthreads();
+            if (!sp_wait_all(D, D.flags, D.clist, D.c_off[s], D.c_off[s + 1], st, &ok_sh)) return;
+        }
         // G' in this supernode's columns
         for (int64_t p = D.gptr[f] + tid; p < D.gptr[f + w]; p += 256) {
             const int32_t io = D.grow_orig[p], jo = D.gcol_orig[p];
@@ -505,15 +662,20 @@ __global__ void __launch_bounds__(256, 1)
             L[D.gpos[p]] = v;
         }
         __syncthreads();
-        // children's update matrices, one child after another (extend-add)
-        for (int64_t ci = D.c_off[s]; ci < D.c_off[s + 1]; ++ci) {
-            const int32_t c = D.clist[ci];
-            const int32_t wc = D.sn_first[c + 1] - D.sn_first[c];
-            const int64_t hc = D.rows_off[c + 1] - D.rows_off[c] - wc, lduc = (hc + 3) / 4 * 4;
-            const T *Uc = Ua + D.U_off[c];
-            const int32_t *rel = D.rel + D.u_off[c];
-            sp_extend_add<T>(Uc, lduc, hc, rel, P, ld, U, ldu, w, h);
-            __syncthreads();
+        // children's update matrices (extend-add): shared by 64-row blocks of
+        // this supernode's rows, or one child after another
+        if (kF32 && sp_share(D, (h + 63) / 64) && D.c_off[s + 1] > D.c_off[s]) {
+            if (!sp_run_job(D, kSpJobExtend, s, (h + 63) / 64, Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
+        } else {
+            for (int64_t ci = D.c_off[s]; ci < D.c_off[s + 1]; ++ci) {
+                const int32_t c = D.clist[ci];
+                const int32_t wc = D.sn_first[c + 1] - D.sn_first[c];
+                const int64_t hc = D.rows_off[c + 1] - D.rows_off[c] - wc, lduc = (hc + 3) / 4 * 4;
+                const T *Uc = Ua + D.U_off[c];
+                const int32_t *rel = D.rel + D.u_off[c];
+                sp_extend_add<T>(Uc, lduc, hc, rel, P, ld, U, ldu, w, h, 0, hc);
+                __syncthreads();
+            }
         }
         // the diagonal block: factor and inverse in shared memory
         if (tid == 0) bad_sh = 0;
@@ -549,86 +711,43 @@ __global__ void __launch_bounds__(256, 1)
             if (r >= c) P[(int64_t)c * ld + r] = Lsm(c, r);
             Ws[e] = Wsm(c, r);  // W(r, c), column-major, w x w
         }
-        // rows below: X = B W^T, 32 rows at a time through shared memory
-        // (Bs lies after both views of A and W)
-        for (int64_t r0 = w; r0 < h; r0 += 32) {
-            __syncthreads();
-            {  // all of this thread's loads (at most eight) before the stores
-                T bv[8];
+        // rows below: X = B W^T, shared by 128-row blocks, or 32 rows at a
+        // time through shared memory (Bs lies after both views of A and W)
+        if (kF32 && sp_share(D, (hu + 127) / 128)) {
+            if (!sp_run_job(D, kSpJobTrsm, s, (hu + 127) / 128, Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
+        } else {
+            for (int64_t r0 = w; r0 < h; r0 += 32) {
+                __syncthreads();
+                {  // all of this thread's loads (at most eight) before the stores
+                    T bv[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = tid + 256 * u, t = e / 32, rr = e % 32;
-                    bv[u] = (e < w * 32 && r0 + rr < h) ? P[(int64_t)t * ld + r0 + rr] : T(0);
-                }
+                    for (int u = 0; u < 8; ++u) {
+                        const int e = tid + 256 * u, t = e / 32, rr = e % 32;
+                        bv[u] = (e < w * 32 && r0 + rr < h) ? P[(int64_t)t * ld + r0 + rr] : T(0);
+                    }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = tid + 256 * u;
-                    if (e < w * 32) Bs[e / 32][e % 32] = bv[u];
+                    for (int u = 0; u < 8; ++u) {
+                        const int e = tid + 256 * u;
+                        if (e < w * 32) Bs[e / 32][e % 32] = bv[u];
+                    }
                 }
-            }
-            __syncthreads();
-            for (int e = tid; e < w * 32; e += 256) {
-                const int c = e / 32, rr = e % 32;
-                T acc = T(0);
-                for (int t = 0; t <= c; ++t) acc += Bs[t][rr] * Wsm(t, c);  // W(c, t), zero for t > c
-                if (r0 + rr < h) P[(int64_t)c * ld + r0 + rr] = acc;
+                __syncthreads();
+                for (int e = tid; e < w * 32; e += 256) {
+                    const int c = e / 32, rr = e % 32;
+                    T acc = T(0);
+                    for (int t = 0; t <= c; ++t) acc += Bs[t][rr] * Wsm(t, c);  // W(c, t), zero for t > c
+                    if (r0 + rr < h) P[(int64_t)c * ld + r0 + rr] = acc;
+                }
             }
         }
         __syncthreads();
         // update matrix: U -= X X^T on its lower triangle, X = rows below (hu x w)
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (kF32) {
             const int64_t nbu = (hu + 127) / 128, nblk = nbu * (nbu + 1) / 2;
-            const int slot = (int)blockIdx.x;
-            if (nblk >= kSpJobMinBlocks && slot < D.njobs && nblk < (1 << 20)) {
-                // post the job: the panel and U (zeroed, children added) are
-                // complete; the count of finished blocks is reset first
-                if (tid == 0) {
-                    D.job_done[slot] = 0;
-                    __threadfence();
-                    sp_word_store(D.job_word + slot,
-                                  ((unsigned long long)(s + 1) << 40) | ((unsigned long long)nblk << 20));
-                }
-                __syncthreads();
-                // take blocks of it until none is left
-                for (;;) {
-                    if (tid == 0) {
-                        int64_t b = 0;
-                        const int64_t got = sp_claim_slot(D, slot, sp_word_load(D.job_word + slot), &b);
-                        job_sh[0] = got >= 0 ? b : -1;
-                    }
-                    __syncthreads();
-                    const long long b = job_sh[0];
-                    __syncthreads();
-                    if (b < 0) break;
-                    sp_job_block(D, reinterpret_cast<const float *>(L), reinterpret_cast<float *>(Ua),
-                                 reinterpret_cast<float *>(smem_raw), s, b);
-                    __syncthreads();
-                    if (tid == 0) {
-                        __threadfence();
-                        atomicAdd(D.job_done + slot, 1);
-                    }
-                }
-                // wait (bounded) for the blocks other CTAs took, then free the slot
-                if (tid == 0) {
-                    int ok = 1, spins = 0;
-                    cuda::atomic_ref<int32_t, cuda::thread_scope_device> dn(D.job_done[slot]);
-                    while (dn.load(cuda::memory_order_acquire) < (int32_t)nblk) {
-                        if (sp_flag_load(D.abort) != 0) { ok = 0; break; }
-                        if (++spins > kSpinLimit) {
-                            sp_flag_store(D.abort, 1);
-                            st->timeout = 1;
-                            ok = 0;
-                            break;
-                        }
-                        if (spins > 8) __nanosleep(32);
-                    }
-                    if (ok) sp_word_store(D.job_word + slot, 0ull);
-                    ok_sh = ok;
-                }
-                __syncthreads();
-                if (!ok_sh) return;
+            if (sp_share(D, nblk)) {
+                if (!sp_run_job(D, kSpJobSyrk, s, nblk, Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
             } else {
-                sp_syrk_tiled(P + w, ld, hu, w, U, ldu, reinterpret_cast<float *>(smem_raw));
+                sp_syrk_tiled(P + w, ld, hu, w, U, ldu, smf);
             }
         } else {
             sp_syrk<T>(P + w, ld, hu, w, U, ldu);
@@ -862,7 +981,7 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     int32_t *order_down = (int32_t *)take(4 * ns);
     D.job_word = (unsigned long long *)take(8 * (size_t)kSpJobSlots);
     D.job_done = (int32_t *)take(4 * (size_t)kSpJobSlots);
-    D.njobs = ctas <= kSpJobSlots ? ctas : 0;
+    D.njobs = (ctas <= kSpJobSlots && S.ns < kSpMaxJobSupernodes) ? ctas : 0;
     // per-entry original column of the lower pattern
     std::vector<int32_t> gcol(ng);
     for (int64_t j = 0; j < S.n; ++j)
