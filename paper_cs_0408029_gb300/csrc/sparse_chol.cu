@@ -363,23 +363,31 @@ __device__ __forceinline__ unsigned long long sp_claim_slot(const SpDev &D, int 
 // Uniform across the warp.
 __device__ unsigned long long sp_claim_any(const SpDev &D, int first, int *slot) {
     const int lane = threadIdx.x & 31;
-    for (int base = 0; base < D.njobs; base += 32) {
-        const int sl = (first + base + lane) % D.njobs;
-        unsigned long long w = 0;
-        if (base + lane < D.njobs) w = sp_word_load(D.job_word + sl);
-        unsigned m = __ballot_sync(0xffffffffu, sp_word_open(w));
-        while (m) {
-            const int src = __ffs(m) - 1;
-            const int slw = __shfl_sync(0xffffffffu, sl, src);
-            const unsigned long long ww = __shfl_sync(0xffffffffu, w, src);
-            unsigned long long got = 0;
-            if (lane == 0) got = sp_claim_slot(D, slw, ww);
-            got = __shfl_sync(0xffffffffu, got, 0);
-            if (got != 0) {
-                *slot = slw;
-                return got;
+    constexpr int kRounds = 8;  // slot words a lane reads before the first is looked at
+    for (int base0 = 0; base0 < D.njobs; base0 += 32 * kRounds) {
+        unsigned long long ws[kRounds];
+#pragma unroll
+        for (int q = 0; q < kRounds; ++q) {
+            const int k = base0 + 32 * q + lane;
+            ws[q] = k < D.njobs ? sp_word_load(D.job_word + (first + k) % D.njobs) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < kRounds; ++q) {
+            const int sl = (first + base0 + 32 * q + lane) % D.njobs;
+            unsigned m = __ballot_sync(0xffffffffu, sp_word_open(ws[q]));
+            while (m) {
+                const int src = __ffs(m) - 1;
+                const int slw = __shfl_sync(0xffffffffu, sl, src);
+                const unsigned long long ww = __shfl_sync(0xffffffffu, ws[q], src);
+                unsigned long long got = 0;
+                if (lane == 0) got = sp_claim_slot(D, slw, ww);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (got != 0) {
+                    *slot = slw;
+                    return got;
+                }
+                m &= m - 1;
             }
-            m &= m - 1;
         }
     }
     return 0ull;

@@ -132,7 +132,11 @@ void gram_graph(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col
 // Nested dissection order (order[k] = vertex eliminated k-th).
 class Dissection {
   public:
-    explicit Dissection(const Graph &g) : g_(g), sub_(g.n, -1), level_(g.n, -1) {}
+    explicit Dissection(const Graph &g) : g_(g), sub_(g.n, -1), level_(g.n, -1) {
+        // one thread per core at the deepest threaded level (2^depth <= cores, at most 16)
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        while (thread_depth_ < 4 && (2u << thread_depth_) <= hw) ++thread_depth_;
+    }
 
     std::vector<int32_t> run() {
         std::vector<int32_t> all(g_.n);
@@ -145,9 +149,9 @@ class Dissection {
 
   private:
     static constexpr size_t kLeaf = 48;
-    // splits this shallow whose halves both hold this many vertices run the
-    // first half on a thread of its own (at most 2^kThreadDepth at once)
-    static constexpr int kThreadDepth = 3;
+    // splits shallower than thread_depth_ whose halves both hold this many
+    // vertices run the first half on a thread of its own (at most
+    // 2^thread_depth_ at once)
     static constexpr size_t kThreadMin = 4096;
     static constexpr size_t kOneSweep = 16384;
 
@@ -247,7 +251,7 @@ class Dissection {
             else s.push_back(v);
         }
         bool done = false;
-        if (tdepth < kThreadDepth && a.size() >= kThreadMin && b.size() >= kThreadMin) {
+        if (tdepth < thread_depth_ && a.size() >= kThreadMin && b.size() >= kThreadMin) {
             // a and b are not adjacent (their levels differ by two or more), so
             // the two searches read and write disjoint vertices
             std::vector<int32_t> oa, ob;
@@ -269,6 +273,7 @@ class Dissection {
     }
 
     const Graph &g_;
+    int thread_depth_ = 0;
     std::vector<int32_t> sub_, level_;
     std::atomic<int32_t> next_id_{0};
 };
