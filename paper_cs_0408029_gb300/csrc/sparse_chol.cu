@@ -615,7 +615,8 @@ template <typename T, int NB>
 struct SpSmem {
     static constexpr int P = NB + 4;
     static constexpr size_t core = sizeof(T) * (2 * (size_t)NB * P + (size_t)NB * 36);
-    // the FP32 update matrix's two staged operand panels (sp_syrk_tiled)
+    // the FP32 update matrix's two staged operand panels (sp_syrk_block),
+    // more than a shared panel solve's W and rows (25 KB) need
     static constexpr size_t tiled = sizeof(T) == 4 ? sizeof(float) * 2 * 64 * 132 : 0;
     static constexpr size_t bytes = core > tiled ? core : tiled;
 };
