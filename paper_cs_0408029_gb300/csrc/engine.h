@@ -54,10 +54,16 @@ struct Lane {
     // the batched path's last graph and device arena, replayed by the next
     // call of the same shape (batch.cu owns it; batch_cache_release frees it)
     void *batch_cache = nullptr;
+    // the dense factorisations captured as graphs and the keys seen once
+    // (engine.cu owns them; factor_graph_release frees them)
+    void *factor_graphs = nullptr;
 };
 
 // Free a lane's cached batched graph and arena (the lane's stream idle).
 void batch_cache_release(Lane &l);
+
+// Free a lane's cached factorisation graphs (the lane's streams idle).
+void factor_graph_release(Lane &l);
 
 // NVTX ranges for timeline tools (Nsight Systems): one per solve and one per
 // phase that prof_begin opens; inert unless a tool is attached.

@@ -266,6 +266,27 @@ def test_solve_is_deterministic(ts, ctx):
     assert np.array_equal(x1, x2)
 
 
+def test_factor_graph_replay_is_bitwise_equal(ts, ctx, oracle_mod):
+    """A lane launches a look-ahead factorisation directly the first time it
+    meets its key, captures it into a graph the second time and replays the
+    graph after that: every solve must be bitwise the one launched directly
+    and meet the oracle bar, also with a solve of another size in between."""
+    p = workloads.random_sparse(2600, 1300, 0.004, seed=3, zero_frac=0.4, noise=0.05)
+    q = workloads.random_sparse(900, 700, 0.01, seed=31)
+    ref = oracle_mod.bpp_solve(p)
+    A, B = ts.HostCSR.from_problem(p), ts.HostCSR.from_problem(q)
+    runs = [ctx.solve_ex(A, p.b) for _ in range(3)]
+    xq, _ = ctx.solve(B, q.b)
+    runs.append(ctx.solve_ex(A, p.b))
+    x0, _, inF0, tr0, _ = runs[0]
+    _check_solution(p, ref, x0, inF0)
+    assert np.array_equal(tr0, ref.trace)
+    for x, _, inF, tr, _ in runs[1:]:
+        assert np.array_equal(x, x0) and np.array_equal(inF, inF0) and np.array_equal(tr, tr0)
+    xq2, _ = ctx.solve(B, q.b)
+    assert np.array_equal(xq, xq2)
+
+
 def test_in_order_factor_matches_look_ahead(ts, ctx, oracle_mod):
     """Kernel-by-kernel timing runs the factorisation in order, without the
     look-ahead side stream: both schedules must meet the oracle bar and give
