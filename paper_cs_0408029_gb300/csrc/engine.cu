@@ -243,6 +243,7 @@ struct FactorGraph {
     FactorGraphKey key;
     cudaGraphExec_t exec = nullptr;
     uint64_t used = 0;
+    int64_t launches = 0;  // the kernels a replay runs (launch accounting)
 };
 
 struct FactorGraphCache {
@@ -291,6 +292,7 @@ static cudaError_t launch_cholesky_lane(Lane &lane, cudaStream_t s, T *S, int64_
     for (auto &g : c->graphs)
         if (g.key == key) {
             g.used = c->tick;
+            note_launches((int)g.launches);
             return cudaGraphLaunch(g.exec, s);
         }
     auto seen = std::find(c->seen.begin(), c->seen.end(), key);
@@ -301,7 +303,9 @@ static cudaError_t launch_cholesky_lane(Lane &lane, cudaStream_t s, T *S, int64_
     }
     e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
+    const int64_t l0 = launches_so_far();
     const cudaError_t el = launch_cholesky<T>(s, S, k, lds, lane.st_dev, tc, nullptr, &fs);
+    const int64_t nl = launches_so_far() - l0;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(s, &graph);
     if (el != cudaSuccess || e != cudaSuccess) {
@@ -324,7 +328,7 @@ static cudaError_t launch_cholesky_lane(Lane &lane, cudaStream_t s, T *S, int64_
         }
     }
     c->seen.erase(seen);
-    c->graphs.push_back(FactorGraph{key, exec, c->tick});
+    c->graphs.push_back(FactorGraph{key, exec, c->tick, nl});
     return cudaGraphLaunch(exec, s);
 }
 

@@ -513,6 +513,8 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
     double last_rel = 0.0;
     int64_t trace_rows = 0;
     const int64_t launch0 = launches_so_far();
+    cudaGraphExec_t corr_exec = nullptr;  // one correction's launches, replayed
+    int64_t corr_launches = 0;
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
     char *blk = nullptr;
     char *p = nullptr;
@@ -648,18 +650,53 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
                 TRY_CUDA_L(launch_spmv(s, m, row_ptr, col, val, -1.0, x, n, 1.0, bd, r, avg_row));
                 prof_end(lane, csr_bytes + 8.0 * (3.0 * m + n), 2.0 * nnz);
                 if (conv) break;
-                // inner LSQR on (A_F D) z = r
+                // inner LSQR on (A_F D) z = r.  The correction's launches are
+                // the same every time (every choice above is fixed per solve,
+                // the data lives on the device): captured into a graph on the
+                // first correction and replayed after, so the device starts
+                // each of its 3 inner + 4 kernels sooner
                 prof_begin(lane, TSNNLS_PHASE_LSQR);
-                lsqr_start_kernel<V><<<grid_for(m, L.tpr_r), kLT, 0, s>>>(m, n, r, u, v, w, z, part_u);
-                note_launches(1);
-                TRY_CUDA_L(launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, m, 0.0, nullptr, sv, avg_col));
-                L.vstart(sv, &sc[0]);
-                L.upd(&sc[0], &sc[0], 1);
-                for (int it = 0; it < inner; ++it) {
-                    LsqrScalars *cur = &sc[it & 1], *nxt = &sc[(it + 1) & 1];
-                    L.av_any(cur);
-                    L.atu_any(nxt);
-                    L.upd(cur, nxt, 0);
+                {
+                    auto issue = [&]() -> cudaError_t {
+                        lsqr_start_kernel<V><<<grid_for(m, L.tpr_r), kLT, 0, s>>>(m, n, r, u, v, w, z, part_u);
+                        note_launches(1);
+                        const cudaError_t e = launch_spmv(s, n, col_ptr, row_idx, cval, 1.0, r, m, 0.0, nullptr,
+                                                          sv, avg_col);
+                        if (e != cudaSuccess) return e;
+                        L.vstart(sv, &sc[0]);
+                        L.upd(&sc[0], &sc[0], 1);
+                        for (int it = 0; it < inner; ++it) {
+                            LsqrScalars *cur = &sc[it & 1], *nxt = &sc[(it + 1) & 1];
+                            L.av_any(cur);
+                            L.atu_any(nxt);
+                            L.upd(cur, nxt, 0);
+                        }
+                        return cudaGetLastError();
+                    };
+                    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                    TRY_CUDA_L(cudaStreamIsCapturing(s, &cs));
+                    if (corr_exec) {
+                        TRY_CUDA_L(cudaGraphLaunch(corr_exec, s));
+                        note_launches(corr_launches);
+                    } else if (cs != cudaStreamCaptureStatusNone) {
+                        TRY_CUDA_L(issue());  // inside a caller's own capture
+                    } else {
+                        const int64_t l0 = launches_so_far();
+                        TRY_CUDA_L(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                        const cudaError_t ei = issue();
+                        cudaGraph_t graph = nullptr;
+                        const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+                        if (ei != cudaSuccess || ee != cudaSuccess) {
+                            if (graph) cudaGraphDestroy(graph);
+                            TRY_CUDA_L(ei != cudaSuccess ? ei : ee);
+                        }
+                        const cudaError_t eg = cudaGraphInstantiate(&corr_exec, graph, 0);
+                        cudaGraphDestroy(graph);
+                        if (eg != cudaSuccess) corr_exec = nullptr;
+                        TRY_CUDA_L(eg);
+                        corr_launches = launches_so_far() - l0;
+                        TRY_CUDA_L(cudaGraphLaunch(corr_exec, s));
+                    }
                 }
                 // per inner step: both sparse products (index + value per nonzero,
                 // the row/column pointers), the u and v vectors and D, F flags
@@ -728,6 +765,7 @@ int solve_lsqr_t(Context &ctx, Lane &lane, const tsnnls_csr &A, const double *b,
 cleanup:
     cudaFreeAsync(blk, s);
     cudaStreamSynchronize(s);
+    if (corr_exec) cudaGraphExecDestroy(corr_exec);
     prof_flush(lane);
     if (ex && ex->trace) {
         int64_t best = INT64_MAX;
