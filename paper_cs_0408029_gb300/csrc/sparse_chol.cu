@@ -476,6 +476,7 @@ __device__ void sp_job_block(const SpDev &D, float *L, const float *Wa, float *U
                              unsigned long long word) {
     const int kind = (int)(word >> 62);
     const int64_t s = (int64_t)((word >> 40) & 0x3FFFFFull) - 1, b = (int64_t)(word & 0xFFFFFull);
+    if (!TS_IN(s, D.ns)) return;
     const int32_t w = D.sn_first[s + 1] - D.sn_first[s];
     const int64_t h = D.rows_off[s + 1] - D.rows_off[s], ld = (h + 3) / 4 * 4;
     const int64_t hu = h - w, ldu = (hu + 3) / 4 * 4;
