@@ -107,3 +107,29 @@ def test_malformed_pattern_rejected():
     with pytest.raises(ts.TsnnlsError) as e:
         ts.sparse_analyze(p.m, p.n, p.row_ptr, bad)
     assert e.value.status == ts.EINVAL
+
+
+def test_threaded_analysis_is_repeatable():
+    """A 160 x 160 grid (25600 columns) runs every threaded stage and the
+    dissection's one-search rule for large subgraphs: repeated analyses
+    give the same order, tree and structure, the tree is a postorder
+    (children before parents, every subtree just before its root) and the
+    order is a permutation."""
+    p = workloads.grid_sparse(160, seed=10)
+    runs = [ts.sparse_analyze(p.m, p.n, p.row_ptr, p.col_idx) for _ in range(3)]
+    perm, parent, st = runs[0]
+    for pm, pa, s in runs[1:]:
+        assert np.array_equal(pm, perm) and np.array_equal(pa, parent)
+        assert {k: v for k, v in s.items() if k != "analysis_ms"} == \
+            {k: v for k, v in st.items() if k != "analysis_ms"}
+    n = p.n
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    size = np.ones(n, dtype=np.int64)
+    for j in range(n):
+        if parent[j] >= 0:
+            assert parent[j] > j
+            size[parent[j]] += size[j]
+    for j in range(n):
+        if parent[j] >= 0:
+            assert j >= parent[j] - size[parent[j]] + 1
+    assert st["nnz_l_stored"] >= st["nnz_l"] > 0
