@@ -322,7 +322,9 @@ __device__ __noinline__ void sp_syrk(const T *X, int64_t ld, int64_t hu, int w, 
 //
 // Word: kind << 62 | (supernode + 1) << 40 | blocks << 20 | next block.
 
-constexpr int kSpJobSyrk = 0, kSpJobTrsm = 1, kSpJobExtend = 2;
+// kinds: the update matrix, the rows below, the extend-add (all blocks) and
+// the extend-add's blocks from the second on (the update matrix only)
+constexpr int kSpJobSyrk = 0, kSpJobTrsm = 1, kSpJobExtend = 2, kSpJobExtendRest = 3;
 constexpr int64_t kSpJobMinBlocks = 3;  // share a step of at least three blocks
 constexpr int64_t kSpMaxJobSupernodes = (1ll << 22) - 1;
 
@@ -489,9 +491,10 @@ __device__ void sp_job_block(const SpDev &D, float *L, const float *Wa, float *U
         const int64_t r0 = w + 128 * b;
         sp_trsm_rows(P, ld, h, w, Wa + D.W_off[s], sm, r0, min(h, r0 + 128));
     } else {
-        // this supernode's rows [64 b, 64 b + 64) as columns: every child
+        // this supernode's rows [64 bb, 64 bb + 64) as columns: every child
         // column landing there, child by child in ascending order
-        const int32_t lo = (int32_t)(64 * b), hi = (int32_t)min(h, 64 * b + 64);
+        const int64_t bb = kind == kSpJobExtendRest ? b + 1 : b;
+        const int32_t lo = (int32_t)(64 * bb), hi = (int32_t)min(h, 64 * bb + 64);
         for (int64_t ci = D.c_off[s]; ci < D.c_off[s + 1]; ++ci) {
             const int32_t c = D.clist[ci];
             const int32_t wc = D.sn_first[c + 1] - D.sn_first[c];
@@ -561,20 +564,24 @@ __device__ bool sp_wait_help(const SpDev &D, const int32_t *list, int64_t b, int
     }
 }
 
-// The owner's side of a job: post it in this CTA's slot (everything the
-// blocks read is written and fenced before the word), take blocks until
-// none is left, wait (bounded) until the blocks other CTAs took are done,
-// free the slot.  Uniform across the CTA; false on abort or timeout.
-__device__ bool sp_run_job(const SpDev &D, int kind, int64_t s, int64_t nblk, float *L, const float *Wa, float *Ua,
-                           float *sm, int *red, DevStatus *st, long long *sh) {
-    const int tid = threadIdx.x, slot = (int)blockIdx.x;
+// The owner's side of a job in slot `slot` (one of its CTA's two): post it
+// (everything the blocks read is written and fenced before the word) ...
+__device__ void sp_post_job(const SpDev &D, int slot, int kind, int64_t s, int64_t nblk) {
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         D.job_done[slot] = 0;
         __threadfence();
         sp_word_store(D.job_word + slot, sp_word(kind, s, nblk));
     }
     __syncthreads();
+}
+
+// ... then take blocks until none is left, wait (bounded) until the blocks
+// other CTAs took are done and free the slot.  Uniform across the CTA;
+// false on abort or timeout.
+__device__ bool sp_finish_job(const SpDev &D, int slot, int64_t nblk, float *L, const float *Wa, float *Ua,
+                              float *sm, int *red, DevStatus *st, long long *sh) {
+    const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) sh[0] = (long long)sp_claim_slot(D, slot, sp_word_load(D.job_word + slot));
         __syncthreads();
@@ -608,8 +615,14 @@ __device__ bool sp_run_job(const SpDev &D, int kind, int64_t s, int64_t nblk, fl
     return sh[1] != 0;
 }
 
+__device__ bool sp_run_job(const SpDev &D, int slot, int kind, int64_t s, int64_t nblk, float *L, const float *Wa,
+                           float *Ua, float *sm, int *red, DevStatus *st, long long *sh) {
+    sp_post_job(D, slot, kind, s, nblk);
+    return sp_finish_job(D, slot, nblk, L, Wa, Ua, sm, red, st, sh);
+}
+
 __device__ __forceinline__ bool sp_share(const SpDev &D, int64_t nblk) {
-    return nblk >= kSpJobMinBlocks && (int)blockIdx.x < D.njobs && nblk < (1 << 20);
+    return nblk >= kSpJobMinBlocks && 2 * (int)blockIdx.x + 1 < D.njobs && nblk < (1 << 20);
 }
 
 template <typename T, int NB>
@@ -672,10 +685,19 @@ __global__ void __launch_bounds__(256, 1)
             L[D.gpos[p]] = v;
         }
         __syncthreads();
-        // children's update matrices (extend-add): shared by 64-row blocks of
-        // this supernode's rows, or one child after another
-        if (kF32 && sp_share(D, (h + 63) / 64) && D.c_off[s + 1] > D.c_off[s]) {
-            if (!sp_run_job(D, kSpJobExtend, s, (h + 63) / 64, Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
+        // children's update matrices (extend-add), or one child after
+        // another.  Shared: the owner adds the first 64 of this supernode's
+        // rows (its whole panel: w <= 64) itself, while the blocks from the
+        // second on, which touch the update matrix only, go out as a job
+        // that runs beside the diagonal block and the rows below and is
+        // finished before the update matrix is
+        const int slot_a = 2 * (int)blockIdx.x, slot_b = slot_a + 1;
+        const int64_t nbe = (h + 63) / 64;
+        const bool ext_shared = kF32 && sp_share(D, nbe - 1) && D.c_off[s + 1] > D.c_off[s];
+        if (ext_shared) {
+            sp_post_job(D, slot_a, kSpJobExtendRest, s, nbe - 1);
+            sp_job_block(D, Lf, Wf, Uf, smf, red_sh, sp_word(kSpJobExtend, s, 1));  // block 0
+            __syncthreads();
         } else {
             for (int64_t ci = D.c_off[s]; ci < D.c_off[s + 1]; ++ci) {
                 const int32_t c = D.clist[ci];
@@ -724,7 +746,8 @@ __global__ void __launch_bounds__(256, 1)
         // rows below: X = B W^T, shared by 128-row blocks, or 32 rows at a
         // time through shared memory (Bs lies after both views of A and W)
         if (kF32 && sp_share(D, (hu + 127) / 128)) {
-            if (!sp_run_job(D, kSpJobTrsm, s, (hu + 127) / 128, Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
+            if (!sp_run_job(D, slot_b, kSpJobTrsm, s, (hu + 127) / 128, Lf, Wf, Uf, smf, red_sh, st, job_sh))
+                return;
         } else {
             for (int64_t r0 = w; r0 < h; r0 += 32) {
                 __syncthreads();
@@ -751,11 +774,13 @@ __global__ void __launch_bounds__(256, 1)
             }
         }
         __syncthreads();
+        // the rest of the extend-add, before the update matrix takes X X^T
+        if (ext_shared && !sp_finish_job(D, slot_a, nbe - 1, Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
         // update matrix: U -= X X^T on its lower triangle, X = rows below (hu x w)
         if constexpr (kF32) {
             const int64_t nbu = (hu + 127) / 128, nblk = nbu * (nbu + 1) / 2;
             if (sp_share(D, nblk)) {
-                if (!sp_run_job(D, kSpJobSyrk, s, nblk, Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
+                if (!sp_run_job(D, slot_a, kSpJobSyrk, s, nblk, Lf, Wf, Uf, smf, red_sh, st, job_sh)) return;
             } else {
                 sp_syrk_tiled(P + w, ld, hu, w, U, ldu, smf);
             }
@@ -991,7 +1016,7 @@ cudaError_t SparseChol<T>::setup(const SparseSym &S, void *mem, cudaStream_t s, 
     int32_t *order_down = (int32_t *)take(4 * ns);
     D.job_word = (unsigned long long *)take(8 * (size_t)kSpJobSlots);
     D.job_done = (int32_t *)take(4 * (size_t)kSpJobSlots);
-    D.njobs = (ctas <= kSpJobSlots && S.ns < kSpMaxJobSupernodes) ? ctas : 0;
+    D.njobs = (2 * ctas <= kSpJobSlots && S.ns < kSpMaxJobSupernodes) ? 2 * ctas : 0;  // two slots per CTA
     // per-entry original column of the lower pattern
     std::vector<int32_t> gcol(ng);
     for (int64_t j = 0; j < S.n; ++j)
