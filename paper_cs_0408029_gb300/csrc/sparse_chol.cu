@@ -308,12 +308,14 @@ __device__ __noinline__ void sp_syrk(const T *X, int64_t ld, int64_t hu, int w, 
 // ---- shared jobs (FP32 factor) -----------------------------------------------
 // Near the root the factor's critical path is a chain of tall supernodes,
 // while most CTAs wait for children.  The owner of a tall supernode posts
-// three of its steps as jobs in its CTA's slot, one after the other: the
-// extend-add of its children by 64-column blocks of its own rows (a block
-// gathers, child by child in ascending order, every child column that lands
-// in it, so each entry receives its additions in the sequential order), the
-// rows below X = B W^T by 128-row blocks, and the update matrix by
-// 128 x 128 blocks.  CTAs that wait for children take blocks meanwhile (a
+// three of its steps as jobs in its CTA's two slots: the extend-add of its
+// children by 64-column blocks of its own rows (a block gathers, child by
+// child in ascending order, every child column that lands in it, so each
+// entry receives its additions in the sequential order; the owner adds the
+// first block, its panel, itself, and the others, which touch the update
+// matrix only, run beside its diagonal block and its rows below), the rows
+// below X = B W^T by 128-row blocks, and the update matrix by 128 x 128
+// blocks.  CTAs that wait for children take blocks meanwhile (a
 // compare-and-swap on the slot's word, which carries the kind, the
 // supernode and the block count, so a stale read never claims a block of a
 // job that is not posted); the owner takes blocks too, waits (bounded) until

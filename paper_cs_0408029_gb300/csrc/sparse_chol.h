@@ -28,7 +28,7 @@ struct SpDev {
     int32_t *ticket;     // ticket counter, then the abort flag
     int32_t *abort;
     // shared jobs of the FP32 factor (extend-add, rows below, update
-    // matrix), one slot per CTA: the word holds kind << 62 | (supernode + 1)
+    // matrix), two slots per CTA: the word holds kind << 62 | (supernode + 1)
     // << 40 | blocks << 20 | next block to claim (0 = no job); done counts
     // the finished blocks
     unsigned long long *job_word;
