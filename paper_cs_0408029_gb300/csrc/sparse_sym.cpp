@@ -143,9 +143,15 @@ class Dissection {
         for (int64_t v = 0; v < g_.n; ++v) all[v] = (int32_t)v;
         std::vector<int32_t> order;
         order.reserve(g_.n);
-        split(all, order, 0);
+        split(all, order, 0, &ranges_);
         return order;
     }
+
+    // Ranges [b, e) of the order holding whole subtrees of the dissection
+    // that no edge joins to one another: every position outside them is a
+    // separator of a split that ran its halves on two threads, and lies after
+    // the ranges of both halves.
+    std::vector<std::pair<int64_t, int64_t>> ranges_;
 
   private:
     static constexpr size_t kLeaf = 48;
@@ -179,9 +185,14 @@ class Dissection {
     }
 
     // appends the order of verts (its halves', then its separator) to out
-    void split(std::vector<int32_t> &verts, std::vector<int32_t> &out, int tdepth) {
+    // ranges (may be null): where the independent subtrees of this call's
+    // output land in out (see ranges_)
+    void split(std::vector<int32_t> &verts, std::vector<int32_t> &out, int tdepth,
+               std::vector<std::pair<int64_t, int64_t>> *ranges) {
+        const int64_t base = (int64_t)out.size();
         if (verts.size() <= kLeaf) {
             out.insert(out.end(), verts.begin(), verts.end());
+            if (ranges) ranges->emplace_back(base, (int64_t)out.size());
             return;
         }
         const int32_t id = next_id_.fetch_add(2);
@@ -199,7 +210,7 @@ class Dissection {
                 for (int32_t u : c) sub_[u] = -2;
                 comps.push_back(std::move(c));
             }
-            for (auto &c : comps) split(c, out, tdepth);
+            for (auto &c : comps) split(c, out, tdepth, ranges);  // components are not adjacent
             return;
         }
         // pseudo-peripheral root: repeat from the farthest vertex while the
@@ -226,6 +237,7 @@ class Dissection {
         if (maxl < 2) {  // (nearly) complete subgraph: nothing to dissect
             out.insert(out.end(), verts.begin(), verts.end());
             for (int32_t v : verts) sub_[v] = -1;
+            if (ranges) ranges->emplace_back(base, (int64_t)out.size());
             return;
         }
         std::vector<int64_t> cnt(maxl + 1, 0);
@@ -255,21 +267,28 @@ class Dissection {
             // a and b are not adjacent (their levels differ by two or more), so
             // the two searches read and write disjoint vertices
             std::vector<int32_t> oa, ob;
+            std::vector<std::pair<int64_t, int64_t>> ra, rb;
             try {
-                std::thread t([&] { split(a, oa, tdepth + 1); });
-                split(b, ob, tdepth + 1);
+                std::thread t([&] { split(a, oa, tdepth + 1, &ra); });
+                split(b, ob, tdepth + 1, &rb);
                 t.join();
+                const int64_t ba = (int64_t)out.size(), bb = ba + (int64_t)oa.size();
                 out.insert(out.end(), oa.begin(), oa.end());
                 out.insert(out.end(), ob.begin(), ob.end());
+                if (ranges) {
+                    for (const auto &r : ra) ranges->emplace_back(ba + r.first, ba + r.second);
+                    for (const auto &r : rb) ranges->emplace_back(bb + r.first, bb + r.second);
+                }
                 done = true;
             } catch (const std::system_error &) {  // no thread to be had: in line
             }
         }
         if (!done) {
-            split(a, out, tdepth + 1);
-            split(b, out, tdepth + 1);
+            split(a, out, tdepth + 1, nullptr);
+            split(b, out, tdepth + 1, nullptr);
         }
         out.insert(out.end(), s.begin(), s.end());
+        if (!done && ranges) ranges->emplace_back(base, (int64_t)out.size());  // one subtree
     }
 
     const Graph &g_;
@@ -287,13 +306,19 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
     gram_graph(m, n, row_ptr, col, g);
 
     // 2. nested dissection, then 3. elimination tree and postorder
-    std::vector<int32_t> perm = Dissection(g).run();  // new -> old
+    Dissection nd(g);
+    std::vector<int32_t> perm = nd.run();  // new -> old
     std::vector<int32_t> iperm(n);
+    // Liu's algorithm, row by row.  A row of a dissection range meets only
+    // columns of its own range before it (the ranges are not joined by
+    // edges, and the separators come after them), and its ancestor walks stay
+    // in the range, so the ranges run on threads and the other rows follow
+    // in order: the same tree as one pass over all rows.
     auto etree_of = [&](const std::vector<int32_t> &pm, const std::vector<int32_t> &ipm,
                         std::vector<int32_t> &parent) {
         parent.assign(n, -1);
         std::vector<int32_t> anc(n, -1);
-        for (int64_t i = 0; i < n; ++i) {  // row i of the lower triangle: columns k < i
+        auto row = [&](int64_t i) {  // row i of the lower triangle: columns k < i
             const int32_t vi = pm[i];
             for (int64_t p = g.ptr[vi]; p < g.ptr[vi + 1]; ++p) {
                 int32_t k = ipm[g.adj[p]];
@@ -308,7 +333,16 @@ int sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *
                     parent[k] = (int32_t)i;
                 }
             }
-        }
+        };
+        const auto &rg = nd.ranges_;
+        std::vector<uint8_t> in_range(n, 0);
+        for (const auto &r : rg)
+            for (int64_t i = r.first; i < r.second; ++i) in_range[i] = 1;
+        run_chunks((int64_t)rg.size(), stage_threads(n), [&](unsigned, int64_t q) {
+            for (int64_t i = rg[q].first; i < rg[q].second; ++i) row(i);
+        });
+        for (int64_t i = 0; i < n; ++i)
+            if (!in_range[i]) row(i);
     };
     for (int64_t k = 0; k < n; ++k) iperm[perm[k]] = (int32_t)k;
     std::vector<int32_t> parent;
