@@ -163,24 +163,28 @@ class Dissection {
 
     // breadth-first levels inside the current subset (sub_ == id) from root;
     // returns the vertices in visiting order, level_ set for them
-    std::vector<int32_t> bfs(int32_t root, int32_t id, int32_t *last_level) {
+    std::vector<int32_t> bfs(int32_t root, int32_t id, int32_t *last_level, size_t cap) {
         std::vector<int32_t> q;
+        q.reserve(cap);  // the subset's size bounds the search (pages are touched only as it grows)
+        const int64_t *ptr = g_.ptr.data();
+        const int32_t *adj = g_.adj.data();
+        int32_t *sub = sub_.data(), *lev = level_.data();
         q.push_back(root);
-        level_[root] = 0;
-        sub_[root] = id + 1;  // visited marker: id + 1
+        lev[root] = 0;
+        sub[root] = id + 1;  // visited marker: id + 1
         for (size_t h = 0; h < q.size(); ++h) {
-            const int32_t v = q[h];
-            for (int64_t p = g_.ptr[v]; p < g_.ptr[v + 1]; ++p) {
-                const int32_t u = g_.adj[p];
-                if (sub_[u] == id) {
-                    sub_[u] = id + 1;
-                    level_[u] = level_[v] + 1;
+            const int32_t v = q[h], lv = lev[v] + 1;
+            for (int64_t p = ptr[v]; p < ptr[v + 1]; ++p) {
+                const int32_t u = adj[p];
+                if (sub[u] == id) {
+                    sub[u] = id + 1;
+                    lev[u] = lv;
                     q.push_back(u);
                 }
             }
         }
-        for (int32_t v : q) sub_[v] = id;  // back to "in the subset"
-        *last_level = level_[q.back()];
+        for (int32_t v : q) sub[v] = id;  // back to "in the subset"
+        *last_level = lev[q.back()];
         return q;
     }
 
@@ -199,14 +203,14 @@ class Dissection {
         for (int32_t v : verts) sub_[v] = id;
         // connected components of the subset, each dissected on its own
         int32_t last = 0;
-        std::vector<int32_t> comp = bfs(verts[0], id, &last);
+        std::vector<int32_t> comp = bfs(verts[0], id, &last, verts.size());
         if (comp.size() < verts.size()) {
             std::vector<std::vector<int32_t>> comps;
             for (int32_t v : comp) sub_[v] = -2;
             comps.push_back(comp);
             for (int32_t v : verts) {
                 if (sub_[v] != id) continue;
-                std::vector<int32_t> c = bfs(v, id, &last);
+                std::vector<int32_t> c = bfs(v, id, &last, 0);  // components may be many and small
                 for (int32_t u : c) sub_[u] = -2;
                 comps.push_back(std::move(c));
             }
@@ -220,10 +224,10 @@ class Dissection {
         // work came out 1 % lower, the analysis 12 % faster)
         int32_t root = comp.back(), depth = last, maxl = -1;
         const bool one_sweep = verts.size() > kOneSweep;
-        if (one_sweep) comp = bfs(root, id, &maxl);
+        if (one_sweep) comp = bfs(root, id, &maxl, verts.size());
         for (int it = 0; it < (one_sweep ? 0 : 4); ++it) {
             int32_t d2 = 0;
-            std::vector<int32_t> q = bfs(root, id, &d2);
+            std::vector<int32_t> q = bfs(root, id, &d2, verts.size());
             if (d2 <= depth && it > 0) {  // q is the level structure from root itself: keep it
                 comp.swap(q);
                 maxl = d2;
@@ -233,7 +237,7 @@ class Dissection {
             comp.swap(q);
             root = comp.back();
         }
-        if (maxl < 0) comp = bfs(root, id, &maxl);
+        if (maxl < 0) comp = bfs(root, id, &maxl, verts.size());
         if (maxl < 2) {  // (nearly) complete subgraph: nothing to dissect
             out.insert(out.end(), verts.begin(), verts.end());
             for (int32_t v : verts) sub_[v] = -1;
