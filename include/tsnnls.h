@@ -459,6 +459,23 @@ typedef struct {
 int tsnnls_sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t max_width,
                           int32_t *perm_out, int32_t *parent_out, tsnnls_sparse_stats *stats);
 
+/* The supernodal tree of the same analysis (host only, no GPU, no context;
+ * the arguments before ns_out as for tsnnls_sparse_analyze).  *ns_out
+ * receives the number of supernodes ns; each array (caller-owned, may be
+ * NULL, so a first call with NULL arrays learns ns) receives:
+ *   sn_first (ns + 1): supernode s holds positions sn_first[s] ..
+ *     sn_first[s + 1] - 1 of the order, supernodes in postorder;
+ *   sparent (ns): the parent supernode, -1 at a root;
+ *   order_up (ns): the order in which the persistent factor and forward-solve
+ *     kernels take supernodes by ticket (by height: every child before its
+ *     parent, which their waits rely on);
+ *   order_down (ns): the same for the backward solve (by depth: every parent
+ *     before its children).
+ * TSNNLS_EINVAL for a malformed pattern or a NULL ns_out. */
+int tsnnls_sparse_supernodes(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                             int32_t max_width, int64_t *ns_out, int32_t *sn_first, int32_t *sparent,
+                             int32_t *order_up, int32_t *order_down);
+
 /* Sparse products in FP64 on a device CSR matrix:
  *   trans == 0:  out = alpha * A x + beta * z   (x: n entries, out, z: m)
  *   trans == 1:  out = alpha * A^T x + beta * z (x: m entries, out, z: n)

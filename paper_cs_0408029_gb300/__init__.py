@@ -31,7 +31,7 @@ EXPORTS = (
     "tsnnls_queue_stats_read", "tsnnls_wait_probe", "tsnnls_submit_batch",
     "tsnnls_batch_member_info", "tsnnls_sparse_analyze", "tsnnls_solve_batch_dense_ex",
     "tsnnls_batch_autotune_cached", "tsnnls_batch_tune_key", "tsnnls_tune_cache_get",
-    "tsnnls_tune_cache_put", "tsnnls_check_build", "tsnnls_check_report",
+    "tsnnls_tune_cache_put", "tsnnls_check_build", "tsnnls_check_report", "tsnnls_sparse_supernodes",
 )
 
 PHASES = ("setup", "gram", "exchange", "gather", "factor", "trsv", "spmv", "vector", "lsqr",
@@ -139,6 +139,7 @@ def load(build_if_missing: bool = True):
                                 ctypes.c_int),
         "tsnnls_batch_member_info": ([p, i64, i32, ctypes.POINTER(Info)], ctypes.c_int),
         "tsnnls_sparse_analyze": ([i64, i64, p, p, i32, p, p, ctypes.POINTER(SparseStats)], ctypes.c_int),
+        "tsnnls_sparse_supernodes": ([i64, i64, p, p, i32, p, p, p, p, p], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -211,6 +212,23 @@ def sparse_analyze(m, n, row_ptr, col_idx, max_width=64):
     _check(load().tsnnls_sparse_analyze(int(m), int(n), _np_ptr(rp), _np_ptr(ci), int(max_width), _np_ptr(perm),
                                         _np_ptr(parent), ctypes.byref(st)), "sparse_analyze")
     return perm, parent, {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def sparse_supernodes(m, n, row_ptr, col_idx, max_width=64):
+    """Host-only supernodal tree of the sparse analysis: (sn_first, sparent,
+    order_up, order_down) as int32 arrays."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    ns = ctypes.c_int64(0)
+    f = load().tsnnls_sparse_supernodes
+    _check(f(int(m), int(n), _np_ptr(rp), _np_ptr(ci), int(max_width), ctypes.byref(ns), None, None, None, None),
+           "sparse_supernodes")
+    k = int(ns.value)
+    first = np.empty(k + 1, dtype=np.int32)
+    sparent, up, down = (np.empty(k, dtype=np.int32) for _ in range(3))
+    _check(f(int(m), int(n), _np_ptr(rp), _np_ptr(ci), int(max_width), ctypes.byref(ns), _np_ptr(first),
+             _np_ptr(sparent), _np_ptr(up), _np_ptr(down)), "sparse_supernodes")
+    return first, sparent, up, down
 
 
 def wait_probe(polls: int) -> int:

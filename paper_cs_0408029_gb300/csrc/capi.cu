@@ -321,6 +321,23 @@ int tsnnls_sparse_analyze(int64_t m, int64_t n, const int64_t *row_ptr, const in
     return TSNNLS_OK;
 }
 
+int tsnnls_sparse_supernodes(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                             int32_t max_width, int64_t *ns_out, int32_t *sn_first, int32_t *sparent,
+                             int32_t *order_up, int32_t *order_down) {
+    if (m <= 0 || n <= 0 || n > INT32_MAX || !row_ptr || max_width < 1 || !ns_out) return TSNNLS_EINVAL;
+    tsnnls_csr A{m, n, row_ptr[m], row_ptr, col_idx, nullptr, 0};
+    if (A.nnz > 0 && !col_idx) return TSNNLS_EINVAL;
+    auto S = analyze_gram_pattern(A, max_width);
+    if (!S) return TSNNLS_EINVAL;
+    const size_t ns = (size_t)S->ns;
+    *ns_out = S->ns;
+    if (sn_first) std::memcpy(sn_first, S->sn_first.data(), sizeof(int32_t) * (ns + 1));
+    if (sparent) std::memcpy(sparent, S->sparent.data(), sizeof(int32_t) * ns);
+    if (order_up) std::memcpy(order_up, S->order_up.data(), sizeof(int32_t) * ns);
+    if (order_down) std::memcpy(order_down, S->order_down.data(), sizeof(int32_t) * ns);
+    return TSNNLS_OK;
+}
+
 int tsnnls_queue_stats_read(tsnnls_ctx *ctx, tsnnls_queue_stats *out) {
     if (!ctx || !out) return TSNNLS_EINVAL;
     Context &c = ctx->c;

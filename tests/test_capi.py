@@ -51,6 +51,7 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.tsnnls_batch_member_info(None, 1, 0, None) == ts.EINVAL
     assert lib.tsnnls_poll(None, 1, None) == ts.EINVAL
     assert lib.tsnnls_ctx_create(None, 0, 0) == ts.EINVAL
+    assert lib.tsnnls_sparse_supernodes(1, 1, None, None, 64, None, None, None, None, None) == ts.EINVAL
 
 
 def test_struct_layouts_match_the_header(tmp_path):

@@ -133,3 +133,41 @@ def test_threaded_analysis_is_repeatable():
         if parent[j] >= 0:
             assert j >= parent[j] - size[parent[j]] + 1
     assert st["nnz_l_stored"] >= st["nnz_l"] > 0
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_ticket_orders_are_topological(case):
+    """The persistent sparse kernels take supernodes by ticket and wait only
+    on smaller tickets: the factor and the forward solve on children
+    (order_up must put every child before its parent), the backward solve on
+    the supernodes holding a supernode's rows below, its ancestors (order_down
+    must put every parent before its children).  Both orders are
+    permutations; order_up goes by height and order_down by depth; the
+    supernodes tile the columns in postorder with parents after children."""
+    p = [workloads.grid_sparse(96, seed=11), workloads.random_sparse(900, 700, 0.01, seed=31),
+         workloads.grid_sparse(7, seed=2)][case]
+    first, sparent, up, down = ts.sparse_supernodes(p.m, p.n, p.row_ptr, p.col_idx)
+    ns = sparent.size
+    assert first[0] == 0 and first[-1] == p.n and np.all(np.diff(first) >= 1)
+    assert np.all(np.diff(first) <= 64)
+    assert np.all((sparent == -1) | (sparent > np.arange(ns)))
+    for order in (up, down):
+        assert np.array_equal(np.sort(order), np.arange(ns))
+    pos_up = np.empty(ns, dtype=np.int64)
+    pos_up[up] = np.arange(ns)
+    pos_down = np.empty(ns, dtype=np.int64)
+    pos_down[down] = np.arange(ns)
+    has = sparent >= 0
+    child = np.nonzero(has)[0]
+    assert np.all(pos_up[child] < pos_up[sparent[child]])
+    assert np.all(pos_down[child] > pos_down[sparent[child]])
+    height = np.zeros(ns, dtype=np.int64)
+    for s in range(ns):  # children before parents
+        if sparent[s] >= 0:
+            height[sparent[s]] = max(height[sparent[s]], height[s] + 1)
+    depth = np.zeros(ns, dtype=np.int64)
+    for s in range(ns - 1, -1, -1):  # parents before children
+        if sparent[s] >= 0:
+            depth[s] = depth[sparent[s]] + 1
+    assert np.all(np.diff(height[up]) >= 0)
+    assert np.all(np.diff(depth[down]) >= 0)
